@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: discrete
+closed forms, continuum closed forms (second-order convergence), independent
+direct solvers, manufactured solutions evaluated symbolically, invariants of
+the multigrid operators, and the paper's own worked-example statements.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from oracle import exact
+
+
+def _grid(pr):
+    x = S.node_coords(pr["nx"], pr["Lx"])
+    y = S.node_coords(pr["ny"], pr["Ly"])
+    z = S.node_coords(pr["nz"], pr["Lz"])
+    return np.meshgrid(z, y, x, indexing="ij")  # Z, Y, X with shape [nz][ny][nx]
+
+
+# ---------------------------------------------------------------------------
+# Lower-boundary problem, eq. (lower_bound)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 3)])
+def test_2d_single_sine_mode_discrete_closed_form(m, n):
+    """B_z = sin(m pi x/Lx) sin(n pi y/Ly) is an eigenvector of the 5-point
+    Laplacian with Dirichlet edges; the exact discrete solution is B_z divided
+    by 4/hx^2 sin^2(m pi hx/(2Lx)) + 4/hy^2 sin^2(n pi hy/(2Ly))."""
+    pr = S.problem(17, 33, 3, Lx=1.0, Ly=2.0)
+    bz = S.magnetogram_mode(17, 33, 1.0, 2.0, m, n)
+    hx, hy = 1.0 / 16, 2.0 / 32
+    mu = 4 / hx**2 * math.sin(m * math.pi * hx / 2) ** 2 + 4 / hy**2 * math.sin(n * math.pi * hy / (2 * 2.0)) ** 2
+    expect = bz / mu
+    P0, cyc, rel, _ = oracle.solve2d(pr, bz, tol=1e-14, max_cycles=100)
+    assert rel < 1e-13
+    assert np.abs(P0 - expect).max() <= 1e-12 * np.abs(expect).max()
+    Ps = exact.separable_solve2d(pr, bz)
+    assert np.abs(Ps - expect).max() <= 1e-12 * np.abs(expect).max()
+
+
+def test_2d_fixed_point_of_paper_jacobi_update():
+    """The converged lower-boundary solution is a fixed point of the paper's
+    Gauss-Jacobi update (Sect. 4 listing):
+    P <- ((P_E + P_W)/dx^2 + (P_N + P_S)/dy^2 + B_z) / (2 (1/dx^2 + 1/dy^2)).
+    This fixes the sign convention P_xx + P_yy = -B_z and allows dx != dy."""
+    nx, ny = 33, 17
+    pr = S.problem(nx, ny, 3, Lx=1.0, Ly=0.75)
+    bz = S.magnetogram_random(nx, ny, 1.0, 0.75, seed=11)
+    P0, _, rel, _ = oracle.solve2d(pr, bz, tol=1e-14, max_cycles=100)
+    dx, dy = 1.0 / (nx - 1), 0.75 / (ny - 1)
+    idx2, idy2 = 1 / dx**2, 1 / dy**2
+    upd = ((P0[1:-1, 2:] + P0[1:-1, :-2]) * idx2 + (P0[2:, 1:-1] + P0[:-2, 1:-1]) * idy2 + bz[1:-1, 1:-1]) / (
+        2 * (idx2 + idy2))
+    assert np.abs(upd - P0[1:-1, 1:-1]).max() <= 1e-12 * np.abs(P0).max()
+
+
+def test_2d_multigrid_matches_two_direct_solvers():
+    pr = S.problem(65, 33, 3, Lx=1.0, Ly=0.5)
+    bz = S.magnetogram_random(65, 33, 1.0, 0.5, seed=5)
+    P0, _, rel, _ = oracle.solve2d(pr, bz, tol=1e-14, max_cycles=100)
+    Ps = exact.separable_solve2d(pr, bz)
+    Pk = exact.kron_solve2d(pr, bz)
+    sc = np.abs(Pk).max()
+    assert np.abs(Ps - Pk).max() <= 1e-12 * sc
+    assert np.abs(P0 - Pk).max() <= 1e-11 * sc
+
+
+# ---------------------------------------------------------------------------
+# Interior problem, eq. (scalar_pot)
+# ---------------------------------------------------------------------------
+
+XI2 = dict(xi_kind=2, xi_a=0.7, xi_b=0.3, xi_omega=math.pi, xi_kappa=0.1)   # the paper's xi_2 family
+XI1 = dict(xi_kind=1, xi_a=0.7, xi_kappa=0.2)                                # the paper's xi_1 family
+
+
+def test_two_direct_solvers_agree_variable_xi():
+    pr = S.problem(9, 17, 13, Lx=1.0, Ly=1.5, Lz=1.2, alpha=0.7, **XI2)
+    bz = S.magnetogram_random(9, 17, 1.0, 1.5, seed=2)
+    P0 = exact.separable_solve2d(pr, bz)
+    Ps = exact.separable_solve3d(pr, P0)
+    Pk = exact.kron_solve3d(pr, P0)
+    assert np.abs(Ps - Pk).max() <= 1e-13 * np.abs(Pk).max()
+
+
+@pytest.mark.parametrize("shape,xi", [((17, 17, 17), XI2), ((9, 17, 33), XI1), ((33, 33, 17), XI2)])
+def test_multigrid_matches_direct_solvers(shape, xi):
+    nx, ny, nz = shape
+    h = 1.0 / (max(shape) - 1)      # non-cubic grids with isotropic spacing
+    pr = S.problem(nx, ny, nz, Lx=h * (nx - 1), Ly=h * (ny - 1), Lz=h * (nz - 1), alpha=0.5, **xi)
+    bz = S.magnetogram_random(nx, ny, pr["Lx"], pr["Ly"], seed=7)
+    P, info = oracle.solve(pr, bz, 1e-14, 1e-13, max_cycles=100)
+    assert info["rel_res_3d"] < 1e-13
+    Pe = exact.exact_solution(pr, bz)
+    assert np.linalg.norm(P - Pe) <= 1e-11 * np.linalg.norm(Pe)
+    if nx * ny * nz <= 17**3:
+        Pk = exact.kron_solve3d(pr, exact.kron_solve2d(pr, bz))
+        assert np.linalg.norm(P - Pk) <= 1e-11 * np.linalg.norm(Pk)
+
+
+def _max_err_continuum(n, alpha=0.5, c=0.3, Lx=1.0, Ly=1.5, Lz=1.0):
+    pr = S.problem(n, n, n, Lx=Lx, Ly=Ly, Lz=Lz, alpha=alpha, xi_kind=1, xi_a=c, xi_kappa=0.0)
+    bz = S.magnetogram_mode(n, n, Lx, Ly, 1, 2)
+    P, info = oracle.solve(pr, bz, 1e-14, 1e-13, max_cycles=100)
+    Pc = exact.continuum_mode_solution(pr, 1, 2)
+    Z, Y, X = _grid(pr)
+    return np.abs(P - Pc(X, Y, Z)).max()
+
+
+def test_constant_xi_continuum_second_order():
+    """Constant xi = c: P = P0(x,y) sinh(k(Lz - z))/sinh(k Lz), k^2 = (1-c)K^2 - alpha^2,
+    solves eq. (scalar_pot) with eq. (lower_bound) on z = 0 and P = 0 on the
+    other faces.  The discrete solution must converge at second order."""
+    errs = [_max_err_continuum(n) for n in (9, 17, 33)]
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.6 < r < 4.4 for r in ratios), (errs, ratios)
+
+
+def _mms_case(n, xi_kind, alpha=0.5):
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    if xi_kind == 2:
+        xi = (sp.Rational(7, 10) + sp.Rational(3, 10) * sp.sin(sp.pi * z)) * sp.exp(-z / 10)
+        pars = XI2
+    else:
+        xi = sp.Rational(7, 10) * sp.exp(-z / 5)
+        pars = XI1
+    Pstar = sp.sin(sp.pi * x) * sp.sin(2 * sp.pi * y) * (1 - z) * sp.exp(z)
+    L = (1 - xi) * (sp.diff(Pstar, x, 2) + sp.diff(Pstar, y, 2)) + sp.diff(Pstar, z, 2) + alpha**2 * Pstar
+    fP = sp.lambdify((x, y, z), Pstar, "numpy")
+    fL = sp.lambdify((x, y, z), L, "numpy")
+    pr = S.problem(n, n, n, alpha=alpha, **pars)
+    Z, Y, X = _grid(pr)
+    Pex = fP(X, Y, Z)
+    f = fL(X, Y, Z)
+    P = np.zeros_like(Pex)
+    P[0], P[-1] = Pex[0], Pex[-1]
+    P[:, 0], P[:, -1], P[:, :, 0], P[:, :, -1] = Pex[:, 0], Pex[:, -1], Pex[:, :, 0], Pex[:, :, -1]
+    Ps, cyc, rel, _, _ = oracle.solve3d(pr, P, f, tol=1e-13, max_cycles=100)
+    assert rel < 1e-13
+    return np.abs(Ps - Pex).max()
+
+
+@pytest.mark.parametrize("xi_kind", [1, 2])
+def test_manufactured_solution_second_order(xi_kind):
+    """f = L P* for P* = sin(pi x) sin(2 pi y)(1 - z) e^z, L evaluated symbolically
+    from eq. (scalar_pot) with the paper's xi_1 / xi_2 families.  Any error in
+    where xi(z) enters, in the sign of alpha^2 or in a neighbour index fails
+    the second-order refinement."""
+    errs = [_mms_case(n, xi_kind) for n in (9, 17, 33)]
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
+
+
+def test_vcycle_convergence_factor():
+    """V(2,2) red-black Gauss-Seidel on the isotropic linear-MHS problem: the
+    mean residual reduction per cycle is well below 0.2 (threshold ours; the
+    paper prints no factor)."""
+    pr, bz = S.linear_mhs(65)
+    P, info = oracle.solve(pr, bz, 1e-12, 1e-12)
+    assert info["conv_factor_3d"] < 0.15
+    assert info["cycles_3d"] <= 14
+
+
+def test_potential_pair_antisymmetry():
+    """B_z of the +/- pair is odd under x -> 1 - x, hence so is P (xi = 0, alpha = 0)."""
+    pr, bz = S.potential_field_33()
+    P, info = oracle.solve(pr, bz, 1e-12, 1e-12)
+    assert np.abs(P + P[:, :, ::-1]).max() <= 1e-12 * np.abs(P).max()
+    assert info["rel_res_3d"] < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Multigrid building blocks
+# ---------------------------------------------------------------------------
+
+def test_red_black_sweep_zeroes_own_colour_residual():
+    """After the red half-sweep the residual vanishes at red nodes; after the
+    black half-sweep at black nodes (each update solves its own row)."""
+    pr = S.problem(9, 11, 13, Lx=1.0, Ly=1.3, Lz=0.9, alpha=0.6, **XI2)
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal((13, 11, 9))
+    f = rng.standard_normal((13, 11, 9))
+    K, J, I = np.meshgrid(np.arange(13), np.arange(11), np.arange(9), indexing="ij")
+    interior = (I > 0) & (I < 8) & (J > 0) & (J < 10) & (K > 0) & (K < 12)
+    red = interior & ((I + J + K) % 2 == 0)
+    black = interior & ((I + J + K) % 2 == 1)
+    u1 = oracle.rbgs3d_colour(pr, u, f, 0)
+    r1 = oracle.residual3d(pr, u1, f)
+    assert np.abs(r1[red]).max() < 1e-10 * np.abs(f).max() * 400
+    assert np.abs(r1[black]).max() > 1e-3
+    u2 = oracle.rbgs3d_colour(pr, u1, f, 1)
+    r2 = oracle.residual3d(pr, u2, f)
+    assert np.abs(r2[black]).max() < 1e-10 * np.abs(f).max() * 400
+    # a full sweep is the two colour passes in order
+    assert np.array_equal(oracle.rbgs3d(pr, u, f, 1), u2)
+    # boundary entries are never touched
+    assert np.array_equal(u2[~interior], u[~interior])
+
+
+def test_gauss_seidel_converges_to_direct_solution():
+    pr = S.problem(9, 9, 9, alpha=0.5, **XI1)
+    bz = S.magnetogram_random(9, 9, seed=4)
+    P0 = exact.separable_solve2d(pr, bz)
+    u = np.zeros((9, 9, 9)); u[0] = P0
+    u = oracle.rbgs3d(pr, u, None, 400)
+    assert np.abs(u - exact.separable_solve3d(pr, P0)).max() < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(9, 17, 9), (17, 9)])
+def test_restriction_is_scaled_adjoint_of_prolongation(shape):
+    """Full weighting R and (bi/tri)linear interpolation I satisfy
+    <R r, e>_coarse = 2^-d <r, I e>_fine for r vanishing on the fine boundary
+    and e vanishing on the coarse boundary."""
+    d = len(shape)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(shape)
+    inner = tuple(slice(1, -1) for _ in shape)
+    mask = np.zeros(shape, bool); mask[inner] = True
+    r[~mask] = 0.0
+    cs = oracle.coarse_shape(shape)
+    e = rng.standard_normal(cs)
+    cmask = np.zeros(cs, bool); cmask[tuple(slice(1, -1) for _ in cs)] = True
+    e[~cmask] = 0.0
+    Rr = oracle.restrict(r)
+    Ie = oracle.prolong_add(e, np.zeros(shape))
+    assert abs(np.sum(Rr * e) - 2.0**-d * np.sum(r * Ie)) < 1e-12 * np.sum(np.abs(r)) * np.abs(e).max()
+
+
+def test_transfer_operators_reproduce_linear_functions():
+    shape = (9, 13, 17)
+    cs = oracle.coarse_shape(shape)
+    kf, jf, if_ = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    kc, jc, ic = np.meshgrid(*[np.arange(n, dtype=float) for n in cs], indexing="ij")
+    lin_f = 0.3 + 0.2 * if_ - 0.7 * jf + 1.1 * kf
+    lin_c = 0.3 + 0.4 * ic - 1.4 * jc + 2.2 * kc     # same function in coarse index units
+    Ie = oracle.prolong_add(lin_c, np.zeros(shape))
+    assert np.allclose(Ie[1:-1, 1:-1, 1:-1], lin_f[1:-1, 1:-1, 1:-1], atol=1e-12)
+    Rr = oracle.restrict(lin_f)
+    assert np.allclose(Rr[1:-1, 1:-1, 1:-1], lin_c[1:-1, 1:-1, 1:-1], atol=1e-12)
+    assert np.all(Rr[0] == 0) and np.all(Rr[:, :, -1] == 0)
+
+
+# ---------------------------------------------------------------------------
+# Background atmosphere (Sect. 3) and field recovery (Sect. 2.2)
+# ---------------------------------------------------------------------------
+
+def test_background_pressure_matches_hydrostatic_ode():
+    """p_b from its piecewise closed form against a numerical integration of
+    dp_b/dz = -g p_b / T_b with the paper's T_b (T_cor = 150, transition 5..10)."""
+    from scipy.integrate import solve_ivp
+    pr = S.problem(3, 3, 241, Lz=24.0, g=1.3)
+    prof = oracle.profiles(pr)
+    z = S.node_coords(241, 24.0)
+
+    def T(zz):
+        if zz <= 5: return 1.0
+        if zz <= 10: return 150.0 ** ((zz - 5) / 5)
+        return 150.0
+
+    sol = solve_ivp(lambda zz, p: [-1.3 * p[0] / T(zz)], (0, 24), [1.0], t_eval=z, rtol=1e-11, atol=1e-14,
+                    max_step=0.05)
+    assert np.allclose(prof["pb"], sol.y[0], rtol=1e-8, atol=0)
+    assert np.allclose(prof["Tb"], [T(v) for v in z])
+    assert np.allclose(prof["rhob"], prof["pb"] / prof["Tb"], rtol=1e-15)
+
+
+def test_force_free_fields_are_background():
+    """xi = 0 (force-free case of Sect. 3.1): p = p_b and rho = rho_b exactly."""
+    pr = S.problem(17, 17, 17, Lx=2.0, Ly=2.0, Lz=12.0, alpha=0.4)
+    bz = S.magnetogram_random(17, 17, 2.0, 2.0, seed=9)
+    P, _ = oracle.solve(pr, bz, 1e-12, 1e-12)
+    F = oracle.fields(pr, P)
+    prof = oracle.profiles(pr)
+    assert np.array_equal(F["p"], np.broadcast_to(prof["pb"][:, None, None], F["p"].shape))
+    assert np.array_equal(F["rho"], np.broadcast_to(prof["rhob"][:, None, None], F["rho"].shape))
+
+
+def _analytic_fields(n, alpha=0.6):
+    """Oracle fields of a closed-form P against the symbolic B, p, rho."""
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    a, kap, mu0, g = 0.7, 0.2, 0.5, 1.0
+    xi = a * sp.exp(-kap * z)
+    P = sp.sin(sp.pi * x) * sp.cos(2 * y) * sp.exp(-z) * (1 + z * z)
+    Bx = alpha * sp.diff(P, y) + sp.diff(P, x, z)
+    By = -alpha * sp.diff(P, x) + sp.diff(P, y, z)
+    Bz = -(sp.diff(P, x, 2) + sp.diff(P, y, 2))
+    pb = sp.exp(-g * z)    # isothermal region z <= 5
+    p = pb - xi * Bz**2 / (2 * mu0)
+    BgradBz = Bx * sp.diff(Bz, x) + By * sp.diff(Bz, y) + Bz * sp.diff(Bz, z)
+    rho = pb + (sp.diff(xi, z) * Bz**2 / (2 * mu0) + xi * BgradBz / mu0) / g
+    pr = S.problem(n, n, n, Lx=1.0, Ly=1.2, Lz=1.5, alpha=alpha, xi_kind=1, xi_a=a, xi_kappa=kap, mu0=mu0, g=g)
+    Z, Y, X = _grid(pr)
+    Pn = sp.lambdify((x, y, z), P, "numpy")(X, Y, Z)
+    F = oracle.fields(pr, Pn)
+    errs = {}
+    for name, expr in [("Bx", Bx), ("By", By), ("Bz", Bz), ("p", p), ("rho", rho)]:
+        ex = sp.lambdify((x, y, z), expr, "numpy")(X, Y, Z) * np.ones_like(X)
+        errs[name] = (np.abs(F[name] - ex).max(), np.abs(F[name] - ex)[2:-2, 2:-2, 2:-2].max())
+    return errs
+
+
+def test_fields_of_closed_form_potential_converge_second_order():
+    """B_x = alpha P_y + P_xz, B_y = -alpha P_x + P_yz, B_z = -(P_xx + P_yy),
+    eq. (pressure) and eq. (density) against their symbolic values: second
+    order inside (two nodes from the faces), at least first order at the faces
+    where one-sided differences of differences meet."""
+    e = [_analytic_fields(n) for n in (33, 65, 129)]
+    for name in ["Bx", "By", "Bz", "p", "rho"]:
+        inner = [e[i][name][1] for i in range(3)]
+        whole = [e[i][name][0] for i in range(3)]
+        r_in = [inner[i] / inner[i + 1] for i in range(2)]
+        r_all = [whole[i] / whole[i + 1] for i in range(2)]
+        assert all(3.5 < r < 4.6 for r in r_in), (name, inner, r_in)
+        assert all(r > 1.8 for r in r_all), (name, whole, r_all)
+
+
+def _div_B(pr, F):
+    hx, hy, hz = pr["Lx"] / (pr["nx"] - 1), pr["Ly"] / (pr["ny"] - 1), pr["Lz"] / (pr["nz"] - 1)
+    return (np.gradient(F["Bx"], hx, axis=2, edge_order=2) + np.gradient(F["By"], hy, axis=1, edge_order=2)
+            + np.gradient(F["Bz"], hz, axis=0, edge_order=2))
+
+
+def test_div_B_mimetic_vanishes_and_compact_is_second_order():
+    """With B_z = -(D_x D_x + D_y D_y) P the central/one-sided first differences
+    commute, so D . B vanishes to rounding (eq. mhs3); the compact B_z of
+    eq. (lower_bound) gives an O(h^2) divergence."""
+    errs = []
+    for n in (17, 33, 65):
+        pr = S.problem(n, n, n, alpha=0.5, **XI1)
+        bz = S.magnetogram_mode(n, n, 1.0, 1.0, 1, 1)
+        P, _ = oracle.solve(pr, bz, 1e-13, 1e-13)
+        Fm = oracle.fields(pr, P, bz_mode=1)
+        scale = np.abs(Fm["Bz"]).max() / (1.0 / (n - 1))
+        assert np.abs(_div_B(pr, Fm)).max() < 1e-10 * scale
+        Fc = oracle.fields(pr, P, bz_mode=0)
+        errs.append(np.abs(_div_B(pr, Fc))[2:-2, 2:-2, 2:-2].max())
+    assert 3.0 < errs[0] / errs[1] and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def _force_residual(pr, F):
+    """mu0^-1 (curl B) x B - grad p - rho g e_z (eq. mhs1) by numpy second-order differences."""
+    hx, hy, hz = pr["Lx"] / (pr["nx"] - 1), pr["Ly"] / (pr["ny"] - 1), pr["Lz"] / (pr["nz"] - 1)
+    d = lambda f, ax, h: np.gradient(f, h, axis=ax, edge_order=2)
+    Bx, By, Bz = F["Bx"], F["By"], F["Bz"]
+    jx = d(Bz, 1, hy) - d(By, 0, hz)
+    jy = d(Bx, 0, hz) - d(Bz, 2, hx)
+    jz = d(By, 2, hx) - d(Bx, 1, hy)
+    mu0, g = pr["mu0"], pr["g"]
+    fx = (jy * Bz - jz * By) / mu0 - d(F["p"], 2, hx)
+    fy = (jz * Bx - jx * Bz) / mu0 - d(F["p"], 1, hy)
+    fz = (jx * By - jy * Bx) / mu0 - d(F["p"], 0, hz) - F["rho"] * g
+    return np.sqrt(fx**2 + fy**2 + fz**2)
+
+
+def test_force_balance_residual_second_order():
+    """The recovered B, p, rho satisfy the MHS force balance eq. (mhs1) up to
+    the discretisation error, which falls as h^2 at fixed interior points."""
+    res = []
+    for n in (17, 33, 65):
+        pr = S.problem(n, n, n, alpha=0.5, **XI1)
+        bz = S.magnetogram_mode(n, n, 1.0, 1.0, 1, 1)
+        P, _ = oracle.solve(pr, bz, 1e-13, 1e-13)
+        F = oracle.fields(pr, P)
+        fr = _force_residual(pr, F)
+        s = (n - 1) // 16      # stride to the common 17^3 nodes
+        res.append(fr[::s, ::s, ::s][3:-3, 3:-3, 3:-3].max())
+    assert 3.3 < res[0] / res[1] < 4.7 and 3.5 < res[1] / res[2] < 4.5, res
