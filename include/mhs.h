@@ -1,0 +1,249 @@
+/*
+ * mhs.h -- C ABI of libmhs, a single-GPU (GB300, sm_103a) multigrid solver
+ * for linear magnetohydrostatic (MHS) equilibria in the poloidal/toroidal
+ * representation used by MacTaggart, Elsheikh, McLaughlin & Simitev,
+ * "Non-symmetric magnetohydrostatic equilibria: a multigrid approach".
+ *
+ * The method (Sect. 2):
+ *   1. P = 0 everywhere (Sect. 2.2, step 1);
+ *   2. multigrid solve of eq. (lower_bound), P_xx + P_yy = -B_z on z = 0 with
+ *      P = 0 on the edges of that plane (Sect. 2.2, step 2);
+ *   3. multigrid solve of eq. (scalar_pot),
+ *      [1 - xi(z)](P_xx + P_yy) + P_zz + alpha^2 P = 0, in the interior with
+ *      P from step 2 on z = 0 and P = 0 on the top and side faces
+ *      (Sect. 2.2, step 3; elliptic for xi < 1, Sect. 2.1);
+ *   4. B = curl[curl(P e_z) + alpha P e_z] (eqs. b_iden, t):
+ *      B_x = alpha P_y + P_xz, B_y = -alpha P_x + P_yz, B_z = -(P_xx + P_yy),
+ *      by second-order finite differences (Sect. 2.2);
+ *   5. p = p_b(z) - xi B_z^2/(2 mu0)                         (eq. pressure)
+ *      rho = rho_b(z) + [xi' B_z^2/(2 mu0) + xi B.grad(B_z)/mu0]/g  (eq. density)
+ *      with the background atmosphere of Sect. 3.
+ *
+ * Grid: nx*ny*nz vertex-centred nodes on [0,Lx] x [0,Ly] x [0,Lz] (z = 0 is
+ * the photosphere), node (i,j,k) at (i Lx/(nx-1), j Ly/(ny-1), k Lz/(nz-1)).
+ * Every array crossing this interface is a dense double array in
+ * [nz][ny][nx] order (x fastest): element (i,j,k) at i + nx*(j + ny*k);
+ * 2D arrays are [ny][nx].  A pointer may be a host pointer (pageable or
+ * pinned) or a CUDA device pointer; the library detects which.  The caller
+ * owns every buffer it passes; the library copies in and out and keeps no
+ * pointer after the call returns.
+ *
+ * Errors: every call returns an mhs_status; no C++ exception crosses the
+ * interface; a failed call leaves the handle usable (except after
+ * MHS_ERR_CUDA caused by a sticky device fault).  mhs_last_error() returns a
+ * thread-local message describing the last failure on the calling thread.
+ *
+ * Streams: all device work of a handle is ordered on its stream (default:
+ * the legacy default stream).  Calls that return results to host memory
+ * synchronise that stream before they return.  A handle must not be used by
+ * two threads at once.
+ */
+#ifndef MHS_H
+#define MHS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MHS_API __attribute__((visibility("default")))
+#else
+#define MHS_API
+#endif
+
+typedef struct mhs_ctx* mhs_handle;
+
+typedef enum {
+    MHS_OK = 0,
+    MHS_ERR_INVALID_ARG = 1,     /* a size, length, pointer or option is out of range */
+    MHS_ERR_NOT_ELLIPTIC = 2,    /* xi(z_k) >= 1 on an interior plane (Sect. 2.1), or alpha^2 not below
+                                    the smallest eigenvalue bound of the discrete operator */
+    MHS_ERR_OUT_OF_MEMORY = 3,   /* device or host allocation failed */
+    MHS_ERR_CUDA = 4,            /* a CUDA runtime call failed; see mhs_last_error() */
+    MHS_ERR_NO_CONVERGENCE = 5,  /* the residual did not reach the tolerance within the cycle limit */
+    MHS_ERR_NONFINITE = 6,       /* B_z holds NaN/Inf, or a residual norm became non-finite */
+    MHS_ERR_BAD_STATE = 7,       /* call order violated (solve before set_lower_bz, fields before solve) */
+    MHS_ERR_TIMEOUT = 8,         /* a bounded wait expired */
+    MHS_ERR_REJECTED = 9         /* a request exceeds the server's device-memory budget */
+} mhs_status;
+
+/* Height profile xi(z) of the cross-field current, F = xi(z) B_z / g
+ * (Sect. 2.1, after eq. helm).  The families are those of Sect. 3.2. */
+typedef enum {
+    MHS_XI_NONE = 0,     /* xi = 0: linear force-free field (Sect. 3.1) */
+    MHS_XI_EXP = 1,      /* xi = a exp(-kappa z)                 (xi_1 family) */
+    MHS_XI_EXP_SIN = 2   /* xi = (a + b sin(omega z)) exp(-kappa z) (xi_2 family) */
+} mhs_xi_kind;
+
+typedef struct {
+    int kind;            /* mhs_xi_kind */
+    double a, kappa, b, omega;
+} mhs_xi_params;
+
+/* Background atmosphere (Sect. 3): T_b = 1 for z <= z1,
+ * T_cor^((z - z1)/(z2 - z1)) for z1 < z <= z2, T_cor above; p_b = rho_b T_b;
+ * dp_b/dz = -g p_b / T_b with p_b(0) = 1.  mu0 is the permeability in code
+ * units (1/2 when B is measured in B0 = (2 mu0 p0)^(1/2) and p in p0). */
+typedef struct {
+    double g, mu0, T_cor, z1, z2;
+} mhs_atmos_params;
+
+typedef enum {
+    MHS_FP64 = 0,        /* every multigrid operation in FP64 */
+    MHS_MIXED = 1        /* FP64 residual and update around FP32 V-cycles (defect correction) */
+} mhs_precision;
+
+/* Solver options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+    int nu1;             /* pre-smoothing red-black sweeps per level [2] */
+    int nu2;             /* post-smoothing sweeps [2] */
+    int max_cycles;      /* V-cycles (FP64 mode) or outer steps (mixed mode) per solve [100] */
+    int inner_cycles;    /* FP32 V-cycles per outer step in mixed mode [1] */
+    int flags;           /* MHS_FLAG_* bits */
+} mhs_solver_opts;
+
+#define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
+#define MHS_FLAG_BZ_MIMETIC 2   /* B_z = -(D_x D_x + D_y D_y) P with the first-difference operators,
+                                   which makes the central-difference div B vanish to rounding */
+
+typedef struct {
+    int cycles_2d;       /* V-cycles (or outer steps) of the lower-boundary solve */
+    int cycles_3d;       /* V-cycles (or outer steps) of the interior solve */
+    double rel_res_2d;   /* final ||b - A P||_2 / ||b||_2 of eq. (lower_bound) */
+    double rel_res_3d;   /* same for eq. (scalar_pot), b = right-hand side after lifting the z = 0 data */
+    double conv_factor;  /* geometric-mean residual reduction per interior cycle */
+    double ms;           /* device time of the solve (CUDA events on the handle's stream) */
+} mhs_solve_info;
+
+/* Create a solver for an nx*ny*nz node grid on [0,Lx]x[0,Ly]x[0,Lz].
+ * Each n must be odd, >= 5 and <= 16385 (nx, ny <= 4097); multigrid coarsens all three axes together
+ * while every axis stays odd and >= 3 nodes, so n = 2^k m + 1 with small m
+ * gives the deepest hierarchy.  Lengths must be > 0; xi == NULL means
+ * xi = 0; atm == NULL means g = 1, mu0 = 1/2, T_cor = 150, z1 = 5, z2 = 10.
+ * Allocates the whole device hierarchy (owned by the handle) and computes
+ * the per-plane coefficients on the device.
+ * Errors: MHS_ERR_INVALID_ARG, MHS_ERR_NOT_ELLIPTIC (xi(z_k) >= 1 on an
+ * interior plane, Sect. 2.1), MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_create(int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                      const mhs_xi_params* xi, const mhs_atmos_params* atm, mhs_handle* out);
+
+/* Release every device and host resource of h (NULL is accepted). */
+MHS_API void mhs_destroy(mhs_handle h);
+
+/* Order all later device work of h on stream (a cudaStream_t; NULL = legacy default stream). */
+MHS_API mhs_status mhs_set_stream(mhs_handle h, void* stream);
+
+/* Replace the solver options (NULL restores the defaults). */
+MHS_API mhs_status mhs_set_options(mhs_handle h, const mhs_solver_opts* opts);
+
+/* Change alpha and the xi profile of an existing handle (same grid); the
+ * per-plane coefficients are recomputed on the device.  Same errors as
+ * mhs_create for these arguments. */
+MHS_API mhs_status mhs_set_params(mhs_handle h, double alpha, const mhs_xi_params* xi, const mhs_atmos_params* atm);
+
+/* Prescribe the normal field B_z on z = 0 (Sect. 2.2, eq. lower_bound):
+ * bz is [ny][nx] doubles, host or device.  Only interior nodes enter the
+ * lower-boundary equation.  Errors: MHS_ERR_INVALID_ARG (NULL),
+ * MHS_ERR_NONFINITE (a NaN/Inf among the interior values), MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_set_lower_bz(mhs_handle h, const double* bz);
+
+/* Steps 1-3 of Sect. 2.2: the lower-boundary and interior multigrid solves,
+ * each until its relative residual ||b - A P||_2/||b||_2 falls below tol
+ * (tol in (0, 1)).  mode is an mhs_precision.  info may be NULL.
+ * Errors: MHS_ERR_BAD_STATE (no B_z yet), MHS_ERR_INVALID_ARG,
+ * MHS_ERR_NO_CONVERGENCE (P is still the last iterate and usable),
+ * MHS_ERR_NONFINITE, MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info* info);
+
+/* Copy P (the poloidal potential of eq. b_iden), [nz][ny][nx], to phi (host
+ * or device).  Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_INVALID_ARG. */
+MHS_API mhs_status mhs_get_phi(mhs_handle h, double* phi);
+
+/* Steps 4-5 (Sect. 2.2, eqs. b_iden, t, pressure, density): B_x, B_y, B_z,
+ * p and rho on every node, each [nz][ny][nx] (host or device; any may be
+ * NULL to skip it).  Central differences inside, second-order one-sided
+ * differences on the first and last node of each axis.
+ * Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_fields(mhs_handle h, double* Bx, double* By, double* Bz, double* p, double* rho);
+
+/* Number of multigrid levels of the interior (dim = 3) or lower-boundary
+ * (dim = 2) hierarchy, and the node counts of one level (level 0 finest). */
+MHS_API mhs_status mhs_num_levels(mhs_handle h, int dim, int* nlevels);
+MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, int* ny, int* nz);
+
+/* Level-access hooks for operation-by-operation parity tests.  They expose
+ * the very kernels the solver runs, on one level of the resident hierarchy.
+ *   field: MHS_FIELD_U (iterate / correction), MHS_FIELD_F (right-hand side),
+ *          MHS_FIELD_R (residual)
+ *   prec:  MHS_FP64 or MHS_MIXED (the FP32 copy)
+ * Arrays are dense doubles of the level's shape (converted to/from FP32 for
+ * prec = MHS_MIXED), host or device.
+ * Operations (op):
+ *   MHS_OP_SMOOTH:   one red-black Gauss-Seidel sweep on u (colour (i+j+k)
+ *                    even first, then odd) for A u = f                 (Sect. 4)
+ *   MHS_OP_RESIDUAL: r = f - A u on interior nodes                      (Sect. 4)
+ *   MHS_OP_RESTRICT: f[level+1] = full-weighting restriction of r[level] (Sect. 4)
+ *   MHS_OP_PROLONG:  u[level] += (bi/tri)linear interpolation of u[level+1] (Sect. 4)
+ *   MHS_OP_COARSE:   coarsest-level solve of A u = f (u from 0)
+ *   MHS_OP_VCYCLE:   one V(nu1,nu2)-cycle on A u = f from level down
+ * For the finest interior level, A includes the Dirichlet data held in u's
+ * boundary entries.  Errors: MHS_ERR_INVALID_ARG, MHS_ERR_CUDA. */
+#define MHS_FIELD_U 0
+#define MHS_FIELD_F 1
+#define MHS_FIELD_R 2
+#define MHS_OP_SMOOTH 0
+#define MHS_OP_RESIDUAL 1
+#define MHS_OP_RESTRICT 2
+#define MHS_OP_PROLONG 3
+#define MHS_OP_COARSE 4
+#define MHS_OP_VCYCLE 5
+MHS_API mhs_status mhs_level_write(mhs_handle h, int dim, int level, int field, int prec, const double* src);
+MHS_API mhs_status mhs_level_read(mhs_handle h, int dim, int level, int field, int prec, double* dst);
+MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec);
+
+/* Per-operation device timing (CUDA events on the handle's stream), off by
+ * default.  While enabled, every multigrid operation and field kernel of
+ * the handle is bracketed by two events; mhs_kernel_timing() synchronises
+ * the stream and returns, for one operation kind, the summed duration, the
+ * number of timed launches and the algorithmic bytes and flops of those
+ * launches (minimal traffic of the operation: each input read once, each
+ * output written once).  Kinds are MHS_KT_*; mhs_kernel_timing_reset()
+ * clears the totals. */
+#define MHS_KT_SMOOTH64 0      /* red-black sweep, FP64 */
+#define MHS_KT_SMOOTH32 1      /* red-black sweep, FP32 */
+#define MHS_KT_RESID64 2       /* residual (+ norm partials), FP64 */
+#define MHS_KT_RESID32 3       /* residual, FP32 */
+#define MHS_KT_RESTRICT64 4
+#define MHS_KT_RESTRICT32 5
+#define MHS_KT_PROLONG64 6
+#define MHS_KT_PROLONG32 7
+#define MHS_KT_COARSE64 8
+#define MHS_KT_COARSE32 9
+#define MHS_KT_RESID_MIXED 10  /* FP64 residual rounded to the FP32 right-hand side */
+#define MHS_KT_CORRECT 11      /* P64 += e32 */
+#define MHS_KT_FIELDS 12       /* B, p, rho */
+#define MHS_KT_OTHER 13        /* set-up, copies, norms of the right-hand side */
+#define MHS_KT_COUNT 14
+MHS_API mhs_status mhs_set_kernel_timing(mhs_handle h, int enable);
+MHS_API mhs_status mhs_kernel_timing(mhs_handle h, int kind, double* total_ms, long long* launches,
+                                     double* alg_bytes, double* alg_flops);
+MHS_API mhs_status mhs_kernel_timing_reset(mhs_handle h);
+MHS_API const char* mhs_kernel_kind_name(int kind);
+
+/* Human-readable name of a status code (static storage). */
+MHS_API const char* mhs_status_string(mhs_status s);
+
+/* Thread-local description of the last failure on the calling thread
+ * (empty string if none).  Valid until the next failing call on that thread. */
+MHS_API const char* mhs_last_error(void);
+
+/* Library version string (static storage). */
+MHS_API const char* mhs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHS_H */

@@ -80,6 +80,8 @@ def _load():
                 "orc_solve": (ctypes.c_int, [_PP, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(Info)]),
                 "orc_num_levels": (ctypes.c_int, [_PP, ctypes.c_int]),
+                "orc_vcycle": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                      ctypes.c_int, ctypes.c_int]),
                 "orc_fields": (None, [_PP, _D, _D, _D, _D, _D, _D, ctypes.c_int]),
                 "orc_profiles": (None, [_PP, _D, _D, _D, _D, _D]),
             }
@@ -240,6 +242,19 @@ def solve(pr, bz, tol2d=1e-12, tol3d=1e-12, max_cycles=200, nu1=2, nu2=2):
     return P, dict(status=status, cycles_2d=info.cycles_2d, cycles_3d=info.cycles_3d,
                    rel_res_2d=info.rel_res_2d, rel_res_3d=info.rel_res_3d,
                    conv_factor_3d=info.conv_factor_3d)
+
+
+def vcycle(pr, u, f=None, nu1=2, nu2=2):
+    """One V-cycle on the grid of u (2D [ny][nx] or 3D [nz][ny][nx]); returns the new u."""
+    u = _f64(u).copy(); f = _f64(f)
+    p = _prob(pr)
+    if u.ndim == 2:
+        ny, nx = u.shape
+        _load().orc_vcycle(ctypes.byref(p), 2, nx, ny, 1, _ptr(u), _ptr(f), nu1, nu2)
+    else:
+        nz, ny, nx = u.shape
+        _load().orc_vcycle(ctypes.byref(p), 3, nx, ny, nz, _ptr(u), _ptr(f), nu1, nu2)
+    return u
 
 
 def num_levels(pr, dim=3) -> int:

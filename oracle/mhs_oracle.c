@@ -694,3 +694,19 @@ void orc_profiles(const orc_problem* p, double* xi, double* dxi, double* pb, dou
         if (Tb) Tb[k] = orc_Tb(p, z);
     }
 }
+
+/* One V(nu1,nu2)-cycle for A u = f on the grid of u (dim 3: nx*ny*nz,
+ * dim 2: nx*ny), from that grid down to the coarsest level.  u is updated
+ * in place; its boundary entries are the Dirichlet data. */
+void orc_vcycle(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
+                int nu2) {
+    orc_problem q = with_size(p, nx, ny, dim == 3 ? nz : 1);
+    orc_mg mg;
+    mg_build(&mg, &q, dim);
+    const size_t n = level_size(&mg.L[0]);
+    double* fz = NULL;
+    if (!f) fz = (double*)calloc(n, sizeof(double));
+    vcycle(&mg, 0, u, f ? f : fz, nu1, nu2);
+    free(fz);
+    mg_free(&mg);
+}

@@ -1,0 +1,579 @@
+// Multigrid building blocks for the lower-boundary problem (eq. lower_bound,
+// 5-point stencil) and the interior problem (eq. scalar_pot, 7-point stencil
+// with per-plane coefficients), in FP64 and FP32.
+//
+// The paper parallelises every multigrid stage with one thread per node
+// (Sect. 4: relaxation, residual, restriction and prolongation).  These are
+// the plain per-node kernels of that design, adapted to red-black
+// Gauss-Seidel; the fused, shared-memory-staged fine-level kernels live in
+// kernels_fine.cu.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "mhs_internal.h"
+#include "solver.h"
+
+namespace mhs {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+__device__ __forceinline__ size_t at(const Geom& g, int i, int j, int k) {
+    return size_t(i) + size_t(g.px) * (size_t(j) + size_t(g.ny) * size_t(k));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; every thread of the block must call it.  Result valid in thread 0.
+template <typename T>
+__device__ T block_sum(T v) {
+    __shared__ T ws[32];
+    const int lane = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_sum(v);
+    if ((lane & 31) == 0) ws[lane >> 5] = v;
+    __syncthreads();
+    T s = T(0);
+    if (lane < 32) {
+        s = (lane < (nthreads + 31) / 32) ? ws[lane] : T(0);
+        s = warp_sum(s);
+    }
+    __syncthreads();
+    return s;
+}
+
+// -------------------------------------------------------------------------
+// a1: per-plane coefficients and height profiles (Sect. 2.1, eq. scalar_pot;
+// Sect. 3 background atmosphere and the xi families of Sect. 3.2).
+// -------------------------------------------------------------------------
+
+__device__ double xi_of(const mhs_xi_params& x, double z) {
+    switch (x.kind) {
+    case MHS_XI_EXP: return x.a * exp(-x.kappa * z);
+    case MHS_XI_EXP_SIN: return (x.a + x.b * sin(x.omega * z)) * exp(-x.kappa * z);
+    default: return 0.0;
+    }
+}
+
+__device__ double dxi_of(const mhs_xi_params& x, double z) {
+    switch (x.kind) {
+    case MHS_XI_EXP: return -x.kappa * x.a * exp(-x.kappa * z);
+    case MHS_XI_EXP_SIN:
+        return (x.b * x.omega * cos(x.omega * z) - x.kappa * (x.a + x.b * sin(x.omega * z))) * exp(-x.kappa * z);
+    default: return 0.0;
+    }
+}
+
+template <typename T>
+__global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nz) return;
+    double cx, cy, cz, d;
+    if (dim == 3) {
+        const double om = 1.0 - xi_of(xi, k * g.hz);
+        cx = om / (g.hx * g.hx);
+        cy = om / (g.hy * g.hy);
+        cz = 1.0 / (g.hz * g.hz);
+        d = -2.0 * (cx + cy + cz) + alpha * alpha;
+    } else {
+        cx = 1.0 / (g.hx * g.hx);
+        cy = 1.0 / (g.hy * g.hy);
+        cz = 0.0;
+        d = -2.0 * (cx + cy);
+    }
+    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d)};
+}
+
+// Background atmosphere: T_b piecewise (1, T_cor^((z-z1)/(z2-z1)), T_cor);
+// p_b from dp_b/dz = -g p_b/T_b integrated in closed form per piece
+// (1/T_b is constant or exponential in z); rho_b = p_b / T_b.
+__device__ void background(const mhs_atmos_params& a, double z, double* pb, double* rhob) {
+    const double d = a.z2 - a.z1, lnT = log(a.T_cor);
+    double p, T;
+    if (z <= a.z1) {
+        p = exp(-a.g * z);
+        T = 1.0;
+    } else if (z <= a.z2) {
+        const double s = (z - a.z1) / d;
+        p = exp(-a.g * a.z1) * exp(-a.g * d * (1.0 - pow(a.T_cor, -s)) / lnT);
+        T = pow(a.T_cor, s);
+    } else {
+        const double p2 = exp(-a.g * a.z1) * exp(-a.g * d * (1.0 - 1.0 / a.T_cor) / lnT);
+        p = p2 * exp(-a.g * (z - a.z2) / a.T_cor);
+        T = a.T_cor;
+    }
+    *pb = p;
+    *rhob = p / T;
+}
+
+__global__ void profile_kernel(Geom g, mhs_xi_params xi, mhs_atmos_params atm, double* prof) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nz) return;
+    const double z = k * g.hz;
+    double pb, rb;
+    background(atm, z, &pb, &rb);
+    prof[4 * k + 0] = xi_of(xi, z);
+    prof[4 * k + 1] = dxi_of(xi, z);
+    prof[4 * k + 2] = pb;
+    prof[4 * k + 3] = rb;
+}
+
+template <typename T>
+__global__ void fill_kernel(T* a, size_t n, T v) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) a[i] = v;
+}
+
+// -------------------------------------------------------------------------
+// Red-black Gauss-Seidel colour pass (in place).  Colour c updates the
+// interior nodes with (i + j + k) % 2 == c by solving their own row of
+// A u = f for u_ijk with the current neighbour values.  A thread per node
+// of the colour: thread t of row (j,k) takes i = i0 + 2t.
+// -------------------------------------------------------------------------
+
+template <typename T, bool D3>
+__global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* __restrict__ u,
+                              const T* __restrict__ f, int colour) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (j > g.ny - 2) return;
+    for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
+        const int i = 1 + (((1 + j + k) & 1) != colour) + 2 * t;
+        if (i > g.nx - 2) continue;
+        const PlaneCoef<T> c = coef[k];
+        const size_t o = at(g, i, j, k);
+        T off = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]);
+        if (D3) off += c.cz * (u[o + g.plane] + u[o - g.plane]);
+        const T rhs = f ? f[o] : T(0);
+        u[o] = (rhs - off) * c.inv_d;
+    }
+}
+
+// r = f - A u at interior nodes; per-block partial sums of r^2 (in double)
+// into ns.partial, finished by norm_finish_kernel in fixed order.
+template <typename T, bool D3>
+__global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
+                                const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= g.nx - 2 && j <= g.ny - 2) {
+        for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
+            const PlaneCoef<T> c = coef[k];
+            const size_t o = at(g, i, j, k);
+            T au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
+            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
+            const T rv = (f ? f[o] : T(0)) - au;
+            r[o] = rv;
+            acc += double(rv) * double(rv);
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+}
+
+// Mixed precision: r64 = f - A u in FP64, stored rounded to FP32 (the
+// right-hand side of the FP32 correction equation) plus norm partials.
+template <bool D3>
+__global__ void residual_f32_kernel(Geom g, const PlaneCoef<double>* __restrict__ coef, const double* __restrict__ u,
+                                    const double* __restrict__ f, float* __restrict__ r32, double* __restrict__ partial) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= g.nx - 2 && j <= g.ny - 2) {
+        for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
+            const PlaneCoef<double> c = coef[k];
+            const size_t o = at(g, i, j, k);
+            double au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
+            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
+            const double rv = (f ? f[o] : 0.0) - au;
+            r32[o] = float(rv);
+            acc += rv * rv;
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+}
+
+__global__ void norm_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+    // one block, fixed summation order: thread t sums t, t+blockDim, ...; then a fixed tree
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += partial[b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// Full weighting: tensor product of (1/4, 1/2, 1/4) around the fine node
+// (2I, 2J, 2K) coincident with coarse interior node (I, J, K).
+template <typename T, bool D3>
+__global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc) {
+    const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    for (int K = D3 ? 1 + blockIdx.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gridDim.z) {
+        const size_t o = at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
+        T acc = T(0);
+#pragma unroll
+        for (int c = (D3 ? -1 : 0); c <= (D3 ? 1 : 0); ++c) {
+            const T wc = D3 ? (c == 0 ? T(0.5) : T(0.25)) : T(1);
+            const size_t oc = o + (ptrdiff_t)c * (ptrdiff_t)gf.plane;
+            T s = T(0);
+#pragma unroll
+            for (int b = -1; b <= 1; ++b) {
+                const T wb = (b == 0) ? T(0.5) : T(0.25);
+                const size_t ob = oc + (ptrdiff_t)b * gf.px;
+                s += wb * (T(0.25) * rf[ob - 1] + T(0.5) * rf[ob] + T(0.25) * rf[ob + 1]);
+            }
+            acc += wc * s;
+        }
+        fc[at(gc, I, J, K)] = acc;
+    }
+}
+
+// u_f += I u_c at fine interior nodes: along each axis an even fine index
+// takes coarse node i/2, an odd one the mean of (i-1)/2 and (i+1)/2.
+template <typename T, bool D3>
+__global__ void prolong_kernel(Geom gc, Geom gf, const T* __restrict__ uc, T* __restrict__ uf) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > gf.nx - 2 || j > gf.ny - 2) return;
+    const int I0 = i >> 1, I1 = (i + 1) >> 1;
+    const int J0 = j >> 1, J1 = (j + 1) >> 1;
+    for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? gf.nz - 2 : 0); k += gridDim.z) {
+        const int K0 = k >> 1, K1 = (k + 1) >> 1;
+        auto plane = [&](int K) {
+            const T a = uc[at(gc, I0, J0, K)] + uc[at(gc, I1, J0, K)];
+            const T b = uc[at(gc, I0, J1, K)] + uc[at(gc, I1, J1, K)];
+            return T(0.25) * (a + b);   // (i,j) bilinear with the duplicates of even indices
+        };
+        T v = D3 ? T(0.5) * (plane(K0) + plane(K1)) : plane(0);
+        uf[at(gf, i, j, k)] += v;
+    }
+}
+
+// Coarsest level: one CTA sweeps red-black Gauss-Seidel in shared memory
+// until ||f - A u|| <= tol_rel ||f|| (checked every 4 sweeps) or max_sweeps.
+template <typename T, bool D3>
+__global__ void coarse_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* __restrict__ u_g,
+                              const T* __restrict__ f_g, double tol_rel, int max_sweeps) {
+    extern __shared__ unsigned char smem_raw[];
+    T* u = reinterpret_cast<T*>(smem_raw);
+    T* f = u + g.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (size_t o = tid; o < g.n; o += nt) {
+        u[o] = u_g[o];
+        f[o] = f_g[o];
+    }
+    __syncthreads();
+    const int nxi = g.nx - 2, nyi = g.ny - 2, nzi = D3 ? g.nz - 2 : 1;
+    const int nint = nxi * nyi * nzi;
+    auto node = [&](int q, int& i, int& j, int& k) {
+        i = 1 + q % nxi;
+        j = 1 + (q / nxi) % nyi;
+        k = D3 ? 1 + q / (nxi * nyi) : 0;
+    };
+    auto au_off = [&](int i, int j, int k, const PlaneCoef<T>& c, size_t o) {
+        T off = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]);
+        if (D3) off += c.cz * (u[o + g.plane] + u[o - g.plane]);
+        return off;
+    };
+    double fn = 0.0;
+    for (int q = tid; q < nint; q += nt) {
+        int i, j, k;
+        node(q, i, j, k);
+        const double v = f[at(g, i, j, k)];
+        fn += v * v;
+    }
+    fn = block_sum(fn);
+    __shared__ double s_fn;
+    __shared__ int s_done;
+    if (tid == 0) {
+        s_fn = fn;
+        s_done = (fn == 0.0);
+    }
+    __syncthreads();
+    if (s_done) {
+        for (size_t o = tid; o < g.n; o += nt) u_g[o] = T(0);
+        return;
+    }
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int q = tid; q < nint; q += nt) {
+                int i, j, k;
+                node(q, i, j, k);
+                if (((i + j + k) & 1) != colour) continue;
+                const PlaneCoef<T> c = coef[k];
+                const size_t o = at(g, i, j, k);
+                u[o] = (f[o] - au_off(i, j, k, c, o)) * c.inv_d;
+            }
+            __syncthreads();
+        }
+        if ((sweep & 3) == 3) {
+            double rr = 0.0;
+            for (int q = tid; q < nint; q += nt) {
+                int i, j, k;
+                node(q, i, j, k);
+                const PlaneCoef<T> c = coef[k];
+                const size_t o = at(g, i, j, k);
+                const double rv = double(f[o] - au_off(i, j, k, c, o) - c.d * u[o]);
+                rr += rv * rv;
+            }
+            rr = block_sum(rr);
+            if (tid == 0) s_done = (rr <= tol_rel * tol_rel * s_fn);
+            __syncthreads();
+            if (s_done) break;
+        }
+    }
+    for (size_t o = tid; o < g.n; o += nt) u_g[o] = u[o];
+}
+
+__global__ void lower_rhs_kernel(Geom g, const double* __restrict__ bz, double* __restrict__ f) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const size_t o = at(g, i, j, 0);
+    f[o] = -bz[o];
+}
+
+__global__ void add_correction_kernel(Geom g, int d3, const float* __restrict__ e, double* __restrict__ u) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    for (int k = d3 ? 1 + blockIdx.z : 0; k <= (d3 ? g.nz - 2 : 0); k += gridDim.z) {
+        const size_t o = at(g, i, j, k);
+        u[o] += double(e[o]);
+    }
+}
+
+template <typename T>
+__global__ void zero_interior_kernel(Geom g, int d3, T* __restrict__ u) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    for (int k = d3 ? 1 + blockIdx.z : 0; k <= (d3 ? g.nz - 2 : 0); k += gridDim.z) u[at(g, i, j, k)] = T(0);
+}
+
+__global__ void copy_plane_kernel(Geom g2, const double* __restrict__ src, Geom g3, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g2.nx || j >= g2.ny) return;
+    dst[at(g3, i, j, 0)] = src[at(g2, i, j, 0)];
+}
+
+__global__ void nonfinite_kernel(Geom g, const double* __restrict__ bz, int* flag) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    if (!isfinite(bz[at(g, i, j, 0)])) atomicExch(flag, 1);
+}
+
+// ||b||^2 of the lifted interior right-hand side: the Dirichlet data on
+// k = 0 enters row (i,j,1) as cz * P(i,j,0).
+__global__ void lift_norm_kernel(Geom g, const PlaneCoef<double>* __restrict__ coef, const double* __restrict__ u,
+                                 double* __restrict__ partial) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= g.nx - 2 && j <= g.ny - 2) {
+        const double v = coef[1].cz * u[at(g, i, j, 0)];
+        acc = v * v;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+dim3 grid_for(const Geom& g, int d3, int xcount, int max_blocks) {
+    const int gx = (xcount + BX - 1) / BX;
+    const int gy = (g.ny - 2 + BY - 1) / BY;
+    int gz = 1;
+    if (d3) {
+        gz = g.nz - 2;
+        const int cap = max_blocks > 0 ? max_blocks / (gx * gy) : 65535;
+        if (gz > cap) gz = cap > 0 ? cap : 1;
+        if (gz > 65535) gz = 65535;
+    }
+    return dim3(gx, gy, gz);
+}
+
+void finish_norm(NormScratch* ns, int nblocks, int slot, cudaStream_t st) {
+    norm_finish_kernel<<<1, 1024, 0, st>>>(ns->partial, nblocks, ns->result + slot);
+    MHS_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// ------------------------------- launchers -------------------------------
+
+template <typename T>
+void launch_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, PlaneCoef<T>* coef,
+                 cudaStream_t st) {
+    coef_kernel<T><<<(g.nz + 127) / 128, 128, 0, st>>>(g, dim, alpha, xi, coef);
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_profiles(const Geom& g, const mhs_xi_params& xi, const mhs_atmos_params& atm, double* prof,
+                     cudaStream_t st) {
+    profile_kernel<<<(g.nz + 127) / 128, 128, 0, st>>>(g, xi, atm, prof);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_fill(T* a, size_t n, T v, cudaStream_t st) {
+    if (n == 0) return;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    fill_kernel<T><<<unsigned(blocks), 256, 0, st>>>(a, n, v);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const int halfx = (g.nx - 2 + 1) / 2;
+    const dim3 grid = grid_for(g, d3, halfx, 0);
+    for (int colour = 0; colour < 2; ++colour) {
+        if (d3) colour_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+        else colour_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+    }
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
+                     NormScratch* ns, int slot, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(g, d3, g.nx - 2, ns->max_blocks);
+    if (d3) residual_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, ns->partial);
+    else residual_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, ns->partial);
+    MHS_CUDA(cudaGetLastError());
+    finish_norm(ns, grid.x * grid.y * grid.z, slot, st);
+}
+
+void launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
+                            const double* f, float* r32, NormScratch* ns, int slot, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(g, d3, g.nx - 2, ns->max_blocks);
+    if (d3) residual_f32_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, ns->partial);
+    else residual_f32_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, ns->partial);
+    MHS_CUDA(cudaGetLastError());
+    finish_norm(ns, grid.x * grid.y * grid.z, slot, st);
+}
+
+template <typename T>
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(gc, d3, gc.nx - 2, 0);
+    if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc);
+    else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(gf, d3, gf.nx - 2, 0);
+    if (d3) prolong_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
+    else prolong_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st) {
+    const size_t smem = 2 * g.n * sizeof(T);
+    const double tol = sizeof(T) == 8 ? 1e-13 : 1e-6;
+    const int max_sweeps = 4000;
+    if (dim == 3) {
+        MHS_CUDA(cudaFuncSetAttribute(coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        coarse_kernel<T, true><<<1, 512, smem, st>>>(g, coef, u, f, tol, max_sweeps);
+    } else {
+        MHS_CUDA(cudaFuncSetAttribute(coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        coarse_kernel<T, false><<<1, 512, smem, st>>>(g, coef, u, f, tol, max_sweeps);
+    }
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st) {
+    const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
+    lower_rhs_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, f64);
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(g, d3, g.nx - 2, 0);
+    add_correction_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, d3, e, u);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(g, d3, g.nx - 2, 0);
+    zero_interior_kernel<T><<<grid, dim3(BX, BY), 0, st>>>(g, d3, u);
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st) {
+    const dim3 grid((g2.nx + BX - 1) / BX, (g2.ny + BY - 1) / BY);
+    copy_plane_kernel<<<grid, dim3(BX, BY), 0, st>>>(g2, src2d, g3, dst3d);
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st) {
+    const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
+    nonfinite_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, flag);
+    MHS_CUDA(cudaGetLastError());
+}
+
+void launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, NormScratch* ns, int slot,
+                      cudaStream_t st) {
+    const dim3 grid((g3.nx - 2 + BX - 1) / BX, (g3.ny - 2 + BY - 1) / BY);
+    lift_norm_kernel<<<grid, dim3(BX, BY), 0, st>>>(g3, coef, u, ns->partial);
+    MHS_CUDA(cudaGetLastError());
+    finish_norm(ns, grid.x * grid.y, slot, st);
+}
+
+#define MHS_INST(T)                                                                                          \
+    template void launch_coef<T>(const Geom&, int, double, const mhs_xi_params&, PlaneCoef<T>*, cudaStream_t); \
+    template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                                 \
+    template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
+    template void launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*,            \
+                                     NormScratch*, int, cudaStream_t);                                         \
+    template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);               \
+    template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \
+    template void launch_coarse<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
+    template void launch_zero_interior<T>(const Geom&, int, T*, cudaStream_t);
+MHS_INST(double)
+MHS_INST(float)
+#undef MHS_INST
+
+}  // namespace mhs
+
+namespace mhs {
+namespace {
+__global__ void d2f_kernel(const double* __restrict__ s, float* __restrict__ d, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        d[i] = float(s[i]);
+}
+__global__ void f2d_kernel(const float* __restrict__ s, double* __restrict__ d, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        d[i] = double(s[i]);
+}
+}  // namespace
+void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st) {
+    d2f_kernel<<<152 * 8, 256, 0, st>>>(src, dst, n);
+    MHS_CUDA(cudaGetLastError());
+}
+void launch_f2d(const float* src, double* dst, size_t n, cudaStream_t st) {
+    f2d_kernel<<<152 * 8, 256, 0, st>>>(src, dst, n);
+    MHS_CUDA(cudaGetLastError());
+}
+}  // namespace mhs

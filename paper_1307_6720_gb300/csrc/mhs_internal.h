@@ -1,0 +1,173 @@
+// Internal declarations of libmhs (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mhs.h"
+
+namespace mhs {
+
+// Error carrying an mhs_status across internal C++ layers; caught at the ABI.
+struct Error : std::runtime_error {
+    mhs_status status;
+    Error(mhs_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+void cuda_check(cudaError_t e, const char* what, const char* file, int line);
+#define MHS_CUDA(call) ::mhs::cuda_check((call), #call, __FILE__, __LINE__)
+
+inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// Per-plane coefficients of the interior operator of eq. (scalar_pot) on one
+// level: (A u)_ijk = cx_k (u_E + u_W) + cy_k (u_N + u_S) + cz (u_U + u_D) + d_k u_ijk,
+// cx_k = (1 - xi(z_k))/hx^2, cy_k = (1 - xi(z_k))/hy^2, cz = 1/hz^2,
+// d_k = -2 (cx_k + cy_k + cz) + alpha^2; inv_d = 1/d_k.
+// For the lower-boundary operator of eq. (lower_bound): one plane with
+// xi = 0, cz = 0, alpha = 0.
+template <typename T>
+struct PlaneCoef {
+    T cx, cy, cz, d, inv_d;
+};
+
+// Geometry of one level.  Device arrays are pitched: element (i,j,k) at
+// i + px*(j + ny*k) with px = nx rounded up to a multiple of 4 elements, so
+// every row starts on a 16-byte boundary for float and 32 bytes for double.
+struct Geom {
+    int nx = 0, ny = 0, nz = 0;   // nz = 1 for the lower-boundary plane
+    int px = 0;                   // row pitch in elements
+    size_t plane = 0;             // px * ny
+    size_t n = 0;                 // plane * nz (allocated elements)
+    double hx = 0, hy = 0, hz = 0;
+    size_t interior() const { return size_t(nx - 2) * (ny - 2) * (nz > 1 ? nz - 2 : 1); }
+};
+
+Geom make_geom(int nx, int ny, int nz, double Lx, double Ly, double Lz);
+
+// Arrays of one level for one precision.
+template <typename T>
+struct LevelArrays {
+    T* u = nullptr;               // iterate (finest interior level: P, with Dirichlet data on the boundary)
+    T* f = nullptr;               // right-hand side
+    T* r = nullptr;               // residual
+    PlaneCoef<T>* coef = nullptr; // nz entries (device)
+};
+
+struct Hierarchy {
+    int dim = 3;                          // 3: interior, 2: lower boundary plane
+    std::vector<Geom> g;                  // level geometries, 0 = finest
+    std::vector<LevelArrays<double>> d;   // FP64 arrays
+    std::vector<LevelArrays<float>> s;    // FP32 arrays
+    int nlev() const { return int(g.size()); }
+};
+
+// Device scratch for norms: per-block partial sums and the final values.
+struct NormScratch {
+    double* partial = nullptr;   // max_blocks entries
+    double* result = nullptr;    // a few doubles (norm^2 slots)
+    double* host = nullptr;      // pinned mirror of result
+    int max_blocks = 0;
+};
+
+// Optional per-operation device timing with CUDA events on the handle's
+// stream (off by default; enabled through mhs_set_kernel_timing).  Each
+// timed operation adds its algorithmic bytes and flops so that achieved
+// bandwidth and arithmetic rates can be formed from measured durations.
+struct KernelTimer {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;   // 2 events per record
+    std::vector<int> kind;           // operation kind per record
+    std::vector<double> bytes, flops;
+    size_t used = 0;
+    double ms[MHS_KT_COUNT] = {};
+    long long count[MHS_KT_COUNT] = {};
+    double alg_bytes[MHS_KT_COUNT] = {};
+    double alg_flops[MHS_KT_COUNT] = {};
+
+    // start a record; returns its index or -1 when disabled
+    int begin(int k, double b, double f, cudaStream_t st);
+    void end(int rec, cudaStream_t st);
+    void collect();   // synchronises on the recorded events and folds them into the totals
+    void reset();
+    void destroy();
+};
+
+struct TimedScope {
+    KernelTimer& t;
+    cudaStream_t st;
+    int rec;
+    TimedScope(KernelTimer& timer, int k, double b, double f, cudaStream_t s)
+        : t(timer), st(s), rec(timer.begin(k, b, f, s)) {}
+    ~TimedScope() { t.end(rec, st); }
+};
+
+}  // namespace mhs
+
+struct mhs_ctx {
+    int nx, ny, nz;
+    double Lx, Ly, Lz, alpha;
+    mhs_xi_params xi;
+    mhs_atmos_params atm;
+    mhs_solver_opts opts;
+    cudaStream_t stream = nullptr;
+    mhs::Hierarchy h3, h2;
+    mhs::NormScratch ns;
+    double* bz = nullptr;          // lower-boundary field [ny x px] (device, pitched)
+    double* prof = nullptr;        // per fine plane: xi, dxi, p_b, rho_b (4*nz doubles, device)
+    int* flag = nullptr;           // device flags (non-finite input detection)
+    int* flag_host = nullptr;      // pinned mirror
+    double* staging = nullptr;     // FP64 staging buffer of the finest size (level hooks, lazily allocated)
+    double* fld[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // pitched Bx, By, Bz, p, rho
+    bool have_bz = false, have_solution = false;
+    bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
+    std::vector<void*> allocations;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    mhs::KernelTimer timer;
+};
+
+namespace mhs {
+
+// ---- kernels (kernels_mg.cu) ----
+template <typename T>
+void launch_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, PlaneCoef<T>* coef,
+                 cudaStream_t st);
+void launch_profiles(const Geom& g, const mhs_xi_params& xi, const mhs_atmos_params& atm, double* prof,
+                     cudaStream_t st);
+template <typename T>
+void launch_fill(T* a, size_t n, T v, cudaStream_t st);
+template <typename T>
+void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
+template <typename T>
+void launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
+                     NormScratch* ns, int slot, cudaStream_t st);
+template <typename T>
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, cudaStream_t st);
+template <typename T>
+void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st);
+template <typename T>
+void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
+// lower-boundary right-hand side f = -B_z at interior nodes (FP64 and FP32 copies)
+void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st);
+// mixed precision pieces
+void launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
+                            const double* f, float* r32, NormScratch* ns, int slot, cudaStream_t st);
+void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cudaStream_t st);
+template <typename T>
+void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st);
+void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st);
+void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st);
+// norm^2 of the lifted right-hand side of the interior problem: cz * P[k=0] on plane k=1
+void launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, NormScratch* ns, int slot,
+                      cudaStream_t st);
+
+// ---- fields (kernels_fields.cu) ----
+void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, const double* prof,
+                   const double* P, double* Bx, double* By, double* Bz, double* p, double* rho, int bz_mode,
+                   cudaStream_t st);
+
+}  // namespace mhs

@@ -1,0 +1,28 @@
+// Driver entry points used by the C-ABI layer.
+#pragma once
+
+#include "mhs_internal.h"
+
+namespace mhs {
+
+// slots of NormScratch::result
+constexpr int NORM_B_SLOT = 0;        // ||b||^2 of the current solve
+constexpr int NORM_RES_SLOT = 1;      // ||f - A u||^2 after the latest cycle
+constexpr int NORM_SCRATCH_SLOT = 2;  // residual norms inside V-cycles (unused by the driver)
+constexpr int NORM_HOOK_SLOT = 3;     // level-hook residuals
+
+void create(mhs_ctx* c);
+void destroy(mhs_ctx* c);
+void compute_coefficients(mhs_ctx* c);
+mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info);
+template <typename T>
+void vcycle(mhs_ctx* c, Hierarchy& H, int l);
+double read_norm2(mhs_ctx* c, int slot);
+void ensure_field_buffers(mhs_ctx* c);
+void ensure_staging(mhs_ctx* c);
+
+// conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)
+void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
+void launch_f2d(const float* src, double* dst, size_t n, cudaStream_t st);
+
+}  // namespace mhs

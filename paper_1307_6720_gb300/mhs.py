@@ -1,0 +1,260 @@
+"""ctypes binding of libmhs (include/mhs.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name.  Array arguments
+may be torch tensors (device or host, float64, contiguous) or numpy float64
+arrays; their data pointers are passed straight through.  Every step of the
+solver runs in the library's CUDA kernels; there is no fallback: if the
+library is missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhs.so")
+
+MHS_OK = 0
+STATUS_NAMES = ["MHS_OK", "MHS_ERR_INVALID_ARG", "MHS_ERR_NOT_ELLIPTIC", "MHS_ERR_OUT_OF_MEMORY", "MHS_ERR_CUDA",
+                "MHS_ERR_NO_CONVERGENCE", "MHS_ERR_NONFINITE", "MHS_ERR_BAD_STATE", "MHS_ERR_TIMEOUT",
+                "MHS_ERR_REJECTED"]
+(MHS_ERR_INVALID_ARG, MHS_ERR_NOT_ELLIPTIC, MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA, MHS_ERR_NO_CONVERGENCE,
+ MHS_ERR_NONFINITE, MHS_ERR_BAD_STATE, MHS_ERR_TIMEOUT, MHS_ERR_REJECTED) = range(1, 10)
+MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
+MHS_FP64, MHS_MIXED = 0, 1
+MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC = 1, 2
+MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
+MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
+
+
+class XiParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("b", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class AtmosParams(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("mu0", ctypes.c_double), ("T_cor", ctypes.c_double),
+                ("z1", ctypes.c_double), ("z2", ctypes.c_double)]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("cycles_2d", ctypes.c_int), ("cycles_3d", ctypes.c_int), ("rel_res_2d", ctypes.c_double),
+                ("rel_res_3d", ctypes.c_double), ("conv_factor", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MhsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+_H = ctypes.c_void_p
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "mhs_create": [_I, _I, _I, _D, _D, _D, _D, ctypes.POINTER(XiParams), ctypes.POINTER(AtmosParams),
+                   ctypes.POINTER(_H)],
+    "mhs_destroy": [_H],
+    "mhs_set_stream": [_H, _P],
+    "mhs_set_options": [_H, ctypes.POINTER(SolverOpts)],
+    "mhs_set_params": [_H, _D, ctypes.POINTER(XiParams), ctypes.POINTER(AtmosParams)],
+    "mhs_set_lower_bz": [_H, _P],
+    "mhs_solve": [_H, _D, _I, ctypes.POINTER(SolveInfo)],
+    "mhs_get_phi": [_H, _P],
+    "mhs_fields": [_H, _P, _P, _P, _P, _P],
+    "mhs_num_levels": [_H, _I, ctypes.POINTER(_I)],
+    "mhs_level_shape": [_H, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "mhs_level_write": [_H, _I, _I, _I, _I, _P],
+    "mhs_level_read": [_H, _I, _I, _I, _I, _P],
+    "mhs_level_op": [_H, _I, _I, _I, _I],
+    "mhs_status_string": [_I],
+    "mhs_last_error": [],
+    "mhs_version": [],
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libmhs not built ({path} missing): run __graft_entry__.build() "
+                          "or python paper_1307_6720_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        if name == "mhs_destroy":
+            fn.restype = None
+        elif name in ("mhs_status_string", "mhs_last_error", "mhs_version"):
+            fn.restype = ctypes.c_char_p
+        else:
+            fn.restype = ctypes.c_int
+    return lib
+
+
+LIB = load()
+
+
+def _check(status: int) -> None:
+    if status != MHS_OK:
+        raise MhsError(status, LIB.mhs_last_error().decode())
+
+
+def ptr(a) -> int | None:
+    """Data pointer of a torch tensor or numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous(), "expected a contiguous float64 tensor"
+        return a.data_ptr()
+    import numpy as np
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "expected a contiguous float64 array"
+    return a.ctypes.data
+
+
+def xi_params(kind=MHS_XI_NONE, a=0.0, kappa=0.0, b=0.0, omega=0.0) -> XiParams:
+    return XiParams(kind, a, kappa, b, omega)
+
+
+def atmos_params(g=1.0, mu0=0.5, T_cor=150.0, z1=5.0, z2=10.0) -> AtmosParams:
+    return AtmosParams(g, mu0, T_cor, z1, z2)
+
+
+# ---- one wrapper per C entry point, same names ----
+
+def mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha, xi: XiParams | None = None, atm: AtmosParams | None = None) -> int:
+    h = _H()
+    _check(LIB.mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha, ctypes.byref(xi) if xi is not None else None,
+                          ctypes.byref(atm) if atm is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def mhs_destroy(h) -> None:
+    LIB.mhs_destroy(h)
+
+
+def mhs_set_stream(h, stream) -> None:
+    """stream: a torch.cuda.Stream, an integer cudaStream_t, or None (legacy default)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(LIB.mhs_set_stream(h, stream))
+
+
+def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags)
+    _check(LIB.mhs_set_options(h, ctypes.byref(o)))
+
+
+def mhs_set_params(h, alpha, xi: XiParams | None = None, atm: AtmosParams | None = None) -> None:
+    _check(LIB.mhs_set_params(h, alpha, ctypes.byref(xi) if xi is not None else None,
+                              ctypes.byref(atm) if atm is not None else None))
+
+
+def mhs_set_lower_bz(h, bz) -> None:
+    _check(LIB.mhs_set_lower_bz(h, ptr(bz)))
+
+
+def mhs_solve(h, tol, mode=MHS_FP64) -> dict:
+    info = SolveInfo()
+    st = LIB.mhs_solve(h, tol, mode, ctypes.byref(info))
+    if st != MHS_OK:
+        err = MhsError(st, LIB.mhs_last_error().decode())
+        err.info = info.as_dict()
+        raise err
+    return info.as_dict()
+
+
+def mhs_get_phi(h, phi) -> None:
+    _check(LIB.mhs_get_phi(h, ptr(phi)))
+
+
+def mhs_fields(h, Bx=None, By=None, Bz=None, p=None, rho=None) -> None:
+    _check(LIB.mhs_fields(h, ptr(Bx), ptr(By), ptr(Bz), ptr(p), ptr(rho)))
+
+
+def mhs_num_levels(h, dim=3) -> int:
+    n = _I()
+    _check(LIB.mhs_num_levels(h, dim, ctypes.byref(n)))
+    return n.value
+
+
+def mhs_level_shape(h, dim, level):
+    nx, ny, nz = _I(), _I(), _I()
+    _check(LIB.mhs_level_shape(h, dim, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz)))
+    return nx.value, ny.value, nz.value
+
+
+def mhs_level_write(h, dim, level, field, prec, src) -> None:
+    _check(LIB.mhs_level_write(h, dim, level, field, prec, ptr(src)))
+
+
+def mhs_level_read(h, dim, level, field, prec, dst) -> None:
+    _check(LIB.mhs_level_read(h, dim, level, field, prec, ptr(dst)))
+
+
+def mhs_level_op(h, dim, level, op, prec) -> None:
+    _check(LIB.mhs_level_op(h, dim, level, op, prec))
+
+
+def mhs_status_string(s: int) -> str:
+    return LIB.mhs_status_string(s).decode()
+
+
+def mhs_last_error() -> str:
+    return LIB.mhs_last_error().decode()
+
+
+def mhs_version() -> str:
+    return LIB.mhs_version().decode()
+
+
+class Solver:
+    """Owns one handle; device buffers come from torch (memory and streams only)."""
+
+    def __init__(self, nx, ny, nz, Lx=1.0, Ly=1.0, Lz=1.0, alpha=0.0, xi: XiParams | None = None,
+                 atm: AtmosParams | None = None, stream=None):
+        self.shape = (nz, ny, nx)
+        self.h = mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha, xi, atm)
+        if stream is not None:
+            mhs_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h:
+            mhs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        mhs_set_options(self.h, **kw)
+
+    def set_lower_bz(self, bz):
+        mhs_set_lower_bz(self.h, bz)
+
+    def solve(self, tol=1e-10, mode=MHS_FP64) -> dict:
+        return mhs_solve(self.h, tol, mode)
+
+    def phi(self, device="cuda"):
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device=device)
+        mhs_get_phi(self.h, out)
+        return out
+
+    def fields(self, device="cuda"):
+        import torch
+        outs = [torch.empty(self.shape, dtype=torch.float64, device=device) for _ in range(5)]
+        mhs_fields(self.h, *outs)
+        return dict(zip(["Bx", "By", "Bz", "p", "rho"], outs))

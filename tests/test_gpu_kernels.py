@@ -1,0 +1,192 @@
+"""Operation-by-operation parity of the CUDA kernels with the CPU oracle,
+through the C-ABI level hooks (the kernels the solver itself runs).
+
+Grids are small, odd and non-cubic so several thread blocks and ragged
+tails are exercised.  FP64 kernels agree with the oracle to a few ulp (the
+GPU multiplies by a precomputed 1/d where the oracle divides by d, and sums
+in a different order); FP32 kernels agree to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+XI2 = dict(xi_kind=2, xi_a=0.7, xi_b=0.3, xi_omega=np.pi, xi_kappa=0.1)
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1307_6720_gb300 import mhs
+    return mhs
+
+
+SHAPES = [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5)]
+
+
+def _make(M, nx, ny, nz, Lx=1.0, Ly=0.6, Lz=0.8, alpha=0.7, xi=XI2):
+    pr = S.problem(nx, ny, nz, Lx=Lx, Ly=Ly, Lz=Lz, alpha=alpha, **xi)
+    h = M.mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha,
+                     M.xi_params(xi["xi_kind"], xi["xi_a"], xi["xi_kappa"], xi.get("xi_b", 0), xi.get("xi_omega", 0)))
+    return pr, h
+
+
+def _read(M, h, dim, level, field, prec):
+    nx, ny, nz = M.mhs_level_shape(h, dim, level)
+    out = np.zeros((nz, ny, nx)) if dim == 3 else np.zeros((ny, nx))
+    M.mhs_level_read(h, dim, level, field, prec, out)
+    return out
+
+
+def _tol(prec):
+    return 2e-13 if prec == 0 else 3e-6
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_smooth_parity_3d(M, shape, prec):
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz)
+    rng = np.random.default_rng(nx * 7 + ny)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 50
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:   # the FP32 kernels see the rounded inputs
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    for _ in range(2):
+        M.mhs_level_op(h, 3, 0, M.MHS_OP_SMOOTH, prec)
+    got = _read(M, h, 3, 0, M.MHS_FIELD_U, prec)
+    want = oracle.rbgs3d(pr, u, f, 2)
+    assert _rel(got, want) < _tol(prec) * 10
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_residual_parity_3d(M, shape, prec):
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx))
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    M.mhs_level_op(h, 3, 0, M.MHS_OP_RESIDUAL, prec)
+    got = _read(M, h, 3, 0, M.MHS_FIELD_R, prec)
+    want = oracle.residual3d(pr, u, f)
+    sl = (slice(1, -1),) * 3
+    scale = np.abs(u).max() * 4 * (nx - 1) ** 2 / pr["Lx"] ** 2
+    assert np.abs(got[sl] - want[sl]).max() < _tol(prec) * scale
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
+def test_restriction_and_prolongation_parity(M, dim, prec):
+    nx, ny, nz = 33, 17, 9
+    pr, h = _make(M, nx, ny, nz)
+    rng = np.random.default_rng(5)
+    fine = (nz, ny, nx) if dim == 3 else (ny, nx)
+    r = rng.standard_normal(fine)
+    inner = (slice(1, -1),) * len(fine)
+    mask = np.zeros(fine, bool); mask[inner] = True
+    r[~mask] = 0.0
+    M.mhs_level_write(h, dim, 0, M.MHS_FIELD_R, prec, r)
+    M.mhs_level_op(h, dim, 0, M.MHS_OP_RESTRICT, prec)
+    fc = _read(M, h, dim, 1, M.MHS_FIELD_F, prec)
+    want = oracle.restrict(r if prec == 0 else r.astype(np.float32).astype(np.float64))
+    cin = (slice(1, -1),) * len(fine)
+    assert _rel(fc[cin], want[cin]) < _tol(prec)
+    # prolongation + correction
+    cs = oracle.coarse_shape(fine)
+    ec = rng.standard_normal(cs)
+    cm = np.zeros(cs, bool); cm[(slice(1, -1),) * len(cs)] = True
+    ec[~cm] = 0.0
+    uf = rng.standard_normal(fine)
+    M.mhs_level_write(h, dim, 1, M.MHS_FIELD_U, prec, ec)
+    M.mhs_level_write(h, dim, 0, M.MHS_FIELD_U, prec, uf)
+    M.mhs_level_op(h, dim, 0, M.MHS_OP_PROLONG, prec)
+    got = _read(M, h, dim, 0, M.MHS_FIELD_U, prec)
+    if prec == 1:
+        ec, uf = ec.astype(np.float32).astype(np.float64), uf.astype(np.float32).astype(np.float64)
+    assert _rel(got, oracle.prolong_add(ec, uf)) < _tol(prec)
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_smooth_and_residual_parity_2d(M, prec):
+    nx, ny = 65, 33
+    pr, h = _make(M, nx, ny, 9, Lx=1.0, Ly=0.5)
+    rng = np.random.default_rng(8)
+    u = rng.standard_normal((ny, nx)); u[0] = u[-1] = 0; u[:, 0] = u[:, -1] = 0
+    f = rng.standard_normal((ny, nx)) * 100
+    M.mhs_level_write(h, 2, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 2, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    M.mhs_level_op(h, 2, 0, M.MHS_OP_SMOOTH, prec)
+    got = _read(M, h, 2, 0, M.MHS_FIELD_U, prec)
+    want = oracle.rbgs2d(pr, u, f, 1)
+    assert _rel(got, want) < _tol(prec) * 10
+    M.mhs_level_op(h, 2, 0, M.MHS_OP_RESIDUAL, prec)
+    r = _read(M, h, 2, 0, M.MHS_FIELD_R, prec)
+    rw = oracle.residual2d(pr, want, f)
+    scale = np.abs(want).max() * 4 * (nx - 1) ** 2
+    assert np.abs(r[1:-1, 1:-1] - rw[1:-1, 1:-1]).max() < _tol(prec) * scale * 10
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
+def test_coarse_solve_reaches_coarse_solution(M, dim, prec):
+    """The one-CTA coarsest-level solve returns the solution of the coarse
+    system (checked by the oracle's residual on that grid)."""
+    nx, ny, nz = 65, 65, 33
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=1.0, Lz=0.5)
+    L = M.mhs_num_levels(h, dim) - 1
+    cshape = M.mhs_level_shape(h, dim, L)
+    shape = cshape[::-1] if dim == 3 else cshape[1::-1]
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal(shape)
+    M.mhs_level_write(h, dim, L, M.MHS_FIELD_F, prec, f)
+    M.mhs_level_op(h, dim, L, M.MHS_OP_COARSE, prec)
+    u = _read(M, h, dim, L, M.MHS_FIELD_U, prec)
+    fm = f.copy()
+    fm[(0,) if dim == 2 else (0,)] = 0
+    if dim == 3:
+        r = oracle.residual3d(pr, u, f)
+        fi = f[1:-1, 1:-1, 1:-1]
+    else:
+        r = oracle.residual2d(pr, u, f)
+        fi = f[1:-1, 1:-1]
+    assert np.linalg.norm(r) <= (1e-12 if prec == 0 else 1e-5) * np.linalg.norm(fi)
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vcycle_parity_3d(M, prec):
+    nx, ny, nz = 33, 33, 17
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=1.0, Lz=0.5)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 100
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    M.mhs_level_op(h, 3, 0, M.MHS_OP_VCYCLE, prec)
+    got = _read(M, h, 3, 0, M.MHS_FIELD_U, prec)
+    want = oracle.vcycle(pr, u, f)
+    assert _rel(got, want) < (1e-11 if prec == 0 else 1e-5)
+    M.mhs_destroy(h)
