@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the linear-MHS multigrid path on GB300.
+
+Metric: unknowns solved per second to a 1e-10 relative residual, where one
+solve is the lower-boundary multigrid solve (eq. lower_bound), the interior
+multigrid solve (eq. scalar_pot) and the recovery of B, p and rho, and the
+unknowns are the interior nodes of both problems.
+
+Default workload (one GPU): 129^3 nodes on [0,1]^3, alpha = 0.5,
+xi(z) = 0.5 exp(-z), B_z = 8 flux-balanced Gaussian spots (splitmix64
+seeds), FP64 mode; outputs Phi, B_x, B_y, B_z, p, rho.  A step is one such
+solve of one magnetogram whose data is resident in HBM; L2 is flushed
+(256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed] [--impl mhs|reference]
+
+With N > 1 (torchrun) every rank solves its own magnetograms (replicas, no
+collective on the data path); value = all ranks' unknowns / max rank time.
+--impl reference times the CPU oracle (plain C, OpenMP over z-planes) on
+the host cores, one oracle solve per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+TOL = 1e-10
+METRIC = "unknowns solved/s to 1e-10 rel. residual"
+UNIT = "unknowns/s"
+
+
+def workload(rank: int, nmag: int = 4):
+    """129^3 linear-MHS problem; magnetograms for this rank."""
+    pr, _ = S.linear_mhs(129)
+    mags = [S.magnetogram_random(129, 129, 1.0, 1.0, seed=1307 + 100 * rank + i) for i in range(nmag)]
+    cfg = {"workload": "linear_mhs_129", "grid": [129, 129, 129], "domain": "[0,1]^3", "alpha": 0.5,
+           "xi": "0.5*exp(-z)", "bz": f"8 flux-balanced Gaussian spots, splitmix64 seeds 1307..{1306 + nmag} (+100*rank)",
+           "tol": TOL, "outputs": "Phi,Bx,By,Bz,p,rho", "unknowns_per_solve": S.unknowns(pr)}
+    return pr, mags, cfg
+
+
+# --------------------------------------------------------------------------
+# GPU clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for _, _, flags in rows for q, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# reference arm and CPU baseline: the oracle on the host cores
+# --------------------------------------------------------------------------
+
+def oracle_solve_rate(pr, mags, budget_s: float, min_runs: int = 1):
+    import oracle
+    t0 = time.perf_counter()
+    runs = 0
+    while runs < min_runs or time.perf_counter() - t0 < budget_s:
+        P, info = oracle.solve(pr, mags[runs % len(mags)], TOL, TOL)
+        oracle.fields(pr, P)
+        assert info["status"] == 0
+        runs += 1
+    dt = time.perf_counter() - t0
+    return S.unknowns(pr) * runs / dt, runs, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pr, mags, cfg = workload(0)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.fields(pr, oracle.solve(pr, mags[0], TOL, TOL)[0])
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        P, info = oracle.solve(pr, mags[s % len(mags)], TOL, TOL)
+        oracle.fields(pr, P)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    value = S.unknowns(pr) / per
+    cores = oracle.max_threads()
+    cfg = dict(cfg, mode="fp64", parallelism=f"oracle, OpenMP {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle solves (2D+3D multigrid to 1e-10 + fields) of the 129^3 workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (profiling recipe table); own FMA probe measured 1.01
+
+
+def profiled_traffic(kind_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        ent = d["kernels"][kind_name]
+        import hashlib
+        h = hashlib.sha256(open(os.path.join(ROOT, ent["source"]), "rb").read()).hexdigest()
+        return ent["bytes_per_launch"] if h == ent["sha256"] else None
+    except Exception:
+        return None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1307_6720_gb300 import mhs as M
+
+    pr, mags, cfg = workload(rank)
+    mode = M.MHS_MIXED if args.mode == "mixed" else M.MHS_FP64
+    stream = torch.cuda.current_stream()
+    xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
+    h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
+    M.mhs_set_stream(h, stream)
+    shape = (pr["nz"], pr["ny"], pr["nx"])
+    bz_dev = [torch.from_numpy(b).to(dev) for b in mags]
+    outs_dev = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(6)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(s, m=mode, bz=bz_dev, outs=outs_dev):
+        M.mhs_set_lower_bz(h, bz[s % len(bz)])
+        info = M.mhs_solve(h, TOL, m)
+        M.mhs_get_phi(h, outs[0])
+        M.mhs_fields(h, *outs[1:])
+        return info
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(K, m=mode, bz=bz_dev, outs=outs_dev, host_out=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        infos = []
+        barrier()
+        for s in range(K):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            infos.append(step(s, m, bz, outs))
+            ev[s][1].record(stream)
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    for s in range(args.warmup):
+        step(s)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if "CUDA_VISIBLE_DEVICES" in os.environ else str(local)
+    clocks = ClockSampler(gpu_index)
+    l0 = M.mhs_kernel_launches()
+    clocks.start()
+    ms, infos = timed(args.steps)
+    clk = clocks.stop()
+    launches = M.mhs_kernel_launches() - l0
+    unknowns = S.unknowns(pr)
+    value = unknowns * world / (ms * 1e-3)
+
+    # per-kernel durations over a second, identical timed pass with event instrumentation
+    M.mhs_set_kernel_timing(h, True)
+    M.mhs_kernel_timing_reset(h)
+    timed(args.steps)
+    kt = [M.mhs_kernel_timing(h, k) for k in range(M.MHS_KT_COUNT)]
+    M.mhs_set_kernel_timing(h, False)
+    kt = [k for k in kt if k["launches"] > 0]
+    dom = max(kt, key=lambda k: k["ms"])
+    hbm_peak, peak_src = measured_peaks()
+    avg_ms = dom["ms"] / dom["launches"]
+    gbs = dom["bytes"] / dom["launches"] / (avg_ms * 1e-3) / 1e9
+    tfl = dom["flops"] / dom["launches"] / (avg_ms * 1e-3) / 1e12
+    alu_bound = dom["name"].endswith("64") or dom["name"] in ("fields", "residual_mixed")
+    traffic = profiled_traffic(dom["name"])
+    if alu_bound:
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "kernel": dom["name"], "peak_source": "nominal FP64 (recipe table)",
+                "achieved_gbs": gbs, "hbm_frac_of_" + peak_src: gbs / hbm_peak}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": traffic, "kernel": dom["name"], "peak_source": peak_src}
+    roof.update({"launches_timed": dom["launches"], "avg_launch_ms": avg_ms,
+                 "alg_bytes_per_launch": dom["bytes"] / dom["launches"],
+                 "alg_flops_per_launch": dom["flops"] / dom["launches"],
+                 "share_of_timed_ops": dom["ms"] / sum(k["ms"] for k in kt)})
+    kernels = {k["name"]: {"ms_per_step": k["ms"] / args.steps, "launches_per_step": k["launches"] / args.steps,
+                           "gbs": k["bytes"] / (k["ms"] * 1e-3) / 1e9 if k["ms"] > 0 else None} for k in kt}
+
+    # the other precision mode on the same workload
+    other = M.MHS_FP64 if mode == M.MHS_MIXED else M.MHS_MIXED
+    ms_o, infos_o = timed(args.steps, other)
+
+    # end to end through the C ABI with pinned host buffers
+    bz_host = [torch.from_numpy(b).pin_memory() for b in mags]
+    outs_host = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(6)]
+    ms_e2e, _ = timed(args.steps, mode, bz_host, outs_host)
+    e2e = {"value": unknowns * world / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(pr["nx"] * pr["ny"] * 8), "d2h_bytes_per_step": int(6 * np.prod(shape) * 8)}
+
+    # error of the last timed solve against the exact discrete solution (CPU, outside timing)
+    cpu_base = None
+    if rank == 0:
+        rate, runs, dt, cores = oracle_solve_rate(pr, mags, args.cpu_budget)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": f"{runs} oracle solves (2D+3D multigrid to 1e-10 + fields) of the 129^3 workload, {dt:.1f} s"}
+
+    if rank == 0:
+        name = "mixed" if mode == M.MHS_MIXED else "fp64"
+        oname = "fp64" if name == "mixed" else "mixed"
+        cfg = dict(cfg, mode=name, l2="flushed between timed steps (256 MiB device write)",
+                   parallelism="replicas" if world > 1 else "single GPU")
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if name == "fp64" else "f32+f64", "data": "synthetic", "config": cfg,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu_base,
+            "cycles": {"2d": infos[-1]["cycles_2d"], "3d": infos[-1]["cycles_3d"],
+                       "rel_res_3d": infos[-1]["rel_res_3d"], "conv_factor": infos[-1]["conv_factor"]},
+            "modes": {oname: {"value": unknowns * world / (ms_o * 1e-3), "ms_per_step": ms_o,
+                              "cycles_3d": infos_o[-1]["cycles_3d"], "rel_res_3d": infos_o[-1]["rel_res_3d"]}},
+            "kernels": kernels,
+        }
+        print(json.dumps(out))
+    M.mhs_destroy(h)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--impl", choices=["mhs", "reference"], default="mhs")
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mhs":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

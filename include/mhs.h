@@ -239,6 +239,10 @@ MHS_API const char* mhs_status_string(mhs_status s);
  * (empty string if none).  Valid until the next failing call on that thread. */
 MHS_API const char* mhs_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles; for launch accounting around a timed region). */
+MHS_API long long mhs_kernel_launches(void);
+
 /* Library version string (static storage). */
 MHS_API const char* mhs_version(void);
 

@@ -129,6 +129,8 @@ extern "C" {
 
 const char* mhs_version(void) { return "mhs-gb300 0.1"; }
 
+long long mhs_kernel_launches(void) { return mhs::launches(); }
+
 const char* mhs_last_error(void) { return g_last_error.c_str(); }
 
 const char* mhs_status_string(mhs_status s) {
@@ -200,7 +202,10 @@ mhs_status mhs_set_options(mhs_handle h, const mhs_solver_opts* opts) {
                  opts->nu1 > 16 || opts->nu2 > 16 || opts->inner_cycles > 16))
         return fail(MHS_ERR_INVALID_ARG, "options out of range");
     fill_opts(&h->opts, opts);
-    return MHS_OK;
+    return guarded([&] {
+        mhs::invalidate_graphs(h);
+        return MHS_OK;
+    });
 }
 
 mhs_status mhs_set_params(mhs_handle h, double alpha, const mhs_xi_params* xi, const mhs_atmos_params* atm) {
@@ -369,9 +374,9 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
             switch (op) {
             case MHS_OP_SMOOTH: mhs::launch_smooth<T>(g, dim, A.coef, A.u, A.f, st); break;
             case MHS_OP_RESIDUAL:
-                mhs::launch_residual<T>(g, dim, A.coef, A.u, A.f, A.r, &h->ns, mhs::NORM_HOOK_SLOT, st);
+                mhs::launch_residual<T>(g, dim, A.coef, A.u, A.f, A.r, nullptr, 0, st);
                 break;
-            case MHS_OP_RESTRICT: mhs::launch_restrict<T>(g, H.g[level + 1], dim, A.r, C.f, st); break;
+            case MHS_OP_RESTRICT: mhs::launch_restrict<T>(g, H.g[level + 1], dim, A.r, C.f, (T*)nullptr, st); break;
             case MHS_OP_PROLONG: mhs::launch_prolong<T>(H.g[level + 1], g, dim, C.u, A.u, st); break;
             case MHS_OP_COARSE:
                 if (2 * g.n * sizeof(T) > 200 * 1024) throw mhs::Error(MHS_ERR_INVALID_ARG, "level too large for the one-CTA solve");

@@ -12,6 +12,7 @@
 // first derivative along z.  B_z takes the compact three-point second
 // difference (the operator of eq. lower_bound) or, with bz_mode = 1, the
 // first-difference operator applied twice.
+#include "device_util.cuh"
 #include "mhs_internal.h"
 
 namespace mhs {
@@ -38,10 +39,6 @@ __device__ __forceinline__ St d2(int t, int n, double h) {
     if (t == 0) return St{{0, 1, 2, 3}, {2.0 * a, -5.0 * a, 4.0 * a, -a}, 4};
     if (t == n - 1) return St{{0, -1, -2, -3}, {2.0 * a, -5.0 * a, 4.0 * a, -a}, 4};
     return St{{-1, 0, 1, 0}, {a, -2.0 * a, a, 0.0}, 3};
-}
-
-__device__ __forceinline__ size_t at(const Geom& g, int i, int j, int k) {
-    return size_t(i) + size_t(g.px) * (size_t(j) + size_t(g.ny) * size_t(k));
 }
 
 // d/dx_a applied along axis a (0,1,2) of array f at (i,j,k)
@@ -143,8 +140,10 @@ void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, con
     const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, gz);
     const double inv2mu0 = 1.0 / (2.0 * atm.mu0);
     field_b_kernel<<<grid, blk, 0, st>>>(g, alpha, inv2mu0, prof, P, Bx, By, Bz, p, bz_mode);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
     field_rho_kernel<<<grid, blk, 0, st>>>(g, inv2mu0, 1.0 / atm.mu0, 1.0 / atm.g, prof, Bx, By, Bz, rho);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 

@@ -11,6 +11,7 @@
 
 #include <cmath>
 
+#include "device_util.cuh"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -19,35 +20,6 @@ namespace mhs {
 namespace {
 
 constexpr int BX = 32, BY = 8;
-
-__device__ __forceinline__ size_t at(const Geom& g, int i, int j, int k) {
-    return size_t(i) + size_t(g.px) * (size_t(j) + size_t(g.ny) * size_t(k));
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-wide sum; every thread of the block must call it.  Result valid in thread 0.
-template <typename T>
-__device__ T block_sum(T v) {
-    __shared__ T ws[32];
-    const int lane = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-    v = warp_sum(v);
-    if ((lane & 31) == 0) ws[lane >> 5] = v;
-    __syncthreads();
-    T s = T(0);
-    if (lane < 32) {
-        s = (lane < (nthreads + 31) / 32) ? ws[lane] : T(0);
-        s = warp_sum(s);
-    }
-    __syncthreads();
-    return s;
-}
 
 // -------------------------------------------------------------------------
 // a1: per-plane coefficients and height profiles (Sect. 2.1, eq. scalar_pot;
@@ -155,8 +127,9 @@ __global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* 
     }
 }
 
-// r = f - A u at interior nodes; per-block partial sums of r^2 (in double)
-// into ns.partial, finished by norm_finish_kernel in fixed order.
+// r = f - A u at interior nodes; with partial != nullptr also per-block
+// partial sums of r^2 (in double), finished in fixed order by
+// norm_finish_kernel / check_kernel.
 template <typename T, bool D3>
 __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
                                 const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
@@ -174,6 +147,7 @@ __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, c
             acc += double(rv) * double(rv);
         }
     }
+    if (partial == nullptr) return;   // uniform across the block
     const double s = block_sum(acc);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
@@ -213,8 +187,10 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, do
 
 // Full weighting: tensor product of (1/4, 1/2, 1/4) around the fine node
 // (2I, 2J, 2K) coincident with coarse interior node (I, J, K).
+// With uc != nullptr the coarse iterate is zeroed at the same nodes (the
+// initial guess of the coarse-grid correction).
 template <typename T, bool D3>
-__global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc) {
+__global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc, T* __restrict__ uc) {
     const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (I > gc.nx - 2 || J > gc.ny - 2) return;
@@ -235,6 +211,7 @@ __global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* _
             acc += wc * s;
         }
         fc[at(gc, I, J, K)] = acc;
+        if (uc) uc[at(gc, I, J, K)] = T(0);
     }
 }
 
@@ -403,10 +380,6 @@ dim3 grid_for(const Geom& g, int d3, int xcount, int max_blocks) {
     return dim3(gx, gy, gz);
 }
 
-void finish_norm(NormScratch* ns, int nblocks, int slot, cudaStream_t st) {
-    norm_finish_kernel<<<1, 1024, 0, st>>>(ns->partial, nblocks, ns->result + slot);
-    MHS_CUDA(cudaGetLastError());
-}
 
 }  // namespace
 
@@ -416,12 +389,14 @@ template <typename T>
 void launch_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, PlaneCoef<T>* coef,
                  cudaStream_t st) {
     coef_kernel<T><<<(g.nz + 127) / 128, 128, 0, st>>>(g, dim, alpha, xi, coef);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
 void launch_profiles(const Geom& g, const mhs_xi_params& xi, const mhs_atmos_params& atm, double* prof,
                      cudaStream_t st) {
     profile_kernel<<<(g.nz + 127) / 128, 128, 0, st>>>(g, xi, atm, prof);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -431,6 +406,7 @@ void launch_fill(T* a, size_t n, T v, cudaStream_t st) {
     size_t blocks = (n + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     fill_kernel<T><<<unsigned(blocks), 256, 0, st>>>(a, n, v);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -442,37 +418,47 @@ void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
     for (int colour = 0; colour < 2; ++colour) {
         if (d3) colour_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
         else colour_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+        count_launches(1);
     }
     MHS_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-void launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
-                     NormScratch* ns, int slot, cudaStream_t st) {
+int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r, double* partial,
+                    int max_blocks, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, ns->max_blocks);
-    if (d3) residual_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, ns->partial);
-    else residual_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, ns->partial);
+    const dim3 grid = grid_for(g, d3, g.nx - 2, partial ? max_blocks : 0);
+    if (d3) residual_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+    else residual_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
-    finish_norm(ns, grid.x * grid.y * grid.z, slot, st);
+    return int(grid.x * grid.y * grid.z);
 }
 
-void launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
-                            const double* f, float* r32, NormScratch* ns, int slot, cudaStream_t st) {
-    const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, ns->max_blocks);
-    if (d3) residual_f32_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, ns->partial);
-    else residual_f32_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, ns->partial);
+void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t st) {
+    norm_finish_kernel<<<1, 1024, 0, st>>>(partial, n, out);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
-    finish_norm(ns, grid.x * grid.y * grid.z, slot, st);
+}
+
+int launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u, const double* f,
+                           float* r32, double* partial, int max_blocks, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = grid_for(g, d3, g.nx - 2, max_blocks);
+    if (d3) residual_f32_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
+    else residual_f32_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+    return int(grid.x * grid.y * grid.z);
 }
 
 template <typename T>
-void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, cudaStream_t st) {
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st) {
     const int d3 = dim == 3;
     const dim3 grid = grid_for(gc, d3, gc.nx - 2, 0);
-    if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc);
-    else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc);
+    if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
+    else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -482,6 +468,7 @@ void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf,
     const dim3 grid = grid_for(gf, d3, gf.nx - 2, 0);
     if (d3) prolong_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
     else prolong_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -493,9 +480,11 @@ void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
     if (dim == 3) {
         MHS_CUDA(cudaFuncSetAttribute(coarse_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         coarse_kernel<T, true><<<1, 512, smem, st>>>(g, coef, u, f, tol, max_sweeps);
+        count_launches(1);
     } else {
         MHS_CUDA(cudaFuncSetAttribute(coarse_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         coarse_kernel<T, false><<<1, 512, smem, st>>>(g, coef, u, f, tol, max_sweeps);
+        count_launches(1);
     }
     MHS_CUDA(cudaGetLastError());
 }
@@ -503,6 +492,7 @@ void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
 void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st) {
     const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
     lower_rhs_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, f64);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -510,6 +500,7 @@ void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cu
     const int d3 = dim == 3;
     const dim3 grid = grid_for(g, d3, g.nx - 2, 0);
     add_correction_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, d3, e, u);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
@@ -518,36 +509,40 @@ void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st) {
     const int d3 = dim == 3;
     const dim3 grid = grid_for(g, d3, g.nx - 2, 0);
     zero_interior_kernel<T><<<grid, dim3(BX, BY), 0, st>>>(g, d3, u);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
 void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st) {
     const dim3 grid((g2.nx + BX - 1) / BX, (g2.ny + BY - 1) / BY);
     copy_plane_kernel<<<grid, dim3(BX, BY), 0, st>>>(g2, src2d, g3, dst3d);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
 void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st) {
     const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
     nonfinite_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, flag);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
-void launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, NormScratch* ns, int slot,
-                      cudaStream_t st) {
+int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, double* partial,
+                     cudaStream_t st) {
     const dim3 grid((g3.nx - 2 + BX - 1) / BX, (g3.ny - 2 + BY - 1) / BY);
-    lift_norm_kernel<<<grid, dim3(BX, BY), 0, st>>>(g3, coef, u, ns->partial);
+    lift_norm_kernel<<<grid, dim3(BX, BY), 0, st>>>(g3, coef, u, partial);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
-    finish_norm(ns, grid.x * grid.y, slot, st);
+    return int(grid.x * grid.y);
 }
 
 #define MHS_INST(T)                                                                                          \
     template void launch_coef<T>(const Geom&, int, double, const mhs_xi_params&, PlaneCoef<T>*, cudaStream_t); \
     template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                                 \
     template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
-    template void launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*,            \
-                                     NormScratch*, int, cudaStream_t);                                         \
-    template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);               \
+    template int launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*, double*,    \
+                                    int, cudaStream_t);                                                        \
+    template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t);           \
     template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \
     template void launch_coarse<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
     template void launch_zero_interior<T>(const Geom&, int, T*, cudaStream_t);
@@ -570,10 +565,12 @@ __global__ void f2d_kernel(const float* __restrict__ s, double* __restrict__ d, 
 }  // namespace
 void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st) {
     d2f_kernel<<<152 * 8, 256, 0, st>>>(src, dst, n);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 void launch_f2d(const float* src, double* dst, size_t n, cudaStream_t st) {
     f2d_kernel<<<152 * 8, 256, 0, st>>>(src, dst, n);
+    count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 }  // namespace mhs

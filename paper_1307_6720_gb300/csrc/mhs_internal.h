@@ -20,6 +20,10 @@ struct Error : std::runtime_error {
 };
 
 void cuda_check(cudaError_t e, const char* what, const char* file, int line);
+
+// Process-wide count of kernels this library has launched (mhs_kernel_launches).
+void count_launches(long long n);
+long long launches();
 #define MHS_CUDA(call) ::mhs::cuda_check((call), #call, __FILE__, __LINE__)
 
 inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
@@ -63,7 +67,40 @@ struct Hierarchy {
     std::vector<Geom> g;                  // level geometries, 0 = finest
     std::vector<LevelArrays<double>> d;   // FP64 arrays
     std::vector<LevelArrays<float>> s;    // FP32 arrays
+    int cut64 = 0, cut32 = 0;             // first level handled by the one-CTA sub-cycle (per precision)
     int nlev() const { return int(g.size()); }
+};
+
+// Device-side control block of one iterative solve (lower-boundary or
+// interior): the convergence test runs on the device so that the whole
+// solve can be one CUDA graph with a conditional while node.
+struct SolveCtl {
+    double tol;        // stop when rel < tol
+    double bnorm;      // ||b||_2 of the lifted right-hand side
+    double rel0, rel;  // relative residual at the start / after the latest cycle
+    int max_cycles;
+    int cycles;
+    int status;        // MHS_OK or MHS_ERR_NONFINITE
+    int cont;          // 1 while another cycle is needed
+};
+
+// One level of a multigrid sub-hierarchy solved inside a single CTA.
+template <typename T>
+struct SubLevel {
+    Geom g;
+    const PlaneCoef<T>* coef;
+    int off_u, off_f;    // element offsets of u and f in dynamic shared memory
+};
+
+constexpr int MAX_SUB_LEVELS = 12;
+
+template <typename T>
+struct SubParams {
+    int nlev, dim, nu1, nu2;
+    SubLevel<T> L[MAX_SUB_LEVELS];
+    T* u_g;              // iterate of the top level in global memory (in/out)
+    const T* f_g;        // right-hand side of the top level in global memory
+    size_t smem_bytes;
 };
 
 // Device scratch for norms: per-block partial sums and the final values.
@@ -128,6 +165,12 @@ struct mhs_ctx {
     std::vector<void*> allocations;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     mhs::KernelTimer timer;
+    mhs::SolveCtl* ctl = nullptr;       // device control blocks [0] lower boundary, [1] interior
+    mhs::SolveCtl* ctl_host = nullptr;  // pinned mirror
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;  // private streams for graph capture
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};             // captured solve per precision mode
+    long long gkey[2] = {-1, -1};                              // options the graph was captured with
+    bool use_graphs = true;
 };
 
 namespace mhs {
@@ -142,11 +185,15 @@ template <typename T>
 void launch_fill(T* a, size_t n, T v, cudaStream_t st);
 template <typename T>
 void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
+// residual r = f - A u; with partial != nullptr also per-block partial sums
+// of r^2; returns the number of partials written
 template <typename T>
-void launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
-                     NormScratch* ns, int slot, cudaStream_t st);
+int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
+                    double* partial, int max_blocks, cudaStream_t st);
+// finish partial sums into *out (fixed order)
+void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t st);
 template <typename T>
-void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, cudaStream_t st);
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st);
 template <typename T>
 void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st);
 template <typename T>
@@ -154,16 +201,25 @@ void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
 // lower-boundary right-hand side f = -B_z at interior nodes (FP64 and FP32 copies)
 void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st);
 // mixed precision pieces
-void launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
-                            const double* f, float* r32, NormScratch* ns, int slot, cudaStream_t st);
+int launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
+                           const double* f, float* r32, double* partial, int max_blocks, cudaStream_t st);
 void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cudaStream_t st);
 template <typename T>
 void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st);
 void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st);
 void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st);
 // norm^2 of the lifted right-hand side of the interior problem: cz * P[k=0] on plane k=1
-void launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, NormScratch* ns, int slot,
-                      cudaStream_t st);
+int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, double* partial,
+                     cudaStream_t st);
+
+// ---- control and sub-cycle (kernels_ctl.cu) ----
+void launch_bnorm(const double* partial, int n, SolveCtl* ctl, cudaStream_t st);
+void launch_check(const double* partial, int n, SolveCtl* ctl, int first, cudaGraphConditionalHandle handle,
+                  int use_handle, cudaStream_t st);
+size_t subcycle_smem_limit();
+void subcycle_prepare();
+template <typename T>
+void launch_subcycle(const SubParams<T>& p, cudaStream_t st);
 
 // ---- fields (kernels_fields.cu) ----
 void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, const double* prof,

@@ -2,6 +2,7 @@
 // and the FP32-in-FP64 (defect correction) solves of Sect. 2.2 steps 2-3, and
 // field recovery (steps 4-5).  Every arithmetic step runs in the kernels of
 // kernels_mg.cu / kernels_fields.cu; this file only sequences launches.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,10 @@
 #include "solver.h"
 
 namespace mhs {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
     if (e != cudaSuccess) {
@@ -47,22 +52,39 @@ static void* dev_alloc(mhs_ctx* c, size_t bytes) {
     return p;
 }
 
+// Smallest level count handled by the one-CTA sub-cycle: the sub-hierarchy
+// from level l down must fit in shared memory (u and f per level) and the
+// level must be small enough that one SM sweeps it quickly (FP64 runs at a
+// small fraction of the FP32 rate on one SM, so its cut-off is lower).
+static int choose_cut(const Hierarchy& H, size_t elem, size_t max_interior) {
+    int cut = H.nlev() - 1;
+    for (int l = H.nlev() - 1; l >= 0; --l) {
+        size_t bytes = 0;
+        for (int m = l; m < H.nlev(); ++m) bytes += 2 * H.g[m].n * elem;
+        if (bytes > subcycle_smem_limit() || H.g[l].interior() > max_interior) break;
+        cut = l;
+    }
+    return cut;
+}
+
 static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
     H.dim = dim;
     int nx = c->nx, ny = c->ny, nz = dim == 3 ? c->nz : 1;
     for (;;) {
         H.g.push_back(make_geom(nx, ny, nz, c->Lx, c->Ly, c->Lz));
         const bool can = coarsenable(nx) && coarsenable(ny) && (dim == 2 || coarsenable(nz));
-        if (!can || H.g.size() == 24) break;
+        if (!can || H.g.size() == size_t(MAX_SUB_LEVELS)) break;
         nx = (nx - 1) / 2 + 1;
         ny = (ny - 1) / 2 + 1;
         if (dim == 3) nz = (nz - 1) / 2 + 1;
     }
     const Geom& gc = H.g.back();
-    if (2 * gc.n * sizeof(double) > 200 * 1024)
+    if (2 * gc.n * sizeof(double) > subcycle_smem_limit())
         throw Error(MHS_ERR_INVALID_ARG,
                     "coarsest multigrid level too large (" + std::to_string(gc.nx) + "x" + std::to_string(gc.ny) +
                         "x" + std::to_string(gc.nz) + "); use node counts of the form 2^k m + 1 with small m");
+    H.cut64 = choose_cut(H, sizeof(double), 1200);
+    H.cut32 = choose_cut(H, sizeof(float), 5000);
     for (const Geom& g : H.g) {
         LevelArrays<double> d;
         LevelArrays<float> s;
@@ -92,6 +114,9 @@ void compute_coefficients(mhs_ctx* c) {
 void create(mhs_ctx* c) {
     MHS_CUDA(cudaEventCreate(&c->ev0));
     MHS_CUDA(cudaEventCreate(&c->ev1));
+    MHS_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    MHS_CUDA(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
+    subcycle_prepare();
     build_hierarchy(c, c->h3, 3);
     build_hierarchy(c, c->h2, 2);
     c->ns.max_blocks = 65536;
@@ -100,21 +125,35 @@ void create(mhs_ctx* c) {
     MHS_CUDA(cudaMallocHost(&c->ns.host, 16 * sizeof(double)));
     c->flag = static_cast<int*>(dev_alloc(c, 16 * sizeof(int)));
     MHS_CUDA(cudaMallocHost(&c->flag_host, 16 * sizeof(int)));
+    c->ctl = static_cast<SolveCtl*>(dev_alloc(c, 2 * sizeof(SolveCtl)));
+    MHS_CUDA(cudaMallocHost(&c->ctl_host, 2 * sizeof(SolveCtl)));
     c->bz = static_cast<double*>(dev_alloc(c, c->h2.g[0].n * sizeof(double)));
     c->prof = static_cast<double*>(dev_alloc(c, 4 * size_t(c->nz) * sizeof(double)));
     compute_coefficients(c);
     MHS_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+void invalidate_graphs(mhs_ctx* c) {
+    for (int m = 0; m < 2; ++m) {
+        if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
+        c->gexec[m] = nullptr;
+        c->gkey[m] = -1;
+    }
+}
+
 void destroy(mhs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
+    invalidate_graphs(c);
     for (void* p : c->allocations) cudaFree(p);
     c->allocations.clear();
     if (c->ns.host) cudaFreeHost(c->ns.host);
     if (c->flag_host) cudaFreeHost(c->flag_host);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
     if (c->staging) cudaFree(c->staging);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     c->timer.destroy();
 }
 
@@ -128,8 +167,42 @@ template <>
 LevelArrays<float>& arrays<float>(Hierarchy& H, int l) { return H.s[l]; }
 
 template <typename T>
+static int cut_of(const Hierarchy& H) { return sizeof(T) == 8 ? H.cut64 : H.cut32; }
+
+// V-cycle from level l down; levels at or below the cut-off run in one CTA.
+template <typename T>
+void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
+    SubParams<T> p{};
+    p.nlev = H.nlev() - l;
+    p.dim = H.dim;
+    p.nu1 = c->opts.nu1;
+    p.nu2 = c->opts.nu2;
+    size_t off = 0;
+    for (int m = 0; m < p.nlev; ++m) {
+        const Geom& g = H.g[l + m];
+        p.L[m].g = g;
+        p.L[m].coef = arrays<T>(H, l + m).coef;
+        p.L[m].off_u = int(off);
+        off += round_up(g.n, 4);
+        p.L[m].off_f = int(off);
+        off += round_up(g.n, 4);
+    }
+    p.u_g = arrays<T>(H, l).u;
+    p.f_g = arrays<T>(H, l).f;
+    p.smem_bytes = off * sizeof(T);
+    if (p.smem_bytes > subcycle_smem_limit()) throw Error(MHS_ERR_INVALID_ARG, "sub-cycle does not fit shared memory");
+    const bool dbl = sizeof(T) == 8;
+    TimedScope t(c->timer, dbl ? MHS_KT_COARSE64 : MHS_KT_COARSE32, 2.0 * H.g[l].n * sizeof(T), 0.0, c->stream);
+    launch_subcycle<T>(p, c->stream);
+}
+
+template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
+    if (l >= cut_of<T>(H)) {
+        subcycle<T>(c, H, l);
+        return;
+    }
     LevelArrays<T>& A = arrays<T>(H, l);
     const Geom& g = H.g[l];
     const bool dbl = sizeof(T) == 8;
@@ -137,26 +210,20 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     // f vanishes on the finest FP64 interior level (the Dirichlet data sits in u)
     const double fs = (dbl && l == 0 && H.dim == 3 && c->f_zero_finest) ? 0.0 : s;
     const double upd_flops = H.dim == 3 ? 10.0 : 7.0;
-    if (l == H.nlev() - 1) {
-        TimedScope t(c->timer, dbl ? MHS_KT_COARSE64 : MHS_KT_COARSE32, 2.0 * g.n * s, 0.0, st);
-        launch_coarse<T>(g, H.dim, A.coef, A.u, A.f, st);
-        return;
-    }
     for (int q = 0; q < c->opts.nu1; ++q) {
         TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st);
         launch_smooth<T>(g, H.dim, A.coef, A.u, A.f, st);
     }
     {
         TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st);
-        launch_residual<T>(g, H.dim, A.coef, A.u, A.f, A.r, &c->ns, NORM_SCRATCH_SLOT, st);
+        launch_residual<T>(g, H.dim, A.coef, A.u, A.f, A.r, nullptr, 0, st);
     }
     LevelArrays<T>& C = arrays<T>(H, l + 1);
     const double Nc = double(H.g[l + 1].interior());
     {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + Nc) * s,
+        TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
                      Nc * (H.dim == 3 ? 54.0 : 18.0), st);
-        launch_restrict<T>(g, H.g[l + 1], H.dim, A.r, C.f, st);
-        MHS_CUDA(cudaMemsetAsync(C.u, 0, H.g[l + 1].n * sizeof(T), st));
+        launch_restrict<T>(g, H.g[l + 1], H.dim, A.r, C.f, C.u, st);
     }
     vcycle<T>(c, H, l + 1);
     {
@@ -179,93 +246,196 @@ double read_norm2(mhs_ctx* c, int slot) {
     return c->ns.host[slot];
 }
 
-// Solve A u = f on level 0 of H (u's boundary entries carry the Dirichlet
-// data) to ||f - A u|| < tol * bnorm.  Returns cycles (or outer steps).
-static int mg_solve(mhs_ctx* c, Hierarchy& H, int mode, double tol, double bnorm, double* rel_out,
-                    double* conv_out) {
-    cudaStream_t st = c->stream;
+// ------------------------- solve sequences ---------------------------------
+//
+// One solve = lower-boundary prologue, while(cond) {lower-boundary cycle},
+// interior prologue, while(cond) {interior cycle}.  The convergence test is
+// check_kernel on the device; in graph mode it drives the conditional while
+// nodes, in eager mode the host reads the control block after each check.
+
+struct Enq {
+    mhs_ctx* c;
+    int mode;
+    bool graph;
+    cudaGraphConditionalHandle hnd = 0;
+};
+
+// residual of the current iterate (FP64, or FP64 rounded into the FP32
+// right-hand side in mixed mode) with norm partials; returns their count
+static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
     const Geom& g = H.g[0];
     LevelArrays<double>& A = H.d[0];
-    LevelArrays<float>& S = H.s[0];
     const double N = double(g.interior());
     const double fb = (H.dim == 3 && c->f_zero_finest) ? 0.0 : 8.0;
     const double fl = H.dim == 3 ? 11.0 : 8.0;
-    auto residual_norm = [&]() {
-        if (mode == MHS_MIXED) {
-            TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + fb + 4.0), N * fl, st);
-            launch_residual_to_f32(g, H.dim, A.coef, A.u, A.f, S.f, &c->ns, NORM_RES_SLOT, st);
-        } else {
-            TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, st);
-            launch_residual<double>(g, H.dim, A.coef, A.u, A.f, A.r, &c->ns, NORM_RES_SLOT, st);
-        }
-        return std::sqrt(read_norm2(c, NORM_RES_SLOT));
-    };
-    double rn = residual_norm();
-    if (!std::isfinite(rn)) throw Error(MHS_ERR_NONFINITE, "non-finite residual norm");
-    double rel = bnorm > 0 ? rn / bnorm : 0.0;
-    const double rel0 = rel;
-    int cyc = 0;
-    while (bnorm > 0 && rel >= tol && cyc < c->opts.max_cycles) {
-        if (mode == MHS_MIXED) {
-            MHS_CUDA(cudaMemsetAsync(S.u, 0, g.n * sizeof(float), st));
-            for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
-            TimedScope t(c->timer, MHS_KT_CORRECT, N * 20.0, N, st);
-            launch_add_correction(g, H.dim, S.u, A.u, st);
-        } else {
-            vcycle<double>(c, H, 0);
-        }
-        ++cyc;
-        rn = residual_norm();
-        if (!std::isfinite(rn)) throw Error(MHS_ERR_NONFINITE, "non-finite residual norm");
-        rel = rn / bnorm;
+    if (mode == MHS_MIXED) {
+        TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + fb + 4.0), N * fl, c->stream);
+        return launch_residual_to_f32(g, H.dim, A.coef, A.u, A.f, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
     }
-    if (rel_out) *rel_out = rel;
-    if (conv_out) *conv_out = (cyc > 0 && rel0 > 0 && rel > 0) ? std::pow(rel / rel0, 1.0 / cyc) : 0.0;
-    return (bnorm > 0 && rel >= tol) ? -cyc - 1 : cyc;
+    TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream);
+    return launch_residual<double>(g, H.dim, A.coef, A.u, A.f, A.r, c->ns.partial, c->ns.max_blocks, c->stream);
+}
+
+static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
+    mhs_ctx* c = e.c;
+    const Geom& g = H.g[0];
+    if (e.mode == MHS_MIXED) {
+        MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
+        for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
+        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()), c->stream);
+        launch_add_correction(g, H.dim, H.s[0].u, H.d[0].u, c->stream);
+    } else {
+        vcycle<double>(c, H, 0);
+    }
+    const int nb = residual_partials(c, H, e.mode);
+    launch_check(c->ns.partial, nb, ctl, 0, e.hnd, e.graph ? 1 : 0, c->stream);
+}
+
+static void prologue_2d(const Enq& e) {
+    mhs_ctx* c = e.c;
+    Hierarchy& H = c->h2;
+    const Geom& g = H.g[0];
+    TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
+    MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
+    launch_lower_rhs(g, c->bz, H.d[0].f, c->stream);
+    // with u = 0 the residual is the right-hand side: its norm is ||b||
+    const int nb = residual_partials(c, H, e.mode);
+    launch_bnorm(c->ns.partial, nb, c->ctl + 0, c->stream);
+    launch_check(c->ns.partial, nb, c->ctl + 0, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+}
+
+static void prologue_3d(const Enq& e) {
+    mhs_ctx* c = e.c;
+    Hierarchy& H = c->h3;
+    const Geom& g = H.g[0];
+    TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
+    // P = 0 everywhere (Sect. 2.2, step 1), unless a warm start keeps the resident iterate
+    if (!(c->opts.flags & MHS_FLAG_WARM)) MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
+    launch_copy_plane(c->h2.g[0], c->h2.d[0].u, g, H.d[0].u, c->stream);
+    const int nl = launch_lift_norm(g, H.d[0].coef, H.d[0].u, c->ns.partial, c->stream);
+    launch_bnorm(c->ns.partial, nl, c->ctl + 1, c->stream);
+    const int nb = residual_partials(c, H, e.mode);
+    launch_check(c->ns.partial, nb, c->ctl + 1, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+}
+
+// Append a while node to the graph being captured on c->stream whose body
+// is captured from fn on the second capture stream.
+template <typename F>
+static void add_while(mhs_ctx* c, cudaGraphConditionalHandle hnd, F&& fn) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t graph;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    MHS_CUDA(cudaStreamGetCaptureInfo(c->stream, &status, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MHS_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    MHS_CUDA(cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t outer = c->stream;
+    c->stream = c->cap_stream2;
+    MHS_CUDA(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    fn();
+    cudaGraph_t captured;
+    MHS_CUDA(cudaStreamEndCapture(c->stream, &captured));
+    c->stream = outer;
+}
+
+static long long graph_key(mhs_ctx* c) {
+    return (long long)c->opts.nu1 | (long long)c->opts.nu2 << 8 | (long long)c->opts.inner_cycles << 16 |
+           (long long)(c->opts.flags & MHS_FLAG_WARM) << 24 | (long long)c->f_zero_finest << 25;
+}
+
+static void build_graph(mhs_ctx* c, int mode) {
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    try {
+        MHS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g;
+        MHS_CUDA(cudaStreamGetCaptureInfo(c->stream, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h2, h3;
+        MHS_CUDA(cudaGraphConditionalHandleCreate(&h2, g, 0, cudaGraphCondAssignDefault));
+        MHS_CUDA(cudaGraphConditionalHandleCreate(&h3, g, 0, cudaGraphCondAssignDefault));
+        Enq e2{c, mode, true, h2}, e3{c, mode, true, h3};
+        prologue_2d(e2);
+        add_while(c, h2, [&] { cycle_body(e2, c->h2, c->ctl + 0); });
+        prologue_3d(e3);
+        add_while(c, h3, [&] { cycle_body(e3, c->h3, c->ctl + 1); });
+        MHS_CUDA(cudaStreamEndCapture(c->stream, &graph));
+        MHS_CUDA(cudaGraphInstantiate(&c->gexec[mode], graph, 0));
+        cudaGraphDestroy(graph);
+    } catch (...) {
+        cudaGraph_t junk;
+        if (cudaStreamEndCapture(c->stream, &junk) == cudaSuccess && junk) cudaGraphDestroy(junk);
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        c->stream = user;
+        throw;
+    }
+    c->stream = user;
+    c->gkey[mode] = graph_key(c);
+}
+
+static bool read_cont(mhs_ctx* c, int which) {
+    MHS_CUDA(cudaMemcpyAsync(c->ctl_host + which, c->ctl + which, sizeof(SolveCtl), cudaMemcpyDeviceToHost, c->stream));
+    MHS_CUDA(cudaStreamSynchronize(c->stream));
+    return c->ctl_host[which].cont != 0;
 }
 
 mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     cudaStream_t st = c->stream;
+    for (int q = 0; q < 2; ++q) {
+        c->ctl_host[q] = SolveCtl{};
+        c->ctl_host[q].tol = tol;
+        c->ctl_host[q].max_cycles = c->opts.max_cycles;
+    }
+    MHS_CUDA(cudaMemcpyAsync(c->ctl, c->ctl_host, 2 * sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
     MHS_CUDA(cudaEventRecord(c->ev0, st));
-    // step 2: lower boundary, eq. (lower_bound), from P = 0 (step 1)
-    Hierarchy& H2 = c->h2;
-    const Geom& g2 = H2.g[0];
-    MHS_CUDA(cudaMemsetAsync(H2.d[0].u, 0, g2.n * sizeof(double), st));
-    launch_lower_rhs(g2, c->bz, H2.d[0].f, st);
-    // ||b|| of the 2D problem: residual of u = 0 is f
-    launch_residual<double>(g2, 2, H2.d[0].coef, H2.d[0].u, H2.d[0].f, H2.d[0].r, &c->ns, NORM_B_SLOT, st);
-    const double b2 = std::sqrt(read_norm2(c, NORM_B_SLOT));
-    double rel2 = 0, rel3 = 0, conv = 0;
-    int c2 = mg_solve(c, H2, mode, tol, b2, &rel2, nullptr);
-    // step 3: interior, eq. (scalar_pot), with the plane k = 0 from step 2
-    Hierarchy& H3 = c->h3;
-    const Geom& g3 = H3.g[0];
-    if (!(c->opts.flags & MHS_FLAG_WARM) || !c->have_solution)
-        MHS_CUDA(cudaMemsetAsync(H3.d[0].u, 0, g3.n * sizeof(double), st));
-    launch_copy_plane(g2, H2.d[0].u, g3, H3.d[0].u, st);
-    launch_lift_norm(g3, H3.d[0].coef, H3.d[0].u, &c->ns, NORM_B_SLOT, st);
-    const double b3 = std::sqrt(read_norm2(c, NORM_B_SLOT));
-    int c3 = mg_solve(c, H3, mode, tol, b3, &rel3, &conv);
+    const bool graph = c->use_graphs && !c->timer.enabled;
+    if (graph) {
+        if (!c->gexec[mode] || c->gkey[mode] != graph_key(c)) {
+            if (c->gexec[mode]) cudaGraphExecDestroy(c->gexec[mode]);
+            c->gexec[mode] = nullptr;
+            build_graph(c, mode);   // capture records work only; nothing runs until the launch
+        }
+        MHS_CUDA(cudaGraphLaunch(c->gexec[mode], st));
+    } else {
+        Enq e{c, mode, false, 0};
+        prologue_2d(e);
+        while (read_cont(c, 0)) cycle_body(e, c->h2, c->ctl + 0);
+        prologue_3d(e);
+        while (read_cont(c, 1)) cycle_body(e, c->h3, c->ctl + 1);
+    }
     MHS_CUDA(cudaEventRecord(c->ev1, st));
+    MHS_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl, 2 * sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
     MHS_CUDA(cudaEventSynchronize(c->ev1));
+    MHS_CUDA(cudaStreamSynchronize(st));
     float ms = 0;
     MHS_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    const bool ok = c2 >= 0 && c3 >= 0;
-    if (c2 < 0) c2 = -c2 - 1;
-    if (c3 < 0) c3 = -c3 - 1;
+    const SolveCtl& a = c->ctl_host[0];
+    const SolveCtl& b = c->ctl_host[1];
     if (info) {
-        info->cycles_2d = c2;
-        info->cycles_3d = c3;
-        info->rel_res_2d = rel2;
-        info->rel_res_3d = rel3;
-        info->conv_factor = conv;
+        info->cycles_2d = a.cycles;
+        info->cycles_3d = b.cycles;
+        info->rel_res_2d = a.rel;
+        info->rel_res_3d = b.rel;
+        info->conv_factor = (b.cycles > 0 && b.rel0 > 0 && b.rel > 0) ? std::pow(b.rel / b.rel0, 1.0 / b.cycles) : 0.0;
         info->ms = ms;
     }
     c->have_solution = true;
-    if (!ok) {
+    if (a.status != MHS_OK || b.status != MHS_OK) throw Error(MHS_ERR_NONFINITE, "non-finite residual norm");
+    const bool ok2 = a.bnorm == 0.0 || a.rel < tol;
+    const bool ok3 = b.bnorm == 0.0 || b.rel < tol;
+    if (!ok2 || !ok3) {
         char buf[256];
         std::snprintf(buf, sizeof buf, "no convergence to %g in %d cycles (2D rel %.3e, 3D rel %.3e)", tol,
-                      c->opts.max_cycles, rel2, rel3);
+                      c->opts.max_cycles, a.rel, b.rel);
         throw Error(MHS_ERR_NO_CONVERGENCE, buf);
     }
     return MHS_OK;

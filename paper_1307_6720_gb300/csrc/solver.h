@@ -14,6 +14,7 @@ constexpr int NORM_HOOK_SLOT = 3;     // level-hook residuals
 void create(mhs_ctx* c);
 void destroy(mhs_ctx* c);
 void compute_coefficients(mhs_ctx* c);
+void invalidate_graphs(mhs_ctx* c);
 mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info);
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l);

@@ -77,6 +77,12 @@ _SIGS = {
     "mhs_level_write": [_H, _I, _I, _I, _I, _P],
     "mhs_level_read": [_H, _I, _I, _I, _I, _P],
     "mhs_level_op": [_H, _I, _I, _I, _I],
+    "mhs_set_kernel_timing": [_H, _I],
+    "mhs_kernel_timing": [_H, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                          ctypes.POINTER(_D)],
+    "mhs_kernel_timing_reset": [_H],
+    "mhs_kernel_kind_name": [_I],
+    "mhs_kernel_launches": [],
     "mhs_status_string": [_I],
     "mhs_last_error": [],
     "mhs_version": [],
@@ -93,8 +99,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.argtypes = args
         if name == "mhs_destroy":
             fn.restype = None
-        elif name in ("mhs_status_string", "mhs_last_error", "mhs_version"):
+        elif name in ("mhs_status_string", "mhs_last_error", "mhs_version", "mhs_kernel_kind_name"):
             fn.restype = ctypes.c_char_p
+        elif name == "mhs_kernel_launches":
+            fn.restype = ctypes.c_longlong
         else:
             fn.restype = ctypes.c_int
     return lib
@@ -203,6 +211,31 @@ def mhs_level_read(h, dim, level, field, prec, dst) -> None:
 
 def mhs_level_op(h, dim, level, op, prec) -> None:
     _check(LIB.mhs_level_op(h, dim, level, op, prec))
+
+
+MHS_KT_COUNT = 14
+
+
+def mhs_set_kernel_timing(h, enable: bool) -> None:
+    _check(LIB.mhs_set_kernel_timing(h, 1 if enable else 0))
+
+
+def mhs_kernel_timing(h, kind: int) -> dict:
+    ms, n, b, f = _D(), ctypes.c_longlong(), _D(), _D()
+    _check(LIB.mhs_kernel_timing(h, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f)))
+    return dict(name=mhs_kernel_kind_name(kind), ms=ms.value, launches=n.value, bytes=b.value, flops=f.value)
+
+
+def mhs_kernel_timing_reset(h) -> None:
+    _check(LIB.mhs_kernel_timing_reset(h))
+
+
+def mhs_kernel_kind_name(kind: int) -> str:
+    return LIB.mhs_kernel_kind_name(kind).decode()
+
+
+def mhs_kernel_launches() -> int:
+    return int(LIB.mhs_kernel_launches())
 
 
 def mhs_status_string(s: int) -> str:

@@ -223,3 +223,40 @@ def test_mimetic_bz_divergence_free(M):
     assert np.abs(div).max() < 1e-9 * np.abs(got["Bz"]).max() / h
     want = oracle.fields(pr, exact.exact_solution(pr, bz), bz_mode=1)
     assert rel(got["Bz"], want["Bz"]) < 1e-10
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_and_eager_paths_agree_bitwise(M, mode):
+    """The captured solve (conditional while nodes, device-side convergence
+    test) and the eager launch sequence run the same kernels in the same
+    order: identical results, cycle counts and residuals."""
+    pr, bz = S.linear_mhs(65, seed=12)
+    out = []
+    for timing in (False, True):   # kernel timing forces the eager path
+        h = M.mhs_create(65, 65, 65, 1.0, 1.0, 1.0, pr["alpha"], _xi(M, pr))
+        M.mhs_set_kernel_timing(h, timing)
+        M.mhs_set_lower_bz(h, bz)
+        info = M.mhs_solve(h, 1e-10, mode)
+        phi = np.zeros((65, 65, 65))
+        M.mhs_get_phi(h, phi)
+        M.mhs_destroy(h)
+        out.append((info, phi))
+    (ia, pa), (ib, pb) = out
+    assert np.array_equal(pa, pb)
+    for k in ("cycles_2d", "cycles_3d", "rel_res_2d", "rel_res_3d"):
+        assert ia[k] == ib[k], k
+
+
+def test_repeated_graph_launches_and_option_changes(M):
+    pr, bz = S.linear_mhs(33, seed=13)
+    h = M.mhs_create(33, 33, 33, 1.0, 1.0, 1.0, pr["alpha"], _xi(M, pr))
+    M.mhs_set_lower_bz(h, bz)
+    a = M.mhs_solve(h, 1e-10)
+    b = M.mhs_solve(h, 1e-10)
+    assert a["cycles_3d"] == b["cycles_3d"] and a["rel_res_3d"] == b["rel_res_3d"]
+    M.mhs_set_options(h, nu1=1, nu2=1)           # re-captured with other sweep counts
+    c = M.mhs_solve(h, 1e-10)
+    assert c["cycles_3d"] > a["cycles_3d"] and c["rel_res_3d"] < 1e-10
+    e = M.mhs_solve(h, 1e-6)                      # tolerance lives in device memory, not in the graph
+    assert e["cycles_3d"] < c["cycles_3d"]
+    M.mhs_destroy(h)
