@@ -232,6 +232,33 @@ MHS_API mhs_status mhs_kernel_timing(mhs_handle h, int kind, double* total_ms, l
 MHS_API mhs_status mhs_kernel_timing_reset(mhs_handle h);
 MHS_API const char* mhs_kernel_kind_name(int kind);
 
+/* Allocation-free residual check (the paper has no counterpart; this is a
+ * service for callers that may not allocate device memory: applications
+ * whose device memory is owned entirely by their own pool allocator, and
+ * loops that cannot afford the device-wide synchronisation that cudaMalloc
+ * or cudaFree may imply).  It evaluates, for a caller-supplied potential P,
+ * the interior residual of eq. (scalar_pot) exactly as mhs_solve's stopping
+ * test does:
+ *   out[0] = ||b - A P||_2 over the interior nodes (the z = 0 plane of P is
+ *            the Dirichlet data, the other faces are taken from P as well),
+ *   out[1] = ||b||_2, b = the right-hand side after lifting the z = 0 data,
+ *   out[2] = out[0] / out[1] (0 when ||b|| = 0).
+ * P: device pointer, dense [nz][ny][nx] doubles; out: device pointer to 3
+ * doubles; stream: cudaStream_t (NULL = legacy default stream).  The call is
+ * asynchronous on that stream and allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  Its scratch is one fixed
+ * device array of about 176 KB inside the library, which every GPU that
+ * loads the library holds until the process exits.  Limits: nx, ny, nz >= 3
+ * and nz <= 4097 (MHS_ERR_INVALID_ARG beyond); P and out must be device
+ * pointers (MHS_ERR_INVALID_ARG otherwise).  The first call on each device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call
+ * shares the one scratch array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it, so serialise them. */
+MHS_API mhs_status mhs_interior_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                                                 double alpha, const mhs_xi_params* xi, const double* P,
+                                                 double* out, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 MHS_API const char* mhs_status_string(mhs_status s);
 

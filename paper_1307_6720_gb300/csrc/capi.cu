@@ -10,6 +10,11 @@
 #include "mhs_internal.h"
 #include "solver.h"
 
+namespace mhs {
+mhs_status interior_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                                     const mhs_xi_params* xi, const double* P, double* out, cudaStream_t st);
+}
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -429,6 +434,14 @@ const char* mhs_kernel_kind_name(int kind) {
                                               "restrict32", "prolong64", "prolong32", "coarse64", "coarse32",
                                               "residual_mixed", "correct", "fields", "other"};
     return (kind >= 0 && kind < MHS_KT_COUNT) ? names[kind] : "unknown";
+}
+
+mhs_status mhs_interior_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                                         const mhs_xi_params* xi, const double* P, double* out, void* stream) {
+    return guarded([&] {
+        return mhs::interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha, xi, P, out,
+                                              static_cast<cudaStream_t>(stream));
+    });
 }
 
 }  // extern "C"

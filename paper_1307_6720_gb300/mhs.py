@@ -83,6 +83,7 @@ _SIGS = {
     "mhs_kernel_timing_reset": [_H],
     "mhs_kernel_kind_name": [_I],
     "mhs_kernel_launches": [],
+    "mhs_interior_residual_noalloc": [_I, _I, _I, _D, _D, _D, _D, ctypes.POINTER(XiParams), _P, _P, _P],
     "mhs_status_string": [_I],
     "mhs_last_error": [],
     "mhs_version": [],
@@ -236,6 +237,14 @@ def mhs_kernel_kind_name(kind: int) -> str:
 
 def mhs_kernel_launches() -> int:
     return int(LIB.mhs_kernel_launches())
+
+
+def mhs_interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha, xi: XiParams | None, P, out, stream=None) -> None:
+    """Allocation-free residual check: out (3 device doubles) <- ||b - A P||, ||b||, their ratio."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(LIB.mhs_interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha,
+                                             ctypes.byref(xi) if xi is not None else None, ptr(P), ptr(out), stream))
 
 
 def mhs_status_string(s: int) -> str:
