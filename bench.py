@@ -194,6 +194,8 @@ def run_gpu(args):
     xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
     h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
     M.mhs_set_stream(h, stream)
+    if args.eager:
+        M.mhs_set_options(h, flags=M.MHS_FLAG_NO_GRAPH)
     shape = (pr["nz"], pr["ny"], pr["nx"])
     bz_dev = [torch.from_numpy(b).to(dev) for b in mags]
     outs_dev = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(6)]
@@ -240,6 +242,12 @@ def run_gpu(args):
     launches = M.mhs_kernel_launches() - l0
     unknowns = S.unknowns(pr)
     value = unknowns * world / (ms * 1e-3)
+    if args.light:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms, "light": True,
+                              "gpu_launches": int(launches), "config": cfg}))
+        M.mhs_destroy(h)
+        return
 
     # per-kernel durations over a second, identical timed pass with event instrumentation
     M.mhs_set_kernel_timing(h, True)
@@ -309,6 +317,33 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_op(args):
+    """One finest-level operation of the 129^3 interior hierarchy, repeated; prints its mean device time."""
+    import numpy as np
+    import torch
+    from paper_1307_6720_gb300 import mhs as M
+    pr, mags, cfg = workload(0)
+    xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
+    h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
+    M.mhs_set_stream(h, torch.cuda.current_stream())
+    prec = M.MHS_FP64 if args.prec == "fp64" else M.MHS_MIXED
+    rng = np.random.default_rng(0)
+    shape = (pr["nz"], pr["ny"], pr["nx"])
+    for field in (M.MHS_FIELD_U, M.MHS_FIELD_F, M.MHS_FIELD_R):
+        M.mhs_level_write(h, 3, 0, field, prec, rng.standard_normal(shape))
+    op = {"smooth": M.MHS_OP_SMOOTH, "residual": M.MHS_OP_RESIDUAL, "restrict": M.MHS_OP_RESTRICT,
+          "prolong": M.MHS_OP_PROLONG, "vcycle": M.MHS_OP_VCYCLE}[args.op]
+    for _ in range(args.warmup):
+        M.mhs_level_op(h, 3, 0, op, prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        M.mhs_level_op(h, 3, 0, op, prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"op": args.op, "prec": args.prec, "ms_per_op_wall": (time.perf_counter() - t0) * 1e3 / args.steps}))
+    M.mhs_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,11 +352,20 @@ def main():
     ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--impl", choices=["mhs", "reference"], default="mhs")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--light", action="store_true",
+                    help="timed steps only (no CPU baseline, e2e, kernel timing or second mode): for launch lists")
+    ap.add_argument("--op", choices=["smooth", "residual", "restrict", "prolong", "vcycle"], default=None,
+                    help="repeat one finest-level operation of the interior hierarchy (--steps times) for kernel capture")
+    ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="precision of --op")
+    ap.add_argument("--eager", action="store_true",
+                    help="host-driven kernel-by-kernel solve instead of the captured graph (for launch lists)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mhs":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.op:
+        run_op(args)
     else:
         run_gpu(args)
 

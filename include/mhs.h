@@ -102,11 +102,17 @@ typedef struct {
     int max_cycles;      /* V-cycles (FP64 mode) or outer steps (mixed mode) per solve [100] */
     int inner_cycles;    /* FP32 V-cycles per outer step in mixed mode [1] */
     int flags;           /* MHS_FLAG_* bits */
+    int cut64;           /* FP64: largest interior node count of a level solved, with all coarser levels, by
+                            the one-CTA shared-memory sub-cycle [1200] */
+    int cut32;           /* same for FP32 levels [4000] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
 #define MHS_FLAG_BZ_MIMETIC 2   /* B_z = -(D_x D_x + D_y D_y) P with the first-difference operators,
                                    which makes the central-difference div B vanish to rounding */
+#define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
+                                   one captured CUDA graph (same kernels, same results; for profilers that cannot
+                                   see kernels inside conditional graph nodes) */
 
 typedef struct {
     int cycles_2d;       /* V-cycles (or outer steps) of the lower-boundary solve */
@@ -156,6 +162,21 @@ MHS_API mhs_status mhs_set_lower_bz(mhs_handle h, const double* bz);
  * MHS_ERR_NO_CONVERGENCE (P is still the last iterate and usable),
  * MHS_ERR_NONFINITE, MHS_ERR_CUDA. */
 MHS_API mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info* info);
+
+/* Batched solves (independent instances, any mix of grid sizes and
+ * parameters): runs mhs_solve(hs[q], tol, mode, ...) for q < n with every
+ * instance on its own internal stream, so that the instances' captured
+ * solves overlap on the GPU, and returns when all have finished.  Each
+ * instance runs exactly the kernels of its solo solve: results are bitwise
+ * identical to solving it alone.  infos and statuses (each n entries) may be
+ * NULL; statuses[q] receives the per-instance status.  The return value is
+ * MHS_OK or the first failing instance's status.  Work already queued on a
+ * handle's own stream is ordered before its batch solve.  Each handle may
+ * appear once.  Errors: MHS_ERR_INVALID_ARG, MHS_ERR_BAD_STATE (an instance
+ * without B_z), per-instance MHS_ERR_NO_CONVERGENCE / MHS_ERR_NONFINITE,
+ * MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solve_info* infos,
+                                   mhs_status* statuses);
 
 /* Copy P (the poloidal potential of eq. b_iden), [nz][ny][nx], to phi (host
  * or device).  Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_INVALID_ARG. */

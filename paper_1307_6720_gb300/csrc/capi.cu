@@ -50,7 +50,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -59,6 +59,8 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->nu2 > 0) o->nu2 = in->nu2;
     if (in->max_cycles > 0) o->max_cycles = in->max_cycles;
     if (in->inner_cycles > 0) o->inner_cycles = in->inner_cycles;
+    if (in->cut64 > 0) o->cut64 = in->cut64;
+    if (in->cut32 > 0) o->cut32 = in->cut32;
     o->flags = in->flags;
 }
 
@@ -209,6 +211,7 @@ mhs_status mhs_set_options(mhs_handle h, const mhs_solver_opts* opts) {
     fill_opts(&h->opts, opts);
     return guarded([&] {
         mhs::invalidate_graphs(h);
+        mhs::choose_cuts(h);
         return MHS_OK;
     });
 }
@@ -255,6 +258,20 @@ mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info* info) {
     if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
     if (!h->have_bz) return fail(MHS_ERR_BAD_STATE, "mhs_set_lower_bz must come before mhs_solve");
     return guarded([&] { return mhs::solve(h, tol, mode, info); });
+}
+
+mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solve_info* infos,
+                           mhs_status* statuses) {
+    if (!hs || n < 0) return fail(MHS_ERR_INVALID_ARG, "bad handle array");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(MHS_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
+    for (int q = 0; q < n; ++q) {
+        if (!hs[q]) return fail(MHS_ERR_INVALID_ARG, "NULL handle in batch");
+        if (!hs[q]->have_bz) return fail(MHS_ERR_BAD_STATE, "every handle needs mhs_set_lower_bz before a batch");
+        for (int r = 0; r < q; ++r)
+            if (hs[r] == hs[q]) return fail(MHS_ERR_INVALID_ARG, "a handle appears twice in the batch");
+    }
+    return guarded([&] { return mhs::batch_solve(hs, n, tol, mode, infos, statuses); });
 }
 
 mhs_status mhs_get_phi(mhs_handle h, double* phi) {

@@ -96,37 +96,133 @@ __device__ double D1D1(const Geom& g, const double* P, int i, int j, int k, int 
     return v;
 }
 
-__global__ void field_b_kernel(Geom g, double alpha, double inv2mu0, const double* __restrict__ prof,
-                               const double* __restrict__ P, double* __restrict__ Bx, double* __restrict__ By,
-                               double* __restrict__ Bz, double* __restrict__ p, int bz_mode) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    for (int k = blockIdx.z; k < g.nz; k += gridDim.z) {
+// Per-plane constants: prof[8k + ...] = xi, xi', p_b, rho_b, xi/(2 mu0),
+// xi'/(2 mu0 g), xi/(mu0 g).
+// Generic (face) path for node (i,j,k): any position, one-sided stencils where needed.
+__device__ void field_b_node(const Geom& g, double alpha, const double* __restrict__ prof, const double* __restrict__ P,
+                             double* __restrict__ Bx, double* __restrict__ By, double* __restrict__ Bz,
+                             double* __restrict__ p, int bz_mode, int i, int j, int k) {
+    const size_t o = at(g, i, j, k);
+    const double bx = alpha * D1(g, P, i, j, k, 1) + D1z_then(g, P, i, j, k, 0);
+    const double by = -alpha * D1(g, P, i, j, k, 0) + D1z_then(g, P, i, j, k, 1);
+    const double bz = bz_mode == 1 ? -(D1D1(g, P, i, j, k, 0) + D1D1(g, P, i, j, k, 1))
+                                   : -(D2(g, P, i, j, k, 0) + D2(g, P, i, j, k, 1));
+    Bx[o] = bx;
+    By[o] = by;
+    Bz[o] = bz;
+    p[o] = fma(-prof[8 * k + 4], bz * bz, prof[8 * k + 2]);
+}
+
+__device__ void field_rho_node(const Geom& g, const double* __restrict__ prof, const double* __restrict__ Bx,
+                               const double* __restrict__ By, const double* __restrict__ Bz, double* __restrict__ rho,
+                               int i, int j, int k) {
+    const size_t o = at(g, i, j, k);
+    const double bz = Bz[o];
+    const double bgb = fma(Bx[o], D1(g, Bz, i, j, k, 0), fma(By[o], D1(g, Bz, i, j, k, 1), bz * D1(g, Bz, i, j, k, 2)));
+    rho[o] = fma(prof[8 * k + 5], bz * bz, fma(prof[8 * k + 6], bgb, prof[8 * k + 3]));
+}
+
+// Boundary nodes (the six faces), enumerated as a flat list so that every
+// warp runs the generic path together: planes k = 0 and nz-1, then rows
+// j = 0 and ny-1 of the inner planes, then columns i = 0 and nx-1 of the
+// remaining nodes.
+__device__ bool face_node(const Geom& g, long long q, int& i, int& j, int& k) {
+    const long long pl = (long long)g.nx * g.ny;
+    if (q < 2 * pl) {
+        k = q < pl ? 0 : g.nz - 1;
+        const long long r = q % pl;
+        i = int(r % g.nx);
+        j = int(r / g.nx);
+        return true;
+    }
+    q -= 2 * pl;
+    const long long rows = (long long)(g.nz - 2) * 2 * g.nx;
+    if (q < rows) {
+        k = 1 + int(q / (2 * g.nx));
+        const int r = int(q % (2 * g.nx));
+        j = r < g.nx ? 0 : g.ny - 1;
+        i = r % g.nx;
+        return true;
+    }
+    q -= rows;
+    const long long cols = (long long)(g.nz - 2) * (g.ny - 2) * 2;
+    if (q < cols) {
+        k = 1 + int(q / (2 * (g.ny - 2)));
+        const int r = int(q % (2 * (g.ny - 2)));
+        j = 1 + r / 2;
+        i = (r & 1) ? g.nx - 1 : 0;
+        return true;
+    }
+    return false;
+}
+
+__global__ void field_b_face_kernel(Geom g, double alpha, const double* __restrict__ prof, const double* __restrict__ P,
+                                    double* __restrict__ Bx, double* __restrict__ By, double* __restrict__ Bz,
+                                    double* __restrict__ p, int bz_mode) {
+    int i, j, k;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; face_node(g, q, i, j, k);
+         q += (long long)gridDim.x * blockDim.x)
+        field_b_node(g, alpha, prof, P, Bx, By, Bz, p, bz_mode, i, j, k);
+}
+
+__global__ void field_rho_face_kernel(Geom g, const double* __restrict__ prof, const double* __restrict__ Bx,
+                                      const double* __restrict__ By, const double* __restrict__ Bz,
+                                      double* __restrict__ rho) {
+    int i, j, k;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; face_node(g, q, i, j, k);
+         q += (long long)gridDim.x * blockDim.x)
+        field_rho_node(g, prof, Bx, By, Bz, rho, i, j, k);
+}
+
+// Inner nodes (1 <= i, j, k <= n-2): fixed central stencils.
+__global__ void field_b_kernel(Geom g, double alpha, const double* __restrict__ prof, const double* __restrict__ P,
+                               double* __restrict__ Bx, double* __restrict__ By, double* __restrict__ Bz,
+                               double* __restrict__ p, int bz_mode) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const ptrdiff_t sx = 1, sy = g.px, sz = (ptrdiff_t)g.plane;
+    const double ax = alpha / (2.0 * g.hy), ay = alpha / (2.0 * g.hx);   // alpha d/dy, alpha d/dx
+    const double mxz = 1.0 / (4.0 * g.hx * g.hz), myz = 1.0 / (4.0 * g.hy * g.hz);
+    const double cx = 1.0 / (g.hx * g.hx), cy = 1.0 / (g.hy * g.hy);
+    for (int k = 1 + blockIdx.z; k <= g.nz - 2; k += gridDim.z) {
         const size_t o = at(g, i, j, k);
-        const double bx = alpha * D1(g, P, i, j, k, 1) + D1z_then(g, P, i, j, k, 0);
-        const double by = -alpha * D1(g, P, i, j, k, 0) + D1z_then(g, P, i, j, k, 1);
-        const double bz = bz_mode == 1 ? -(D1D1(g, P, i, j, k, 0) + D1D1(g, P, i, j, k, 1))
-                                       : -(D2(g, P, i, j, k, 0) + D2(g, P, i, j, k, 1));
+        double bx, by, bz;
+        if (bz_mode == 0) {
+            const double* q = P + o;
+            const double pxz = ((q[sx + sz] - q[sx - sz]) - (q[-sx + sz] - q[-sx - sz])) * mxz;
+            const double pyz = ((q[sy + sz] - q[sy - sz]) - (q[-sy + sz] - q[-sy - sz])) * myz;
+            bx = fma(ax, q[sy] - q[-sy], pxz);
+            by = fma(-ay, q[sx] - q[-sx], pyz);
+            const double c = q[0];
+            bz = -fma(cx, fma(-2.0, c, q[sx] + q[-sx]), cy * fma(-2.0, c, q[sy] + q[-sy]));
+        } else {
+            field_b_node(g, alpha, prof, P, Bx, By, Bz, p, bz_mode, i, j, k);
+            continue;
+        }
         Bx[o] = bx;
         By[o] = by;
         Bz[o] = bz;
-        p[o] = prof[4 * k + 2] - prof[4 * k + 0] * bz * bz * inv2mu0;
+        p[o] = fma(-prof[8 * k + 4], bz * bz, prof[8 * k + 2]);
     }
 }
 
-__global__ void field_rho_kernel(Geom g, double inv2mu0, double invmu0, double invg, const double* __restrict__ prof,
-                                 const double* __restrict__ Bx, const double* __restrict__ By,
-                                 const double* __restrict__ Bz, double* __restrict__ rho) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    for (int k = blockIdx.z; k < g.nz; k += gridDim.z) {
+__global__ void field_rho_kernel(Geom g, const double* __restrict__ prof, const double* __restrict__ Bx,
+                                 const double* __restrict__ By, const double* __restrict__ Bz,
+                                 double* __restrict__ rho) {
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const double dx = 1.0 / (2.0 * g.hx), dy = 1.0 / (2.0 * g.hy), dz = 1.0 / (2.0 * g.hz);
+    for (int k = 1 + blockIdx.z; k <= g.nz - 2; k += gridDim.z) {
         const size_t o = at(g, i, j, k);
         const double bz = Bz[o];
-        const double bgb = Bx[o] * D1(g, Bz, i, j, k, 0) + By[o] * D1(g, Bz, i, j, k, 1) + bz * D1(g, Bz, i, j, k, 2);
-        const double xi = prof[4 * k + 0], dxi = prof[4 * k + 1], rb = prof[4 * k + 3];
-        rho[o] = rb + (dxi * bz * bz * inv2mu0 + xi * bgb * invmu0) * invg;
+        const double* q = Bz + o;
+        const double gx = (q[1] - q[-1]) * dx;
+        const double gy = (q[g.px] - q[-(ptrdiff_t)g.px]) * dy;
+        const double gz = (q[g.plane] - q[-(ptrdiff_t)g.plane]) * dz;
+        const double bgb = fma(Bx[o], gx, fma(By[o], gy, bz * gz));
+        rho[o] = fma(prof[8 * k + 5], bz * bz, fma(prof[8 * k + 6], bgb, prof[8 * k + 3]));
     }
 }
 
@@ -135,14 +231,22 @@ __global__ void field_rho_kernel(Geom g, double inv2mu0, double invmu0, double i
 void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, const double* prof, const double* P,
                    double* Bx, double* By, double* Bz, double* p, double* rho, int bz_mode, cudaStream_t st) {
     const dim3 blk(32, 8);
-    int gz = g.nz;
+    int gz = g.nz - 2;
     if (gz > 65535) gz = 65535;
-    const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, gz);
-    const double inv2mu0 = 1.0 / (2.0 * atm.mu0);
-    field_b_kernel<<<grid, blk, 0, st>>>(g, alpha, inv2mu0, prof, P, Bx, By, Bz, p, bz_mode);
+    const dim3 grid((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, gz);
+    const long long faces = 2LL * g.nx * g.ny + 2LL * (g.nz - 2) * g.nx + 2LL * (g.nz - 2) * (g.ny - 2);
+    const int fblocks = int((faces + 255) / 256 < 152 * 16 ? (faces + 255) / 256 : 152 * 16);
+    (void)atm;
+    field_b_kernel<<<grid, blk, 0, st>>>(g, alpha, prof, P, Bx, By, Bz, p, bz_mode);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
-    field_rho_kernel<<<grid, blk, 0, st>>>(g, inv2mu0, 1.0 / atm.mu0, 1.0 / atm.g, prof, Bx, By, Bz, rho);
+    field_b_face_kernel<<<fblocks, 256, 0, st>>>(g, alpha, prof, P, Bx, By, Bz, p, bz_mode);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+    field_rho_kernel<<<grid, blk, 0, st>>>(g, prof, Bx, By, Bz, rho);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+    field_rho_face_kernel<<<fblocks, 256, 0, st>>>(g, prof, Bx, By, Bz, rho);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }

@@ -60,7 +60,7 @@ __global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, Pla
         cz = 0.0;
         d = -2.0 * (cx + cy);
     }
-    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d)};
+    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d), T(cx / d), T(cy / d), T(cz / d)};
 }
 
 // Background atmosphere: T_b piecewise (1, T_cor^((z-z1)/(z2-z1)), T_cor);
@@ -85,16 +85,23 @@ __device__ void background(const mhs_atmos_params& a, double z, double* pb, doub
     *rhob = p / T;
 }
 
+// per plane: xi, xi', p_b, rho_b and the folded field-recovery constants
+// xi/(2 mu0) (eq. pressure), xi'/(2 mu0 g) and xi/(mu0 g) (eq. density)
 __global__ void profile_kernel(Geom g, mhs_xi_params xi, mhs_atmos_params atm, double* prof) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.nz) return;
     const double z = k * g.hz;
     double pb, rb;
     background(atm, z, &pb, &rb);
-    prof[4 * k + 0] = xi_of(xi, z);
-    prof[4 * k + 1] = dxi_of(xi, z);
-    prof[4 * k + 2] = pb;
-    prof[4 * k + 3] = rb;
+    const double x = xi_of(xi, z), dx = dxi_of(xi, z);
+    prof[8 * k + 0] = x;
+    prof[8 * k + 1] = dx;
+    prof[8 * k + 2] = pb;
+    prof[8 * k + 3] = rb;
+    prof[8 * k + 4] = x / (2.0 * atm.mu0);
+    prof[8 * k + 5] = dx / (2.0 * atm.mu0 * atm.g);
+    prof[8 * k + 6] = x / (atm.mu0 * atm.g);
+    prof[8 * k + 7] = 0.0;
 }
 
 template <typename T>
@@ -120,10 +127,11 @@ __global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* 
         if (i > g.nx - 2) continue;
         const PlaneCoef<T> c = coef[k];
         const size_t o = at(g, i, j, k);
-        T off = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]);
-        if (D3) off += c.cz * (u[o + g.plane] + u[o - g.plane]);
-        const T rhs = f ? f[o] : T(0);
-        u[o] = (rhs - off) * c.inv_d;
+        // u = f/d - ax (E + W) - ay (N + S) - az (U + D); f == nullptr means f = 0
+        T v = f ? f[o] * c.inv_d : T(0);
+        if (D3) v = fma(-c.az, u[o + g.plane] + u[o - g.plane], v);
+        v = fma(-c.ay, u[o + g.px] + u[o - g.px], v);
+        u[o] = fma(-c.ax, u[o + 1] + u[o - 1], v);
     }
 }
 
@@ -216,23 +224,37 @@ __global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* _
 }
 
 // u_f += I u_c at fine interior nodes: along each axis an even fine index
-// takes coarse node i/2, an odd one the mean of (i-1)/2 and (i+1)/2.
+// takes coarse node i/2, an odd one the mean of (i-1)/2 and (i+1)/2.  One
+// thread per coarse cell (I..I+1, J..J+1, K..K+1) produces its 8 (2D: 4)
+// fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, sharing the partial sums
+// of the corner values; an even fine index is interior only when its coarse
+// index is >= 1.
 template <typename T, bool D3>
 __global__ void prolong_kernel(Geom gc, Geom gf, const T* __restrict__ uc, T* __restrict__ uf) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > gf.nx - 2 || j > gf.ny - 2) return;
-    const int I0 = i >> 1, I1 = (i + 1) >> 1;
-    const int J0 = j >> 1, J1 = (j + 1) >> 1;
-    for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? gf.nz - 2 : 0); k += gridDim.z) {
-        const int K0 = k >> 1, K1 = (k + 1) >> 1;
-        auto plane = [&](int K) {
-            const T a = uc[at(gc, I0, J0, K)] + uc[at(gc, I1, J0, K)];
-            const T b = uc[at(gc, I0, J1, K)] + uc[at(gc, I1, J1, K)];
-            return T(0.25) * (a + b);   // (i,j) bilinear with the duplicates of even indices
-        };
-        T v = D3 ? T(0.5) * (plane(K0) + plane(K1)) : plane(0);
-        uf[at(gf, i, j, k)] += v;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    const ptrdiff_t cx = 1, cy = gc.px, cz = (ptrdiff_t)gc.plane;
+    const ptrdiff_t fx = 1, fy = gf.px, fz = (ptrdiff_t)gf.plane;
+    const bool ex = I >= 1, ey = J >= 1;
+    for (int K = D3 ? blockIdx.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gridDim.z) {
+        const T* c = uc + at(gc, I, J, K);
+        T* f = uf + at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
+        const T c000 = c[0], c100 = c[cx], c010 = c[cy], c110 = c[cx + cy];
+        const T e100 = c000 + c100, e010 = c000 + c010, e110 = e100 + (c010 + c110);
+        const bool ez = !D3 || K >= 1;
+        if (ex && ey && ez) f[0] += c000;
+        if (ey && ez) f[fx] = fma(T(0.5), e100, f[fx]);
+        if (ex && ez) f[fy] = fma(T(0.5), e010, f[fy]);
+        if (ez) f[fx + fy] = fma(T(0.25), e110, f[fx + fy]);
+        if (D3) {
+            const T c001 = c[cz], c101 = c[cx + cz], c011 = c[cy + cz], c111 = c[cx + cy + cz];
+            const T s01 = c001 + c101, s02 = c001 + c011;
+            if (ex && ey) f[fz] = fma(T(0.5), c000 + c001, f[fz]);
+            if (ey) f[fx + fz] = fma(T(0.25), e100 + s01, f[fx + fz]);
+            if (ex) f[fy + fz] = fma(T(0.25), e010 + s02, f[fy + fz]);
+            f[fx + fy + fz] = fma(T(0.125), e110 + (s01 + (c011 + c111)), f[fx + fy + fz]);
+        }
     }
 }
 
@@ -465,7 +487,11 @@ void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc
 template <typename T>
 void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = grid_for(gf, d3, gf.nx - 2, 0);
+    // one thread per coarse cell: (nc - 1) cells per axis
+    Geom cells = gc;
+    cells.ny = gc.ny + 1;   // grid_for covers ny - 2 rows; cells need ny - 1
+    cells.nz = gc.nz + 1;
+    const dim3 grid = grid_for(cells, d3, gc.nx - 1, 0);
     if (d3) prolong_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
     else prolong_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
     count_launches(1);

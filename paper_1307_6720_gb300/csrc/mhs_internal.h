@@ -34,9 +34,11 @@ inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 // d_k = -2 (cx_k + cy_k + cz) + alpha^2; inv_d = 1/d_k.
 // For the lower-boundary operator of eq. (lower_bound): one plane with
 // xi = 0, cz = 0, alpha = 0.
+// ax = cx/d, ay = cy/d, az = cz/d let a Gauss-Seidel update be written as
+// u = f/d - ax (u_E + u_W) - ay (u_N + u_S) - az (u_U + u_D).
 template <typename T>
 struct PlaneCoef {
-    T cx, cy, cz, d, inv_d;
+    T cx, cy, cz, d, inv_d, ax, ay, az;
 };
 
 // Geometry of one level.  Device arrays are pitched: element (i,j,k) at
@@ -155,7 +157,7 @@ struct mhs_ctx {
     mhs::Hierarchy h3, h2;
     mhs::NormScratch ns;
     double* bz = nullptr;          // lower-boundary field [ny x px] (device, pitched)
-    double* prof = nullptr;        // per fine plane: xi, dxi, p_b, rho_b (4*nz doubles, device)
+    double* prof = nullptr;        // per fine plane: xi, dxi, p_b, rho_b and folded constants (8*nz doubles, device)
     int* flag = nullptr;           // device flags (non-finite input detection)
     int* flag_host = nullptr;      // pinned mirror
     double* staging = nullptr;     // FP64 staging buffer of the finest size (level hooks, lazily allocated)
@@ -170,7 +172,10 @@ struct mhs_ctx {
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;  // private streams for graph capture
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};             // captured solve per precision mode
     long long gkey[2] = {-1, -1};                              // options the graph was captured with
+    long long gcount[2][4] = {};                               // kernels per graph section (see build_graph)
     bool use_graphs = true;
+    bool pending_graph = false;                                 // the enqueued solve is a graph launch
+    cudaStream_t bstream = nullptr;                             // stream of this handle inside batched solves
 };
 
 namespace mhs {

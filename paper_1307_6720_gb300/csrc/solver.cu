@@ -83,8 +83,6 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
         throw Error(MHS_ERR_INVALID_ARG,
                     "coarsest multigrid level too large (" + std::to_string(gc.nx) + "x" + std::to_string(gc.ny) +
                         "x" + std::to_string(gc.nz) + "); use node counts of the form 2^k m + 1 with small m");
-    H.cut64 = choose_cut(H, sizeof(double), 1200);
-    H.cut32 = choose_cut(H, sizeof(float), 5000);
     for (const Geom& g : H.g) {
         LevelArrays<double> d;
         LevelArrays<float> s;
@@ -98,6 +96,13 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
         s.coef = static_cast<PlaneCoef<float>*>(dev_alloc(c, g.nz * sizeof(PlaneCoef<float>)));
         H.d.push_back(d);
         H.s.push_back(s);
+    }
+}
+
+void choose_cuts(mhs_ctx* c) {
+    for (Hierarchy* H : {&c->h3, &c->h2}) {
+        H->cut64 = choose_cut(*H, sizeof(double), size_t(c->opts.cut64));
+        H->cut32 = choose_cut(*H, sizeof(float), size_t(c->opts.cut32));
     }
 }
 
@@ -119,6 +124,7 @@ void create(mhs_ctx* c) {
     subcycle_prepare();
     build_hierarchy(c, c->h3, 3);
     build_hierarchy(c, c->h2, 2);
+    choose_cuts(c);
     c->ns.max_blocks = 65536;
     c->ns.partial = static_cast<double*>(dev_alloc(c, c->ns.max_blocks * sizeof(double)));
     c->ns.result = static_cast<double*>(dev_alloc(c, 16 * sizeof(double)));
@@ -128,7 +134,7 @@ void create(mhs_ctx* c) {
     c->ctl = static_cast<SolveCtl*>(dev_alloc(c, 2 * sizeof(SolveCtl)));
     MHS_CUDA(cudaMallocHost(&c->ctl_host, 2 * sizeof(SolveCtl)));
     c->bz = static_cast<double*>(dev_alloc(c, c->h2.g[0].n * sizeof(double)));
-    c->prof = static_cast<double*>(dev_alloc(c, 4 * size_t(c->nz) * sizeof(double)));
+    c->prof = static_cast<double*>(dev_alloc(c, 8 * size_t(c->nz) * sizeof(double)));
     compute_coefficients(c);
     MHS_CUDA(cudaStreamSynchronize(c->stream));
 }
@@ -154,6 +160,7 @@ void destroy(mhs_ctx* c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->bstream) cudaStreamDestroy(c->bstream);
     c->timer.destroy();
 }
 
@@ -208,15 +215,17 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     const bool dbl = sizeof(T) == 8;
     const double s = sizeof(T), N = double(g.interior());
     // f vanishes on the finest FP64 interior level (the Dirichlet data sits in u)
-    const double fs = (dbl && l == 0 && H.dim == 3 && c->f_zero_finest) ? 0.0 : s;
+    const bool f_zero = dbl && l == 0 && H.dim == 3 && c->f_zero_finest;
+    const double fs = f_zero ? 0.0 : s;
+    const T* f = f_zero ? nullptr : A.f;
     const double upd_flops = H.dim == 3 ? 10.0 : 7.0;
     for (int q = 0; q < c->opts.nu1; ++q) {
         TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st);
-        launch_smooth<T>(g, H.dim, A.coef, A.u, A.f, st);
+        launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
     }
     {
         TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st);
-        launch_residual<T>(g, H.dim, A.coef, A.u, A.f, A.r, nullptr, 0, st);
+        launch_residual<T>(g, H.dim, A.coef, A.u, f, A.r, nullptr, 0, st);
     }
     LevelArrays<T>& C = arrays<T>(H, l + 1);
     const double Nc = double(H.g[l + 1].interior());
@@ -232,7 +241,7 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     }
     for (int q = 0; q < c->opts.nu2; ++q) {
         TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st);
-        launch_smooth<T>(g, H.dim, A.coef, A.u, A.f, st);
+        launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
     }
 }
 
@@ -363,10 +372,22 @@ static void build_graph(mhs_ctx* c, int mode) {
         MHS_CUDA(cudaGraphConditionalHandleCreate(&h2, g, 0, cudaGraphCondAssignDefault));
         MHS_CUDA(cudaGraphConditionalHandleCreate(&h3, g, 0, cudaGraphCondAssignDefault));
         Enq e2{c, mode, true, h2}, e3{c, mode, true, h3};
+        // kernel counts per section (prologues once, bodies once per cycle), so that
+        // launch accounting can add what a graph launch actually ran
+        const long long l0 = launches();
         prologue_2d(e2);
+        const long long l1 = launches();
         add_while(c, h2, [&] { cycle_body(e2, c->h2, c->ctl + 0); });
+        const long long l2 = launches();
         prologue_3d(e3);
+        const long long l3 = launches();
         add_while(c, h3, [&] { cycle_body(e3, c->h3, c->ctl + 1); });
+        const long long l4 = launches();
+        count_launches(-(l4 - l0));   // capture records kernels without running them
+        c->gcount[mode][0] = l1 - l0;
+        c->gcount[mode][1] = l2 - l1;
+        c->gcount[mode][2] = l3 - l2;
+        c->gcount[mode][3] = l4 - l3;
         MHS_CUDA(cudaStreamEndCapture(c->stream, &graph));
         MHS_CUDA(cudaGraphInstantiate(&c->gexec[mode], graph, 0));
         cudaGraphDestroy(graph);
@@ -388,7 +409,9 @@ static bool read_cont(mhs_ctx* c, int which) {
     return c->ctl_host[which].cont != 0;
 }
 
-mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
+// Enqueue a solve on c->stream.  In graph mode nothing waits on the host;
+// in eager mode (kernel timing enabled) the host drives the cycles.
+void solve_begin(mhs_ctx* c, double tol, int mode) {
     cudaStream_t st = c->stream;
     for (int q = 0; q < 2; ++q) {
         c->ctl_host[q] = SolveCtl{};
@@ -397,8 +420,8 @@ mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     }
     MHS_CUDA(cudaMemcpyAsync(c->ctl, c->ctl_host, 2 * sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
     MHS_CUDA(cudaEventRecord(c->ev0, st));
-    const bool graph = c->use_graphs && !c->timer.enabled;
-    if (graph) {
+    c->pending_graph = c->use_graphs && !c->timer.enabled && !(c->opts.flags & MHS_FLAG_NO_GRAPH);
+    if (c->pending_graph) {
         if (!c->gexec[mode] || c->gkey[mode] != graph_key(c)) {
             if (c->gexec[mode]) cudaGraphExecDestroy(c->gexec[mode]);
             c->gexec[mode] = nullptr;
@@ -414,12 +437,20 @@ mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     }
     MHS_CUDA(cudaEventRecord(c->ev1, st));
     MHS_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl, 2 * sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+}
+
+// Wait for the solve enqueued by solve_begin and report it.
+mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     MHS_CUDA(cudaEventSynchronize(c->ev1));
-    MHS_CUDA(cudaStreamSynchronize(st));
+    MHS_CUDA(cudaStreamSynchronize(c->stream));
     float ms = 0;
     MHS_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     const SolveCtl& a = c->ctl_host[0];
     const SolveCtl& b = c->ctl_host[1];
+    if (c->pending_graph) {
+        const long long* n = c->gcount[mode];
+        count_launches(n[0] + a.cycles * n[1] + n[2] + b.cycles * n[3]);
+    }
     if (info) {
         info->cycles_2d = a.cycles;
         info->cycles_3d = b.cycles;
@@ -439,6 +470,56 @@ mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
         throw Error(MHS_ERR_NO_CONVERGENCE, buf);
     }
     return MHS_OK;
+}
+
+mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
+    solve_begin(c, tol, mode);
+    return solve_end(c, tol, mode, info);
+}
+
+// Batched solve: every handle's solve runs on its own internal stream so that
+// instances of different sizes overlap on the GPU; each instance runs exactly
+// the kernels of its solo solve, so results do not depend on the batch.
+mhs_status batch_solve(mhs_ctx** hs, int n, double tol, int mode, mhs_solve_info* infos, mhs_status* statuses) {
+    for (int q = 0; q < n; ++q) {
+        mhs_ctx* c = hs[q];
+        if (!c->bstream) MHS_CUDA(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
+        // order the batch stream after any work already queued on the handle's stream
+        MHS_CUDA(cudaEventRecord(c->ev0, c->stream));
+        MHS_CUDA(cudaStreamWaitEvent(c->bstream, c->ev0, 0));
+    }
+    for (int q = 0; q < n; ++q) {
+        mhs_ctx* c = hs[q];
+        cudaStream_t user = c->stream;
+        c->stream = c->bstream;
+        try {
+            solve_begin(c, tol, mode);
+        } catch (...) {
+            c->stream = user;
+            throw;
+        }
+        c->stream = user;
+    }
+    mhs_status worst = MHS_OK;
+    for (int q = 0; q < n; ++q) {
+        mhs_ctx* c = hs[q];
+        cudaStream_t user = c->stream;
+        c->stream = c->bstream;
+        mhs_status s = MHS_OK;
+        try {
+            s = solve_end(c, tol, mode, infos ? infos + q : nullptr);
+        } catch (const Error& e) {
+            s = e.status;
+            if (s == MHS_ERR_CUDA) {
+                c->stream = user;
+                throw;
+            }
+        }
+        c->stream = user;
+        if (statuses) statuses[q] = s;
+        if (s != MHS_OK && worst == MHS_OK) worst = s;
+    }
+    return worst;
 }
 
 void ensure_field_buffers(mhs_ctx* c) {

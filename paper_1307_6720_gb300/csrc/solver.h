@@ -15,7 +15,11 @@ void create(mhs_ctx* c);
 void destroy(mhs_ctx* c);
 void compute_coefficients(mhs_ctx* c);
 void invalidate_graphs(mhs_ctx* c);
+void choose_cuts(mhs_ctx* c);
 mhs_status solve(mhs_ctx* c, double tol, int mode, mhs_solve_info* info);
+void solve_begin(mhs_ctx* c, double tol, int mode);
+mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info);
+mhs_status batch_solve(mhs_ctx** hs, int n, double tol, int mode, mhs_solve_info* infos, mhs_status* statuses);
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l);
 double read_norm2(mhs_ctx* c, int slot);

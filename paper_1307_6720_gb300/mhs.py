@@ -22,7 +22,7 @@ STATUS_NAMES = ["MHS_OK", "MHS_ERR_INVALID_ARG", "MHS_ERR_NOT_ELLIPTIC", "MHS_ER
  MHS_ERR_NONFINITE, MHS_ERR_BAD_STATE, MHS_ERR_TIMEOUT, MHS_ERR_REJECTED) = range(1, 10)
 MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
 MHS_FP64, MHS_MIXED = 0, 1
-MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC = 1, 2
+MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH = 1, 2, 4
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
 
@@ -39,7 +39,8 @@ class AtmosParams(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int), ("cut64", ctypes.c_int),
+                ("cut32", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -70,6 +71,7 @@ _SIGS = {
     "mhs_set_params": [_H, _D, ctypes.POINTER(XiParams), ctypes.POINTER(AtmosParams)],
     "mhs_set_lower_bz": [_H, _P],
     "mhs_solve": [_H, _D, _I, ctypes.POINTER(SolveInfo)],
+    "mhs_batch_solve": [ctypes.POINTER(_H), _I, _D, _I, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
     "mhs_get_phi": [_H, _P],
     "mhs_fields": [_H, _P, _P, _P, _P, _P],
     "mhs_num_levels": [_H, _I, ctypes.POINTER(_I)],
@@ -158,8 +160,8 @@ def mhs_set_stream(h, stream) -> None:
     _check(LIB.mhs_set_stream(h, stream))
 
 
-def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0) -> None:
-    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags)
+def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32)
     _check(LIB.mhs_set_options(h, ctypes.byref(o)))
 
 
@@ -180,6 +182,18 @@ def mhs_solve(h, tol, mode=MHS_FP64) -> dict:
         err.info = info.as_dict()
         raise err
     return info.as_dict()
+
+
+def mhs_batch_solve(handles, tol, mode=MHS_FP64):
+    """Solve several handles concurrently; returns (per-instance info dicts, per-instance statuses)."""
+    n = len(handles)
+    arr = (_H * n)(*handles)
+    infos = (SolveInfo * n)()
+    sts = (_I * n)()
+    st = LIB.mhs_batch_solve(arr, n, tol, mode, infos, sts)
+    if st not in (MHS_OK, MHS_ERR_NO_CONVERGENCE, MHS_ERR_NONFINITE):
+        _check(st)
+    return [i.as_dict() for i in infos], list(sts)
 
 
 def mhs_get_phi(h, phi) -> None:

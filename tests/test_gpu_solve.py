@@ -260,3 +260,43 @@ def test_repeated_graph_launches_and_option_changes(M):
     e = M.mhs_solve(h, 1e-6)                      # tolerance lives in device memory, not in the graph
     assert e["cycles_3d"] < c["cycles_3d"]
     M.mhs_destroy(h)
+
+
+def test_batch_solve_matches_solo_solves(M):
+    """Instances of different sizes and parameters solved together give
+    bitwise the results of solving each alone."""
+    import torch
+    specs = [(33, 33, 33, 1.0, 0.2, 0.9, 0.7, 41), (65, 65, 65, 1.0, 0.6, 0.5, 1.5, 42),
+             (33, 33, 17, 0.5, 0.0, 0.0, 1.0, 43), (65, 65, 33, 0.5, 0.8, 0.99, 0.5, 44)]
+    solo, hs = [], []
+    for nx, ny, nz, Lz, alpha, a, kappa, seed in specs:
+        bz = S.magnetogram_random(nx, ny, seed=seed)
+        xi = M.xi_params(M.MHS_XI_EXP, a, kappa)
+        h = M.mhs_create(nx, ny, nz, 1.0, 1.0, Lz, alpha, xi)
+        M.mhs_set_lower_bz(h, bz)
+        info = M.mhs_solve(h, 1e-10, M.MHS_MIXED)
+        phi = np.zeros((nz, ny, nx)); M.mhs_get_phi(h, phi)
+        solo.append((info, phi))
+        M.mhs_set_lower_bz(h, bz)
+        hs.append(h)
+    infos, sts = M.mhs_batch_solve(hs, 1e-10, M.MHS_MIXED)
+    assert all(s == 0 for s in sts)
+    for h, (info, phi), bi in zip(hs, solo, infos):
+        got = np.zeros_like(phi); M.mhs_get_phi(h, got)
+        assert np.array_equal(got, phi)
+        assert bi["cycles_3d"] == info["cycles_3d"] and bi["rel_res_3d"] == info["rel_res_3d"]
+        M.mhs_destroy(h)
+
+
+def test_no_graph_flag_matches_graph(M):
+    pr, bz = S.linear_mhs(33, seed=14)
+    out = []
+    for flags in (0, M.MHS_FLAG_NO_GRAPH):
+        h = M.mhs_create(33, 33, 33, 1.0, 1.0, 1.0, pr["alpha"], _xi(M, pr))
+        M.mhs_set_options(h, flags=flags)
+        M.mhs_set_lower_bz(h, bz)
+        M.mhs_solve(h, 1e-10, M.MHS_MIXED)
+        phi = np.zeros((33, 33, 33)); M.mhs_get_phi(h, phi)
+        M.mhs_destroy(h)
+        out.append(phi)
+    assert np.array_equal(out[0], out[1])
