@@ -32,6 +32,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# more hardware work queues, so that the streams of batched and served solves run concurrently
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import synthetic as S  # noqa: E402
 
@@ -254,9 +256,14 @@ def run_gpu(args):
     M.mhs_kernel_timing_reset(h)
     timed(args.steps)
     kt = [M.mhs_kernel_timing(h, k) for k in range(M.MHS_KT_COUNT)]
+    kt0 = {k: M.mhs_kernel_timing_finest(h, k) for k in range(M.MHS_KT_COUNT)}
     M.mhs_set_kernel_timing(h, False)
+    kidx = {k["name"]: i for i, k in enumerate(kt)}
     kt = [k for k in kt if k["launches"] > 0]
-    dom = max(kt, key=lambda k: k["ms"])
+    dom_all = max(kt, key=lambda k: k["ms"])
+    # roofline of the dominant operation on the finest interior level (its largest instance); one
+    # "launch" of a sweep is one red-black sweep (the red and the black kernel)
+    dom = kt0[kidx[dom_all["name"]]] if kt0[kidx[dom_all["name"]]]["launches"] > 0 else dom_all
     hbm_peak, peak_src = measured_peaks()
     avg_ms = dom["ms"] / dom["launches"]
     gbs = dom["bytes"] / dom["launches"] / (avg_ms * 1e-3) / 1e9
@@ -265,15 +272,15 @@ def run_gpu(args):
     traffic = profiled_traffic(dom["name"])
     if alu_bound:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "kernel": dom["name"], "peak_source": "nominal FP64 (recipe table)",
+                "traffic": traffic, "kernel": dom["name"] + " (finest level)", "peak_source": "nominal FP64 (recipe table)",
                 "achieved_gbs": gbs, "hbm_frac_of_" + peak_src: gbs / hbm_peak}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": traffic, "kernel": dom["name"], "peak_source": peak_src}
+                "traffic": traffic, "kernel": dom["name"] + " (finest level)", "peak_source": peak_src}
     roof.update({"launches_timed": dom["launches"], "avg_launch_ms": avg_ms,
                  "alg_bytes_per_launch": dom["bytes"] / dom["launches"],
                  "alg_flops_per_launch": dom["flops"] / dom["launches"],
-                 "share_of_timed_ops": dom["ms"] / sum(k["ms"] for k in kt)})
+                 "share_of_timed_ops": dom_all["ms"] / sum(k["ms"] for k in kt)})
     kernels = {k["name"]: {"ms_per_step": k["ms"] / args.steps, "launches_per_step": k["launches"] / args.steps,
                            "gbs": k["bytes"] / (k["ms"] * 1e-3) / 1e9 if k["ms"] > 0 else None} for k in kt}
 
@@ -295,6 +302,12 @@ def run_gpu(args):
         cpu_base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                     "sample": f"{runs} oracle solves (2D+3D multigrid to 1e-10 + fields) of the 129^3 workload, {dt:.1f} s"}
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["large_grids"] = large_grid_leg(M, 3)
+        extra["batched"] = batched_leg(M)
+        extra["serving"] = serving_leg(M, args.serve_requests)
+
     if rank == 0:
         name = "mixed" if mode == M.MHS_MIXED else "fp64"
         oname = "fp64" if name == "mixed" else "mixed"
@@ -311,6 +324,7 @@ def run_gpu(args):
                               "cycles_3d": infos_o[-1]["cycles_3d"], "rel_res_3d": infos_o[-1]["rel_res_3d"]}},
             "kernels": kernels,
         }
+        out.update(extra)
         print(json.dumps(out))
     M.mhs_destroy(h)
     if world > 1:
@@ -344,6 +358,230 @@ def run_op(args):
     M.mhs_destroy(h)
 
 
+# --------------------------------------------------------------------------
+# other configurations: large grids, batched instances, request serving
+# --------------------------------------------------------------------------
+
+def _timed_solves(M, h, mode, K, bz_list, outs, stream, flush):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    infos = []
+    torch.cuda.synchronize()
+    for s in range(K):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        M.mhs_set_lower_bz(h, bz_list[s % len(bz_list)])
+        infos.append(M.mhs_solve(h, TOL, mode))
+        M.mhs_get_phi(h, outs[0])
+        M.mhs_fields(h, *outs[1:])
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / K, infos
+
+
+def large_grid_leg(M, steps, with_error=True):
+    """Large grids of the mixed-precision configuration: 257^3 on [0,1]^3 and 513x513x257 on
+    [0,1]^2 x [0,0.5], alpha = 0.5, xi = 0.5 exp(-z); FP64 and mixed; error of the last solve of each
+    mode against the oracle's exact discrete solution (relative L2 of Phi, B, p, rho)."""
+    import numpy as np
+    import torch
+    out = {}
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for name, n, nz, Lz in (("257^3", 257, 257, 1.0), ("513x513x257", 513, 257, 0.5)):
+        pr, _ = S.linear_mhs(n, nz=nz, Lz=Lz)
+        bzs = [S.magnetogram_random(n, n, 1.0, 1.0, seed=1307 + i) for i in range(2)]
+        xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
+        h = M.mhs_create(n, n, nz, 1.0, 1.0, Lz, pr["alpha"], xi)
+        M.mhs_set_stream(h, stream)
+        shape = (nz, n, n)
+        outs = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(6)]
+        bz_dev = [torch.from_numpy(b).to(dev) for b in bzs]
+        ent = {"unknowns_per_solve": S.unknowns(pr)}
+        want = None
+        if with_error:
+            import oracle
+            from oracle import exact
+            P = exact.exact_solution(pr, bzs[(steps - 1) % 2])
+            F = oracle.fields(pr, P)
+            want = dict(F, phi=P)
+        for mname, mode in (("fp64", M.MHS_FP64), ("mixed", M.MHS_MIXED)):
+            _timed_solves(M, h, mode, 1, bz_dev, outs, stream, flush)
+            ms, infos = _timed_solves(M, h, mode, steps, bz_dev, outs, stream, flush)
+            e = {"value": S.unknowns(pr) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                 "cycles_3d": infos[-1]["cycles_3d"], "rel_res_3d": infos[-1]["rel_res_3d"]}
+            if want is not None:
+                got = {k: o.cpu().numpy() for k, o in zip(["phi", "Bx", "By", "Bz", "p", "rho"], outs)}
+                e["rel_l2_error_vs_oracle"] = {k: float(np.linalg.norm(got[k] - want[k]) / np.linalg.norm(want[k]))
+                                               for k in got}
+            ent[mname] = e
+        ent["mixed_speedup_vs_fp64"] = ent["fp64"]["ms_per_step"] / ent["mixed"]["ms_per_step"]
+        out[name] = ent
+        M.mhs_destroy(h)
+        del outs, bz_dev
+        torch.cuda.empty_cache()
+    return out
+
+
+def batched_instances(count=256):
+    """Seeded instances: grids 33^3, 65^3, 129^3 and 129x129x65 (on [0,1]^2 x [0,0.5]) in turn,
+    alpha ~ U[0,0.8], xi = a exp(-kappa z) with a ~ U[0,1), kappa ~ U[0.5,2], 8-spot magnetograms;
+    instance i draws from splitmix64(1000 + i)."""
+    shapes = [(33, 33, 1.0), (65, 65, 1.0), (129, 129, 1.0), (129, 65, 0.5)]
+    inst = []
+    for i in range(count):
+        n, nz, Lz = shapes[i % 4]
+        rng = S.SplitMix64(1000 + i)
+        alpha, a, kappa = rng.uniform(0.0, 0.8), rng.uniform(0.0, 1.0), rng.uniform(0.5, 2.0)
+        inst.append(dict(n=n, nz=nz, Lz=Lz, alpha=alpha, a=a, kappa=kappa,
+                         bz=S.magnetogram_random(n, n, seed=1000 + i)))
+    return inst
+
+
+def batched_leg(M, reps=3, count=256):
+    """All instances in one mhs_batch_solve (mixed, graphs) against solving them one after another in
+    FP64 and in mixed mode."""
+    import torch
+    inst = batched_instances(count)
+    hs = []
+    for d in inst:
+        h = M.mhs_create(d["n"], d["n"], d["nz"], 1.0, 1.0, d["Lz"], d["alpha"],
+                         M.xi_params(M.MHS_XI_EXP, d["a"], d["kappa"]))
+        M.mhs_set_lower_bz(h, torch.from_numpy(d["bz"]).cuda())
+        hs.append(h)
+    unknowns = sum(S.unknowns(S.problem(d["n"], d["n"], d["nz"])) for d in inst)
+
+    def seq(mode):
+        for h in hs:
+            M.mhs_solve(h, TOL, mode)
+
+    def bat():
+        infos, sts = M.mhs_batch_solve(hs, TOL, M.MHS_MIXED)
+        assert all(s == 0 for s in sts), sts
+        return infos
+
+    res = {}
+    for name, fn in (("batched_mixed", bat), ("sequential_fp64", lambda: seq(M.MHS_FP64)),
+                     ("sequential_mixed", lambda: seq(M.MHS_MIXED))):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        res[name] = {"solves_per_s": count / dt, "unknowns_per_s": unknowns / dt, "s_per_batch": dt}
+        if name == "batched_mixed":
+            res[name]["max_cycles_3d"] = max(i["cycles_3d"] for i in out)
+            res[name]["max_rel_res_3d"] = max(i["rel_res_3d"] for i in out)
+    res["instances"] = count
+    res["speedup_vs_sequential_fp64"] = res["batched_mixed"]["solves_per_s"] / res["sequential_fp64"]["solves_per_s"]
+    for h in hs:
+        M.mhs_destroy(h)
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving_leg(M, requests=1000, load=0.8, inflight=16, budget_gb=64):
+    """Poisson arrivals of solve requests, grid sizes 65^3 / 129^3 / 257^3 at 60/30/10 %, random
+    magnetograms and alpha / xi parameters (request r: splitmix64(r); arrivals: splitmix64(42)),
+    served with HBM-budget admission and resident hierarchies (mixed precision, Phi + fields into
+    device buffers).  Capacity is measured first with all requests queued at once; the Poisson
+    stream then runs at `load` x capacity.  Baseline: the same requests solved one after another in
+    FP64 through mhs_solve + mhs_fields."""
+    import math as _m
+    import torch
+    sizes = []
+    for r in range(requests):
+        u = S.SplitMix64(r).uniform()
+        sizes.append(65 if u < 0.6 else 129 if u < 0.9 else 257)
+    params, mags = [], {}
+    for r in range(requests):
+        rng = S.SplitMix64(7_000_000 + r)
+        params.append((rng.uniform(0.0, 0.8), rng.uniform(0.0, 0.9), rng.uniform(0.5, 2.0)))
+    for n in (65, 129, 257):   # a few magnetograms per size, reused round-robin
+        mags[n] = [S.magnetogram_random(n, n, seed=9000 + 10 * n + i) for i in range(4)]
+    ring = {n: [[torch.empty((n, n, n), dtype=torch.float64, device="cuda") for _ in range(6)]
+                for _ in range(inflight + 2)] for n in (65, 129, 257)}
+    use = {n: 0 for n in ring}
+
+    def submit(srv, r):
+        n = sizes[r]
+        alpha, a, kappa = params[r]
+        bufs = ring[n][use[n] % len(ring[n])]
+        use[n] += 1
+        return M.mhs_server_submit(srv, n, n, n, 1.0, 1.0, 1.0, alpha, M.xi_params(M.MHS_XI_EXP, a, kappa),
+                                   mags[n][r % 4], TOL, M.MHS_MIXED, phi=bufs[0], Bx=bufs[1], By=bufs[2],
+                                   Bz=bufs[3], p=bufs[4], rho=bufs[5])
+
+    srv = M.mhs_server_create(budget_gb << 30, inflight)
+    # warm the resident hierarchies and capture the graphs
+    for r in range(min(requests, 24)):
+        M.mhs_server_wait(srv, submit(srv, r), 600.0)
+    t0 = time.perf_counter()
+    tickets = [submit(srv, r) for r in range(requests)]
+    for t in tickets:
+        M.mhs_server_wait(srv, t, 600.0)
+    capacity = requests / (time.perf_counter() - t0)
+    M.mhs_server_destroy(srv)
+
+    srv = M.mhs_server_create(budget_gb << 30, inflight)
+    for r in range(min(requests, 24)):
+        M.mhs_server_wait(srv, submit(srv, r), 600.0)
+    rate = load * capacity
+    arr = S.SplitMix64(42)
+    t_next = time.perf_counter()
+    tickets = []
+    t0 = time.perf_counter()
+    for r in range(requests):
+        t_next += -_m.log(1.0 - arr.uniform()) / rate
+        while time.perf_counter() < t_next:
+            pass
+        tickets.append(submit(srv, r))
+    lat = []
+    for t in tickets:
+        info, st, l = M.mhs_server_wait(srv, t, 600.0)
+        assert st == 0, st
+        lat.append(l)
+    span = time.perf_counter() - t0
+    stats = M.mhs_server_stats(srv)
+    M.mhs_server_destroy(srv)
+    lat.sort()
+    pct = lambda p: lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))]
+
+    # sequential FP64 baseline on a sample of the same requests (one handle per size)
+    hs = {n: M.mhs_create(n, n, n, 1.0, 1.0, 1.0, 0.0) for n in (65, 129, 257)}
+    sample = list(range(min(requests, 200)))
+    outs = {n: ring[n][0] for n in ring}
+    for r in sample[:6]:
+        n = sizes[r]; a_, x_, k_ = params[r]
+        M.mhs_set_params(hs[n], a_, M.xi_params(M.MHS_XI_EXP, x_, k_))
+        M.mhs_set_lower_bz(hs[n], mags[n][r % 4]); M.mhs_solve(hs[n], TOL, M.MHS_FP64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in sample:
+        n = sizes[r]; a_, x_, k_ = params[r]
+        M.mhs_set_params(hs[n], a_, M.xi_params(M.MHS_XI_EXP, x_, k_))
+        M.mhs_set_lower_bz(hs[n], mags[n][r % 4])
+        M.mhs_solve(hs[n], TOL, M.MHS_FP64)
+        M.mhs_get_phi(hs[n], outs[n][0])
+        M.mhs_fields(hs[n], *outs[n][1:])
+    torch.cuda.synchronize()
+    seq_rate = len(sample) / (time.perf_counter() - t1)
+    for h in hs.values():
+        M.mhs_destroy(h)
+    del ring
+    torch.cuda.empty_cache()
+    return {"requests": requests, "mix": "65^3/129^3/257^3 at 60/30/10 %", "max_inflight": inflight,
+            "budget_gb": budget_gb, "capacity_solves_per_s": capacity, "offered_load": load,
+            "arrival_rate_per_s": rate, "solves_per_s": requests / span, "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+            "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"],
+            "resident_hierarchies": stats["resident_hierarchies"], "device_bytes": stats["device_bytes"],
+            "sequential_fp64_solves_per_s": seq_rate, "sequential_sample": len(sample),
+            "speedup_vs_sequential_fp64": (requests / span) / seq_rate}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +595,9 @@ def main():
     ap.add_argument("--op", choices=["smooth", "residual", "restrict", "prolong", "vcycle"], default=None,
                     help="repeat one finest-level operation of the interior hierarchy (--steps times) for kernel capture")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="precision of --op")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the large-grid, batched and serving legs")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving leg")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven kernel-by-kernel solve instead of the captured graph (for launch lists)")
     args = ap.parse_args()

@@ -178,6 +178,55 @@ MHS_API mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info*
 MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solve_info* infos,
                                    mhs_status* statuses);
 
+/* ---- request server (continuous batching) ----------------------------
+ * A server owns a worker thread and a pool of resident solver hierarchies
+ * (one pool per grid shape).  Submitted requests are admitted in arrival
+ * order as soon as one of max_inflight slots and enough of the device-
+ * memory budget are free; admitted requests run concurrently, each on its
+ * own stream, while later requests keep arriving.  Idle hierarchies of
+ * other shapes are released when the budget is short.  Each request runs
+ * the kernels of a solo mhs_solve + mhs_fields, so its result does not
+ * depend on what else is in flight. */
+typedef struct mhs_server* mhs_server_t;
+
+typedef struct {
+    int nx, ny, nz;                 /* grid (as mhs_create) */
+    double Lx, Ly, Lz, alpha;
+    mhs_xi_params xi;
+    mhs_atmos_params atm;           /* all-zero = defaults */
+    double tol;                     /* relative residual target, (0, 1) */
+    int mode;                       /* mhs_precision */
+    const double* bz;               /* [ny][nx], host or device; copied during mhs_server_submit */
+    double* phi;                    /* outputs [nz][ny][nx], host or device, any may be NULL; written */
+    double *Bx, *By, *Bz, *p, *rho; /* asynchronously: keep them valid until the request completes */
+} mhs_request;
+
+typedef struct {
+    long long completed, rejected, queued, running;
+    double p50_ms, p99_ms, mean_ms;  /* latency from submission to completion, completed requests */
+    double solves_per_s;             /* completed / (last completion - first submission) */
+    size_t device_bytes;             /* bytes held by resident hierarchies */
+    long long resident_hierarchies;
+} mhs_server_stats_t;
+
+/* Errors: MHS_ERR_INVALID_ARG (budget 0, max_inflight outside [1, 1024]), MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_server_create(size_t budget_bytes, int max_inflight, mhs_server_t* out);
+/* Queue one request; *ticket identifies it.  B_z is copied and checked here
+ * (MHS_ERR_NONFINITE for a NaN/Inf interior value, MHS_ERR_INVALID_ARG for
+ * bad sizes).  A request whose hierarchy exceeds the whole budget completes
+ * with status MHS_ERR_REJECTED. */
+MHS_API mhs_status mhs_server_submit(mhs_server_t s, const mhs_request* req, long long* ticket);
+/* Non-blocking completion check; on completion fills info, the request's
+ * status and its latency, and forgets the ticket. */
+MHS_API mhs_status mhs_server_poll(mhs_server_t s, long long ticket, int* done, mhs_solve_info* info,
+                                   mhs_status* req_status, double* latency_ms);
+/* Blocking wait (timeout_s <= 0: no limit; MHS_ERR_TIMEOUT when it expires). */
+MHS_API mhs_status mhs_server_wait(mhs_server_t s, long long ticket, double timeout_s, mhs_solve_info* info,
+                                   mhs_status* req_status, double* latency_ms);
+MHS_API mhs_status mhs_server_stats(mhs_server_t s, mhs_server_stats_t* out);
+/* Finish every queued and running request, then release the server. */
+MHS_API void mhs_server_destroy(mhs_server_t s);
+
 /* Copy P (the poloidal potential of eq. b_iden), [nz][ny][nx], to phi (host
  * or device).  Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_INVALID_ARG. */
 MHS_API mhs_status mhs_get_phi(mhs_handle h, double* phi);
@@ -250,6 +299,9 @@ MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int pr
 MHS_API mhs_status mhs_set_kernel_timing(mhs_handle h, int enable);
 MHS_API mhs_status mhs_kernel_timing(mhs_handle h, int kind, double* total_ms, long long* launches,
                                      double* alg_bytes, double* alg_flops);
+/* The same totals restricted to operations on the finest interior level. */
+MHS_API mhs_status mhs_kernel_timing_finest(mhs_handle h, int kind, double* total_ms, long long* launches,
+                                            double* alg_bytes, double* alg_flops);
 MHS_API mhs_status mhs_kernel_timing_reset(mhs_handle h);
 MHS_API const char* mhs_kernel_kind_name(int kind);
 

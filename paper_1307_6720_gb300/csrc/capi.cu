@@ -438,6 +438,19 @@ mhs_status mhs_kernel_timing(mhs_handle h, int kind, double* total_ms, long long
     });
 }
 
+mhs_status mhs_kernel_timing_finest(mhs_handle h, int kind, double* total_ms, long long* launches, double* alg_bytes,
+                                    double* alg_flops) {
+    if (!h || kind < 0 || kind >= MHS_KT_COUNT) return fail(MHS_ERR_INVALID_ARG, "bad handle or kind");
+    return guarded([&] {
+        h->timer.collect();
+        if (total_ms) *total_ms = h->timer.ms0[kind];
+        if (launches) *launches = h->timer.count0[kind];
+        if (alg_bytes) *alg_bytes = h->timer.alg_bytes0[kind];
+        if (alg_flops) *alg_flops = h->timer.alg_flops0[kind];
+        return MHS_OK;
+    });
+}
+
 mhs_status mhs_kernel_timing_reset(mhs_handle h) {
     if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
     return guarded([&] {

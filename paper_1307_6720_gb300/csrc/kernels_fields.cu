@@ -174,17 +174,23 @@ __global__ void field_rho_face_kernel(Geom g, const double* __restrict__ prof, c
         field_rho_node(g, prof, Bx, By, Bz, rho, i, j, k);
 }
 
-// Inner nodes (1 <= i, j, k <= n-2): fixed central stencils.
-__global__ void field_b_kernel(Geom g, double alpha, const double* __restrict__ prof, const double* __restrict__ P,
-                               double* __restrict__ Bx, double* __restrict__ By, double* __restrict__ Bz,
-                               double* __restrict__ p, int bz_mode) {
+// Inner nodes (1 <= i, j, k <= n-2): fixed central stencils.  The
+// difference weights come precomputed from the host (FieldWeights).
+struct FieldWeights {
+    double ax, ay;     // alpha/(2 hy), alpha/(2 hx): alpha dP/dy and alpha dP/dx
+    double mxz, myz;   // 1/(4 hx hz), 1/(4 hy hz): mixed derivatives
+    double cx, cy;     // 1/hx^2, 1/hy^2: compact second differences
+    double dx, dy, dz; // 1/(2 h): central first differences of B_z
+};
+
+__global__ void field_b_kernel(Geom g, FieldWeights w, double alpha, const double* __restrict__ prof,
+                               const double* __restrict__ P, double* __restrict__ Bx, double* __restrict__ By,
+                               double* __restrict__ Bz, double* __restrict__ p, int bz_mode) {
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i > g.nx - 2 || j > g.ny - 2) return;
     const ptrdiff_t sx = 1, sy = g.px, sz = (ptrdiff_t)g.plane;
-    const double ax = alpha / (2.0 * g.hy), ay = alpha / (2.0 * g.hx);   // alpha d/dy, alpha d/dx
-    const double mxz = 1.0 / (4.0 * g.hx * g.hz), myz = 1.0 / (4.0 * g.hy * g.hz);
-    const double cx = 1.0 / (g.hx * g.hx), cy = 1.0 / (g.hy * g.hy);
+    const double ax = w.ax, ay = w.ay, mxz = w.mxz, myz = w.myz, cx = w.cx, cy = w.cy;
     for (int k = 1 + blockIdx.z; k <= g.nz - 2; k += gridDim.z) {
         const size_t o = at(g, i, j, k);
         double bx, by, bz;
@@ -207,13 +213,13 @@ __global__ void field_b_kernel(Geom g, double alpha, const double* __restrict__ 
     }
 }
 
-__global__ void field_rho_kernel(Geom g, const double* __restrict__ prof, const double* __restrict__ Bx,
+__global__ void field_rho_kernel(Geom g, FieldWeights w, const double* __restrict__ prof, const double* __restrict__ Bx,
                                  const double* __restrict__ By, const double* __restrict__ Bz,
                                  double* __restrict__ rho) {
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i > g.nx - 2 || j > g.ny - 2) return;
-    const double dx = 1.0 / (2.0 * g.hx), dy = 1.0 / (2.0 * g.hy), dz = 1.0 / (2.0 * g.hz);
+    const double dx = w.dx, dy = w.dy, dz = w.dz;
     for (int k = 1 + blockIdx.z; k <= g.nz - 2; k += gridDim.z) {
         const size_t o = at(g, i, j, k);
         const double bz = Bz[o];
@@ -231,19 +237,30 @@ __global__ void field_rho_kernel(Geom g, const double* __restrict__ prof, const 
 void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, const double* prof, const double* P,
                    double* Bx, double* By, double* Bz, double* p, double* rho, int bz_mode, cudaStream_t st) {
     const dim3 blk(32, 8);
-    int gz = g.nz - 2;
+    // a few planes per thread so that per-thread set-up is amortised
+    int gz = (g.nz - 2 + 3) / 4;
     if (gz > 65535) gz = 65535;
+    FieldWeights w;
+    w.ax = alpha / (2.0 * g.hy);
+    w.ay = alpha / (2.0 * g.hx);
+    w.mxz = 1.0 / (4.0 * g.hx * g.hz);
+    w.myz = 1.0 / (4.0 * g.hy * g.hz);
+    w.cx = 1.0 / (g.hx * g.hx);
+    w.cy = 1.0 / (g.hy * g.hy);
+    w.dx = 1.0 / (2.0 * g.hx);
+    w.dy = 1.0 / (2.0 * g.hy);
+    w.dz = 1.0 / (2.0 * g.hz);
     const dim3 grid((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, gz);
     const long long faces = 2LL * g.nx * g.ny + 2LL * (g.nz - 2) * g.nx + 2LL * (g.nz - 2) * (g.ny - 2);
     const int fblocks = int((faces + 255) / 256 < 152 * 16 ? (faces + 255) / 256 : 152 * 16);
     (void)atm;
-    field_b_kernel<<<grid, blk, 0, st>>>(g, alpha, prof, P, Bx, By, Bz, p, bz_mode);
+    field_b_kernel<<<grid, blk, 0, st>>>(g, w, alpha, prof, P, Bx, By, Bz, p, bz_mode);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     field_b_face_kernel<<<fblocks, 256, 0, st>>>(g, alpha, prof, P, Bx, By, Bz, p, bz_mode);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
-    field_rho_kernel<<<grid, blk, 0, st>>>(g, prof, Bx, By, Bz, rho);
+    field_rho_kernel<<<grid, blk, 0, st>>>(g, w, prof, Bx, By, Bz, rho);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     field_rho_face_kernel<<<fblocks, 256, 0, st>>>(g, prof, Bx, By, Bz, rho);

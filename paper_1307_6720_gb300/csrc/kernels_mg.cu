@@ -9,6 +9,7 @@
 // kernels_fine.cu.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "device_util.cuh"
@@ -138,7 +139,7 @@ __global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* 
 // r = f - A u at interior nodes; with partial != nullptr also per-block
 // partial sums of r^2 (in double), finished in fixed order by
 // norm_finish_kernel / check_kernel.
-template <typename T, bool D3>
+template <typename T, bool D3, bool NORM>
 __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
                                 const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,10 +153,10 @@ __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, c
             if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
             const T rv = (f ? f[o] : T(0)) - au;
             r[o] = rv;
-            acc += double(rv) * double(rv);
+            if (NORM) acc += double(rv) * double(rv);
         }
     }
-    if (partial == nullptr) return;   // uniform across the block
+    if (!NORM) return;
     const double s = block_sum(acc);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
@@ -449,9 +450,16 @@ template <typename T>
 int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r, double* partial,
                     int max_blocks, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, partial ? max_blocks : 0);
-    if (d3) residual_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
-    else residual_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+    // with norm partials, few enough blocks (a multiple of the SM count) that
+    // the fixed-order finish stays short; every thread then covers several planes
+    const dim3 grid = grid_for(g, d3, g.nx - 2, partial ? std::min(max_blocks, 152 * 8) : 0);
+    if (partial) {
+        if (d3) residual_kernel<T, true, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+        else residual_kernel<T, false, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+    } else {
+        if (d3) residual_kernel<T, true, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+        else residual_kernel<T, false, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+    }
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     return int(grid.x * grid.y * grid.z);
@@ -466,7 +474,7 @@ void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t 
 int launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u, const double* f,
                            float* r32, double* partial, int max_blocks, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, max_blocks);
+    const dim3 grid = grid_for(g, d3, g.nx - 2, std::min(max_blocks, 152 * 8));
     if (d3) residual_f32_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
     else residual_f32_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
     count_launches(1);

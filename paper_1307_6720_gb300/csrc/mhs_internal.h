@@ -26,7 +26,7 @@ void count_launches(long long n);
 long long launches();
 #define MHS_CUDA(call) ::mhs::cuda_check((call), #call, __FILE__, __LINE__)
 
-inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+__host__ __device__ inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
 // Per-plane coefficients of the interior operator of eq. (scalar_pot) on one
 // level: (A u)_ijk = cx_k (u_E + u_W) + cy_k (u_N + u_S) + cz (u_U + u_D) + d_k u_ijk,
@@ -121,15 +121,20 @@ struct KernelTimer {
     bool enabled = false;
     std::vector<cudaEvent_t> pool;   // 2 events per record
     std::vector<int> kind;           // operation kind per record
+    std::vector<char> fine;          // record belongs to the finest interior level
     std::vector<double> bytes, flops;
     size_t used = 0;
     double ms[MHS_KT_COUNT] = {};
     long long count[MHS_KT_COUNT] = {};
     double alg_bytes[MHS_KT_COUNT] = {};
     double alg_flops[MHS_KT_COUNT] = {};
+    double ms0[MHS_KT_COUNT] = {};              // the same totals restricted to the finest interior level
+    long long count0[MHS_KT_COUNT] = {};
+    double alg_bytes0[MHS_KT_COUNT] = {};
+    double alg_flops0[MHS_KT_COUNT] = {};
 
     // start a record; returns its index or -1 when disabled
-    int begin(int k, double b, double f, cudaStream_t st);
+    int begin(int k, double b, double f, cudaStream_t st, bool finest = false);
     void end(int rec, cudaStream_t st);
     void collect();   // synchronises on the recorded events and folds them into the totals
     void reset();
@@ -140,8 +145,8 @@ struct TimedScope {
     KernelTimer& t;
     cudaStream_t st;
     int rec;
-    TimedScope(KernelTimer& timer, int k, double b, double f, cudaStream_t s)
-        : t(timer), st(s), rec(timer.begin(k, b, f, s)) {}
+    TimedScope(KernelTimer& timer, int k, double b, double f, cudaStream_t s, bool finest = false)
+        : t(timer), st(s), rec(timer.begin(k, b, f, s, finest)) {}
     ~TimedScope() { t.end(rec, st); }
 };
 

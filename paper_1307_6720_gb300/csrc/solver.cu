@@ -60,8 +60,11 @@ static int choose_cut(const Hierarchy& H, size_t elem, size_t max_interior) {
     int cut = H.nlev() - 1;
     for (int l = H.nlev() - 1; l >= 0; --l) {
         size_t bytes = 0;
-        for (int m = l; m < H.nlev(); ++m) bytes += 2 * H.g[m].n * elem;
-        if (bytes > subcycle_smem_limit() || H.g[l].interior() > max_interior) break;
+        for (int m = l; m < H.nlev(); ++m) bytes += 2 * round_up(H.g[m].n, 4) * elem + H.g[m].nz * 8 * elem;
+        // the sub-cycle decodes node indices with float reciprocals (exact for rows of <= 1024 nodes)
+        if (bytes > subcycle_smem_limit() || H.g[l].interior() > max_interior || H.g[l].nx - 2 > 1024 ||
+            H.g[l].ny - 2 > 1024)
+            break;
         cut = l;
     }
     return cut;
@@ -79,7 +82,7 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
         if (dim == 3) nz = (nz - 1) / 2 + 1;
     }
     const Geom& gc = H.g.back();
-    if (2 * gc.n * sizeof(double) > subcycle_smem_limit())
+    if (2 * gc.n * sizeof(double) > subcycle_smem_limit() || gc.nx - 2 > 1024 || gc.ny - 2 > 1024)
         throw Error(MHS_ERR_INVALID_ARG,
                     "coarsest multigrid level too large (" + std::to_string(gc.nx) + "x" + std::to_string(gc.ny) +
                         "x" + std::to_string(gc.nz) + "); use node counts of the form 2^k m + 1 with small m");
@@ -196,7 +199,9 @@ void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
     }
     p.u_g = arrays<T>(H, l).u;
     p.f_g = arrays<T>(H, l).f;
-    p.smem_bytes = off * sizeof(T);
+    size_t ncoef = 0;
+    for (int m = 0; m < p.nlev; ++m) ncoef += size_t(H.g[l + m].nz);
+    p.smem_bytes = round_up(ncoef * sizeof(PlaneCoef<T>), 16) + off * sizeof(T);
     if (p.smem_bytes > subcycle_smem_limit()) throw Error(MHS_ERR_INVALID_ARG, "sub-cycle does not fit shared memory");
     const bool dbl = sizeof(T) == 8;
     TimedScope t(c->timer, dbl ? MHS_KT_COARSE64 : MHS_KT_COARSE32, 2.0 * H.g[l].n * sizeof(T), 0.0, c->stream);
@@ -219,28 +224,29 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     const double fs = f_zero ? 0.0 : s;
     const T* f = f_zero ? nullptr : A.f;
     const double upd_flops = H.dim == 3 ? 10.0 : 7.0;
+    const bool fine = H.dim == 3 && l == 0;
     for (int q = 0; q < c->opts.nu1; ++q) {
-        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st);
+        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st, fine);
         launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
     }
     {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st);
+        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st, fine);
         launch_residual<T>(g, H.dim, A.coef, A.u, f, A.r, nullptr, 0, st);
     }
     LevelArrays<T>& C = arrays<T>(H, l + 1);
     const double Nc = double(H.g[l + 1].interior());
     {
         TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
-                     Nc * (H.dim == 3 ? 54.0 : 18.0), st);
+                     Nc * (H.dim == 3 ? 54.0 : 18.0), st, fine);
         launch_restrict<T>(g, H.g[l + 1], H.dim, A.r, C.f, C.u, st);
     }
     vcycle<T>(c, H, l + 1);
     {
-        TimedScope t(c->timer, dbl ? MHS_KT_PROLONG64 : MHS_KT_PROLONG32, (2 * N + Nc) * s, 4.0 * N, st);
+        TimedScope t(c->timer, dbl ? MHS_KT_PROLONG64 : MHS_KT_PROLONG32, (2 * N + Nc) * s, 4.0 * N, st, fine);
         launch_prolong<T>(H.g[l + 1], g, H.dim, C.u, A.u, st);
     }
     for (int q = 0; q < c->opts.nu2; ++q) {
-        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st);
+        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st, fine);
         launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
     }
 }
@@ -278,10 +284,10 @@ static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
     const double fb = (H.dim == 3 && c->f_zero_finest) ? 0.0 : 8.0;
     const double fl = H.dim == 3 ? 11.0 : 8.0;
     if (mode == MHS_MIXED) {
-        TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + fb + 4.0), N * fl, c->stream);
+        TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + fb + 4.0), N * fl, c->stream, H.dim == 3);
         return launch_residual_to_f32(g, H.dim, A.coef, A.u, A.f, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
     }
-    TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream);
+    TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream, H.dim == 3);
     return launch_residual<double>(g, H.dim, A.coef, A.u, A.f, A.r, c->ns.partial, c->ns.max_blocks, c->stream);
 }
 
@@ -291,7 +297,8 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     if (e.mode == MHS_MIXED) {
         MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
         for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
-        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()), c->stream);
+        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()), c->stream,
+                     H.dim == 3);
         launch_add_correction(g, H.dim, H.s[0].u, H.d[0].u, c->stream);
     } else {
         vcycle<double>(c, H, 0);
@@ -536,7 +543,7 @@ void ensure_staging(mhs_ctx* c) {
 
 namespace mhs {
 
-int KernelTimer::begin(int k, double b, double f, cudaStream_t st) {
+int KernelTimer::begin(int k, double b, double f, cudaStream_t st, bool finest) {
     if (!enabled) return -1;
     if (2 * (used + 1) > pool.size()) {
         for (int q = 0; q < 64; ++q) {
@@ -548,10 +555,12 @@ int KernelTimer::begin(int k, double b, double f, cudaStream_t st) {
     const int rec = int(used++);
     if (kind.size() < used) {
         kind.resize(used);
+        fine.resize(used);
         bytes.resize(used);
         flops.resize(used);
     }
     kind[rec] = k;
+    fine[rec] = finest ? 1 : 0;
     bytes[rec] = b;
     flops[rec] = f;
     MHS_CUDA(cudaEventRecord(pool[2 * rec], st));
@@ -572,13 +581,22 @@ void KernelTimer::collect() {
         count[kind[r]] += 1;
         alg_bytes[kind[r]] += bytes[r];
         alg_flops[kind[r]] += flops[r];
+        if (fine[r]) {
+            ms0[kind[r]] += m;
+            count0[kind[r]] += 1;
+            alg_bytes0[kind[r]] += bytes[r];
+            alg_flops0[kind[r]] += flops[r];
+        }
     }
     used = 0;
 }
 
 void KernelTimer::reset() {
     collect();
-    for (int k = 0; k < MHS_KT_COUNT; ++k) ms[k] = alg_bytes[k] = alg_flops[k] = 0, count[k] = 0;
+    for (int k = 0; k < MHS_KT_COUNT; ++k) {
+        ms[k] = alg_bytes[k] = alg_flops[k] = 0, count[k] = 0;
+        ms0[k] = alg_bytes0[k] = alg_flops0[k] = 0, count0[k] = 0;
+    }
 }
 
 void KernelTimer::destroy() {

@@ -51,6 +51,25 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("xi", XiParams), ("atm", AtmosParams),
+                ("tol", ctypes.c_double), ("mode", ctypes.c_int), ("bz", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p), ("Bx", ctypes.c_void_p), ("By", ctypes.c_void_p),
+                ("Bz", ctypes.c_void_p), ("p", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("running", ctypes.c_longlong), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("resident_hierarchies", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MhsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         self.status = status
@@ -82,10 +101,19 @@ _SIGS = {
     "mhs_set_kernel_timing": [_H, _I],
     "mhs_kernel_timing": [_H, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                           ctypes.POINTER(_D)],
+    "mhs_kernel_timing_finest": [_H, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                                 ctypes.POINTER(_D)],
     "mhs_kernel_timing_reset": [_H],
     "mhs_kernel_kind_name": [_I],
     "mhs_kernel_launches": [],
     "mhs_interior_residual_noalloc": [_I, _I, _I, _D, _D, _D, _D, ctypes.POINTER(XiParams), _P, _P, _P],
+    "mhs_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_H)],
+    "mhs_server_submit": [_H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)],
+    "mhs_server_poll": [_H, ctypes.c_longlong, ctypes.POINTER(_I), ctypes.POINTER(SolveInfo), ctypes.POINTER(_I),
+                        ctypes.POINTER(_D)],
+    "mhs_server_wait": [_H, ctypes.c_longlong, _D, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    "mhs_server_stats": [_H, ctypes.POINTER(ServerStats)],
+    "mhs_server_destroy": [_H],
     "mhs_status_string": [_I],
     "mhs_last_error": [],
     "mhs_version": [],
@@ -100,7 +128,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        if name == "mhs_destroy":
+        if name in ("mhs_destroy", "mhs_server_destroy"):
             fn.restype = None
         elif name in ("mhs_status_string", "mhs_last_error", "mhs_version", "mhs_kernel_kind_name"):
             fn.restype = ctypes.c_char_p
@@ -241,6 +269,12 @@ def mhs_kernel_timing(h, kind: int) -> dict:
     return dict(name=mhs_kernel_kind_name(kind), ms=ms.value, launches=n.value, bytes=b.value, flops=f.value)
 
 
+def mhs_kernel_timing_finest(h, kind: int) -> dict:
+    ms, n, b, f = _D(), ctypes.c_longlong(), _D(), _D()
+    _check(LIB.mhs_kernel_timing_finest(h, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f)))
+    return dict(name=mhs_kernel_kind_name(kind), ms=ms.value, launches=n.value, bytes=b.value, flops=f.value)
+
+
 def mhs_kernel_timing_reset(h) -> None:
     _check(LIB.mhs_kernel_timing_reset(h))
 
@@ -259,6 +293,45 @@ def mhs_interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha, xi: XiParams | 
         stream = stream.cuda_stream
     _check(LIB.mhs_interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha,
                                              ctypes.byref(xi) if xi is not None else None, ptr(P), ptr(out), stream))
+
+
+def mhs_server_create(budget_bytes: int, max_inflight: int = 16) -> int:
+    h = _H()
+    _check(LIB.mhs_server_create(budget_bytes, max_inflight, ctypes.byref(h)))
+    return h.value
+
+
+def mhs_server_submit(server, nx, ny, nz, Lx, Ly, Lz, alpha, xi: XiParams | None, bz, tol=1e-10, mode=MHS_MIXED,
+                      atm: AtmosParams | None = None, phi=None, Bx=None, By=None, Bz=None, p=None, rho=None) -> int:
+    r = Request(nx, ny, nz, Lx, Ly, Lz, alpha, xi if xi is not None else XiParams(), atm if atm is not None else
+                AtmosParams(), tol, mode, ptr(bz), ptr(phi), ptr(Bx), ptr(By), ptr(Bz), ptr(p), ptr(rho))
+    t = ctypes.c_longlong()
+    _check(LIB.mhs_server_submit(server, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def mhs_server_poll(server, ticket):
+    """Returns None while running, else (info dict, status, latency_ms)."""
+    done, info, st, lat = _I(), SolveInfo(), _I(), _D()
+    _check(LIB.mhs_server_poll(server, ticket, ctypes.byref(done), ctypes.byref(info), ctypes.byref(st),
+                               ctypes.byref(lat)))
+    return (info.as_dict(), st.value, lat.value) if done.value else None
+
+
+def mhs_server_wait(server, ticket, timeout_s=0.0):
+    info, st, lat = SolveInfo(), _I(), _D()
+    _check(LIB.mhs_server_wait(server, ticket, timeout_s, ctypes.byref(info), ctypes.byref(st), ctypes.byref(lat)))
+    return info.as_dict(), st.value, lat.value
+
+
+def mhs_server_stats(server) -> dict:
+    s = ServerStats()
+    _check(LIB.mhs_server_stats(server, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def mhs_server_destroy(server) -> None:
+    LIB.mhs_server_destroy(server)
 
 
 def mhs_status_string(s: int) -> str:
