@@ -151,6 +151,21 @@ def run_reference(args):
 # GPU arm
 # --------------------------------------------------------------------------
 
+def aggregate(ms_local: float, unknowns_per_rank: int, world: int, device=None):
+    """Whole-job rate of the replicas layout: every rank solves its own
+    instances, the step time is the maximum over ranks (one all-reduce of a
+    scalar; no collective on the data path), and the value counts the unknowns
+    of all ranks.  Returns (max step ms, unknowns per second)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, unknowns_per_rank * world / (ms * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -196,8 +211,9 @@ def run_gpu(args):
     xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
     h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
     M.mhs_set_stream(h, stream)
-    if args.eager:
-        M.mhs_set_options(h, flags=M.MHS_FLAG_NO_GRAPH)
+    flags = (M.MHS_FLAG_NO_GRAPH if args.eager else 0) | (M.MHS_FLAG_NO_FMG if args.no_fmg else 0)
+    if flags:
+        M.mhs_set_options(h, flags=flags)
     shape = (pr["nz"], pr["ny"], pr["nx"])
     bz_dev = [torch.from_numpy(b).to(dev) for b in mags]
     outs_dev = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(6)]
@@ -227,10 +243,7 @@ def run_gpu(args):
             ev[s][1].record(stream)
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev) / K
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms, _ = aggregate(ms, 0, world, dev)
         return ms, infos
 
     for s in range(args.warmup):
@@ -268,7 +281,7 @@ def run_gpu(args):
     avg_ms = dom["ms"] / dom["launches"]
     gbs = dom["bytes"] / dom["launches"] / (avg_ms * 1e-3) / 1e9
     tfl = dom["flops"] / dom["launches"] / (avg_ms * 1e-3) / 1e12
-    alu_bound = dom["name"].endswith("64") or dom["name"] in ("fields", "residual_mixed")
+    alu_bound = dom["name"].endswith("64") or dom["name"] == "fields"   # FP64-pipe-bound kernels
     traffic = profiled_traffic(dom["name"])
     if alu_bound:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS,
@@ -600,6 +613,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving leg")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven kernel-by-kernel solve instead of the captured graph (for launch lists)")
+    ap.add_argument("--no-fmg", action="store_true",
+                    help="start each solve from zero with a plain V-cycle instead of a full-multigrid cycle")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mhs":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -105,11 +105,20 @@ typedef struct {
     int cut64;           /* FP64: largest interior node count of a level solved, with all coarser levels, by
                             the one-CTA shared-memory sub-cycle [1200] */
     int cut32;           /* same for FP32 levels [4000] */
+    int fused_min;       /* FP32 3D levels with at least this many interior nodes use the fused, TMA-staged
+                            red-black sweep (one pass per sweep, HBM-bound); smaller, cache-resident levels use the
+                            two colour passes, which have less latency [8000000] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
 #define MHS_FLAG_BZ_MIMETIC 2   /* B_z = -(D_x D_x + D_y D_y) P with the first-difference operators,
                                    which makes the central-difference div B vanish to rounding */
+#define MHS_FLAG_FUSED_SWEEP64 8 /* FP64 3D levels also use the fused out-of-place red-black sweep (one pass per
+                                    sweep; FP32 levels always do); default: the two in-place colour passes, which
+                                    spend no FP64 work on redundant halo updates */
+#define MHS_FLAG_NO_FMG 32      /* start from P = 0 with plain V-cycles instead of a full-multigrid first cycle */
+#define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
+                                   results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
                                    one captured CUDA graph (same kernels, same results; for profilers that cannot
                                    see kernels inside conditional graph nodes) */
@@ -291,8 +300,8 @@ MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int pr
 #define MHS_KT_PROLONG32 7
 #define MHS_KT_COARSE64 8
 #define MHS_KT_COARSE32 9
-#define MHS_KT_RESID_MIXED 10  /* FP64 residual rounded to the FP32 right-hand side */
-#define MHS_KT_CORRECT 11      /* P64 += e32 */
+#define MHS_KT_RESID_MIXED 10  /* double-float outer residual rounded to the FP32 right-hand side */
+#define MHS_KT_CORRECT 11      /* (hi, lo) += e32, the double-float iterate */
 #define MHS_KT_FIELDS 12       /* B, p, rho */
 #define MHS_KT_OTHER 13        /* set-up, copies, norms of the right-hand side */
 #define MHS_KT_COUNT 14

@@ -50,7 +50,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 8000000}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -61,6 +61,7 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->inner_cycles > 0) o->inner_cycles = in->inner_cycles;
     if (in->cut64 > 0) o->cut64 = in->cut64;
     if (in->cut32 > 0) o->cut32 = in->cut32;
+    if (in->fused_min > 0) o->fused_min = in->fused_min;
     o->flags = in->flags;
 }
 
@@ -347,12 +348,16 @@ mhs_status mhs_level_write(mhs_handle h, int dim, int level, int field, int prec
         if (prec == MHS_FP64) {
             double* d = field == MHS_FIELD_U ? H.d[level].u : field == MHS_FIELD_F ? H.d[level].f : H.d[level].r;
             to_pitched(g, d, src, rows, h->stream);
+            if (field == MHS_FIELD_U)   // the sweep twin carries the same (Dirichlet) boundary values
+                MHS_CUDA(cudaMemcpyAsync(H.d[level].t, d, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         } else {
             float* d = field == MHS_FIELD_U ? H.s[level].u : field == MHS_FIELD_F ? H.s[level].f : H.s[level].r;
             mhs::ensure_staging(h);
             MHS_CUDA(cudaMemsetAsync(h->staging, 0, g.n * sizeof(double), h->stream));
             to_pitched(g, h->staging, src, rows, h->stream);
             mhs::launch_d2f(h->staging, d, g.n, h->stream);
+            if (field == MHS_FIELD_U)
+                MHS_CUDA(cudaMemcpyAsync(H.s[level].t, d, g.n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
         }
         MHS_CUDA(cudaStreamSynchronize(h->stream));
         return MHS_OK;
@@ -394,7 +399,7 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
         auto run = [&](auto& A, auto& C, auto tag) {
             using T = decltype(tag);
             switch (op) {
-            case MHS_OP_SMOOTH: mhs::launch_smooth<T>(g, dim, A.coef, A.u, A.f, st); break;
+            case MHS_OP_SMOOTH: mhs::smooth_hook<T>(h, H, level); break;
             case MHS_OP_RESIDUAL:
                 mhs::launch_residual<T>(g, dim, A.coef, A.u, A.f, A.r, nullptr, 0, st);
                 break;

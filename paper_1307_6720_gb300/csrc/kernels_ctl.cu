@@ -43,9 +43,11 @@ __global__ void check_kernel(const double* __restrict__ partial, int n, SolveCtl
         const double rn = sqrt(s);
         const double b = ctl->bnorm;
         const double rel = b > 0.0 ? rn / b : 0.0;
-        if (!first) ctl->cycles += 1;
+        // first = 1: the initial test; first = 2: after the full-multigrid cycle of the prologue, which
+        // counts as a cycle only if the initial test asked for one
+        if (first == 0 || (first == 2 && ctl->cont)) ctl->cycles += 1;
         ctl->rel = rel;
-        if (first) ctl->rel0 = rel;
+        if (first == 1) ctl->rel0 = rel;
         int cont = (b > 0.0 && rel >= ctl->tol && ctl->cycles < ctl->max_cycles) ? 1 : 0;
         if (!isfinite(rn)) {
             ctl->status = MHS_ERR_NONFINITE;

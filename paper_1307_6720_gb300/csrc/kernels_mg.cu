@@ -162,30 +162,6 @@ __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, c
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
 }
 
-// Mixed precision: r64 = f - A u in FP64, stored rounded to FP32 (the
-// right-hand side of the FP32 correction equation) plus norm partials.
-template <bool D3>
-__global__ void residual_f32_kernel(Geom g, const PlaneCoef<double>* __restrict__ coef, const double* __restrict__ u,
-                                    const double* __restrict__ f, float* __restrict__ r32, double* __restrict__ partial) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    double acc = 0.0;
-    if (i <= g.nx - 2 && j <= g.ny - 2) {
-        for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
-            const PlaneCoef<double> c = coef[k];
-            const size_t o = at(g, i, j, k);
-            double au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
-            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
-            const double rv = (f ? f[o] : 0.0) - au;
-            r32[o] = float(rv);
-            acc += rv * rv;
-        }
-    }
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-}
-
 __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
     // one block, fixed summation order: thread t sums t, t+blockDim, ...; then a fixed tree
     double s = 0.0;
@@ -343,16 +319,6 @@ __global__ void lower_rhs_kernel(Geom g, const double* __restrict__ bz, double* 
     f[o] = -bz[o];
 }
 
-__global__ void add_correction_kernel(Geom g, int d3, const float* __restrict__ e, double* __restrict__ u) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    for (int k = d3 ? 1 + blockIdx.z : 0; k <= (d3 ? g.nz - 2 : 0); k += gridDim.z) {
-        const size_t o = at(g, i, j, k);
-        u[o] += double(e[o]);
-    }
-}
-
 template <typename T>
 __global__ void zero_interior_kernel(Geom g, int d3, T* __restrict__ u) {
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,17 +437,6 @@ void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t 
     MHS_CUDA(cudaGetLastError());
 }
 
-int launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u, const double* f,
-                           float* r32, double* partial, int max_blocks, cudaStream_t st) {
-    const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, std::min(max_blocks, 152 * 8));
-    if (d3) residual_f32_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
-    else residual_f32_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r32, partial);
-    count_launches(1);
-    MHS_CUDA(cudaGetLastError());
-    return int(grid.x * grid.y * grid.z);
-}
-
 template <typename T>
 void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st) {
     const int d3 = dim == 3;
@@ -526,14 +481,6 @@ void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
 void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st) {
     const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
     lower_rhs_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, f64);
-    count_launches(1);
-    MHS_CUDA(cudaGetLastError());
-}
-
-void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cudaStream_t st) {
-    const int d3 = dim == 3;
-    const dim3 grid = grid_for(g, d3, g.nx - 2, 0);
-    add_correction_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, d3, e, u);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }

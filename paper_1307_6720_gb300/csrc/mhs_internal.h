@@ -1,6 +1,7 @@
 // Internal declarations of libmhs (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -61,7 +62,22 @@ struct LevelArrays {
     T* u = nullptr;               // iterate (finest interior level: P, with Dirichlet data on the boundary)
     T* f = nullptr;               // right-hand side
     T* r = nullptr;               // residual
+    T* t = nullptr;               // second iterate buffer for out-of-place sweeps (same boundary values as u)
     PlaneCoef<T>* coef = nullptr; // nz entries (device)
+};
+
+// Per-plane coefficients of the finest level as double-float pairs
+// (value = hi + lo, each an FP32 word) for the FP32-only outer residual of
+// mixed mode.
+struct PlaneCoefDF {
+    float cxh, cxl, cyh, cyl, czh, czl, dh, dl;
+};
+
+// Finest-level state of mixed mode: the outer iterate P = hi + lo and the
+// right-hand side f = fh + fl as double-float pairs (FP32 words).
+struct DFState {
+    float *hi = nullptr, *lo = nullptr, *fh = nullptr, *fl = nullptr;
+    PlaneCoefDF* coef = nullptr;
 };
 
 struct Hierarchy {
@@ -70,6 +86,9 @@ struct Hierarchy {
     std::vector<LevelArrays<double>> d;   // FP64 arrays
     std::vector<LevelArrays<float>> s;    // FP32 arrays
     int cut64 = 0, cut32 = 0;             // first level handled by the one-CTA sub-cycle (per precision)
+    DFState df;                           // finest-level double-float state (mixed mode)
+    // TMA plane maps of the FP32 arrays u, t, f per level (3D levels; see kernels_tma.cu)
+    std::vector<CUtensorMap> tm_u, tm_t, tm_f;
     int nlev() const { return int(g.size()); }
 };
 
@@ -210,10 +229,6 @@ template <typename T>
 void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
 // lower-boundary right-hand side f = -B_z at interior nodes (FP64 and FP32 copies)
 void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st);
-// mixed precision pieces
-int launch_residual_to_f32(const Geom& g, int dim, const PlaneCoef<double>* coef, const double* u,
-                           const double* f, float* r32, double* partial, int max_blocks, cudaStream_t st);
-void launch_add_correction(const Geom& g, int dim, const float* e, double* u, cudaStream_t st);
 template <typename T>
 void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st);
 void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st);
@@ -221,6 +236,15 @@ void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStre
 // norm^2 of the lifted right-hand side of the interior problem: cz * P[k=0] on plane k=1
 int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, double* partial,
                      cudaStream_t st);
+
+// ---- fused out-of-place red-black sweep (kernels_sweep.cu) ----
+template <typename T>
+void launch_sweep(const Geom& g, const PlaneCoef<T>* coef, const T* uin, const T* f, T* uout, cudaStream_t st);
+
+// ---- TMA-staged fused sweep for FP32 levels (kernels_tma.cu) ----
+void make_plane_map(CUtensorMap* map, const Geom& g, const float* base);
+void launch_sweep_tma(const Geom& g, const CUtensorMap& tm_in, const CUtensorMap& tm_f,
+                      const PlaneCoef<float>* coef, float* uout, int* err, cudaStream_t st);
 
 // ---- control and sub-cycle (kernels_ctl.cu) ----
 void launch_bnorm(const double* partial, int n, SolveCtl* ctl, cudaStream_t st);
@@ -230,6 +254,21 @@ size_t subcycle_smem_limit();
 void subcycle_prepare();
 template <typename T>
 void launch_subcycle(const SubParams<T>& p, cudaStream_t st);
+
+// ---- double-float outer loop of mixed mode (kernels_df.cu) ----
+void launch_df_coef(const Geom& g, const PlaneCoef<double>* coef, PlaneCoefDF* cdf, cudaStream_t st);
+// (fh, fl) <- f (double) at interior nodes (f == nullptr: zero)
+void launch_df_split(const Geom& g, int dim, const double* f, float* hi, float* lo, cudaStream_t st);
+// r32 = fh + fl - A (hi + lo) rounded to FP32, with per-block partial sums of r32^2; returns the partial count
+int launch_df_residual(const Geom& g, int dim, const PlaneCoefDF* cdf, const float* hi, const float* lo,
+                       const float* fh, const float* fl, float* r32, double* partial, int max_blocks, cudaStream_t st);
+// (hi, lo) += e at interior nodes
+void launch_df_correct(const Geom& g, int dim, const float* e, float* hi, float* lo, cudaStream_t st);
+// P = hi + lo (double) at every node
+void launch_df_to_double(const Geom& g, const float* hi, const float* lo, double* P, cudaStream_t st);
+// plane k = 0 of a 3D double-float pair from a 2D pair
+void launch_df_copy_plane(const Geom& g2, const float* hi2, const float* lo2, const Geom& g3, float* hi3, float* lo3,
+                          cudaStream_t st);
 
 // ---- fields (kernels_fields.cu) ----
 void launch_fields(const Geom& g, double alpha, const mhs_atmos_params& atm, const double* prof,

@@ -92,14 +92,32 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
         d.u = static_cast<double*>(dev_alloc(c, g.n * sizeof(double)));
         d.f = static_cast<double*>(dev_alloc(c, g.n * sizeof(double)));
         d.r = static_cast<double*>(dev_alloc(c, g.n * sizeof(double)));
+        d.t = static_cast<double*>(dev_alloc(c, g.n * sizeof(double)));
         d.coef = static_cast<PlaneCoef<double>*>(dev_alloc(c, g.nz * sizeof(PlaneCoef<double>)));
         s.u = static_cast<float*>(dev_alloc(c, g.n * sizeof(float)));
         s.f = static_cast<float*>(dev_alloc(c, g.n * sizeof(float)));
         s.r = static_cast<float*>(dev_alloc(c, g.n * sizeof(float)));
+        s.t = static_cast<float*>(dev_alloc(c, g.n * sizeof(float)));
         s.coef = static_cast<PlaneCoef<float>*>(dev_alloc(c, g.nz * sizeof(PlaneCoef<float>)));
         H.d.push_back(d);
         H.s.push_back(s);
     }
+    if (dim == 3) {
+        H.tm_u.resize(H.g.size());
+        H.tm_t.resize(H.g.size());
+        H.tm_f.resize(H.g.size());
+        for (size_t l = 0; l < H.g.size(); ++l) {
+            make_plane_map(&H.tm_u[l], H.g[l], H.s[l].u);
+            make_plane_map(&H.tm_t[l], H.g[l], H.s[l].t);
+            make_plane_map(&H.tm_f[l], H.g[l], H.s[l].f);
+        }
+    }
+    const Geom& g0 = H.g[0];
+    H.df.hi = static_cast<float*>(dev_alloc(c, g0.n * sizeof(float)));
+    H.df.lo = static_cast<float*>(dev_alloc(c, g0.n * sizeof(float)));
+    H.df.fh = static_cast<float*>(dev_alloc(c, g0.n * sizeof(float)));
+    H.df.fl = static_cast<float*>(dev_alloc(c, g0.n * sizeof(float)));
+    H.df.coef = static_cast<PlaneCoefDF*>(dev_alloc(c, g0.nz * sizeof(PlaneCoefDF)));
 }
 
 void choose_cuts(mhs_ctx* c) {
@@ -115,6 +133,7 @@ void compute_coefficients(mhs_ctx* c) {
             launch_coef<double>(H->g[l], H->dim, c->alpha, c->xi, H->d[l].coef, c->stream);
             launch_coef<float>(H->g[l], H->dim, c->alpha, c->xi, H->s[l].coef, c->stream);
         }
+        launch_df_coef(H->g[0], H->d[0].coef, H->df.coef, c->stream);
     }
     launch_profiles(c->h3.g[0], c->xi, c->atm, c->prof, c->stream);
 }
@@ -208,6 +227,35 @@ void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
     launch_subcycle<T>(p, c->stream);
 }
 
+// n red-black sweeps on level l.  3D levels use the fused out-of-place sweep
+// (always for FP32, for FP64 with MHS_FLAG_FUSED_SWEEP64), alternating between
+// u and its twin t; otherwise the two colour passes run in place.
+template <typename T>
+static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fine, double bytes, double flops) {
+    LevelArrays<T>& A = arrays<T>(H, l);
+    const Geom& g = H.g[l];
+    const bool dbl = sizeof(T) == 8;
+    const bool fused = H.dim == 3 && A.t &&
+                       (dbl ? (c->opts.flags & MHS_FLAG_FUSED_SWEEP64) != 0
+                            : g.interior() >= size_t(c->opts.fused_min));
+    // FP32 3D levels stage their planes by TMA (maps of u, t and f built at creation)
+    const bool tma = fused && !dbl && !H.tm_u.empty() && !(c->opts.flags & MHS_FLAG_NO_TMA) &&
+                     f == reinterpret_cast<const T*>(H.s[l].f);
+    for (int q = 0; q < n; ++q) {
+        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, bytes, flops, c->stream, fine);
+        const bool even = (q & 1) == 0;
+        if (tma) {
+            launch_sweep_tma(g, even ? H.tm_u[l] : H.tm_t[l], H.tm_f[l], H.s[l].coef, even ? H.s[l].t : H.s[l].u,
+                             c->flag + 1, c->stream);
+        } else if (fused) {
+            launch_sweep<T>(g, A.coef, even ? A.u : A.t, f, even ? A.t : A.u, c->stream);
+        } else {
+            launch_smooth<T>(g, H.dim, A.coef, A.u, f, c->stream);
+        }
+    }
+    if (fused && (n & 1)) MHS_CUDA(cudaMemcpyAsync(A.u, A.t, g.n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+}
+
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
@@ -225,10 +273,7 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     const T* f = f_zero ? nullptr : A.f;
     const double upd_flops = H.dim == 3 ? 10.0 : 7.0;
     const bool fine = H.dim == 3 && l == 0;
-    for (int q = 0; q < c->opts.nu1; ++q) {
-        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st, fine);
-        launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
-    }
+    smooth_n<T>(c, H, l, f, c->opts.nu1, fine, N * (2 * s + fs), N * upd_flops);
     {
         TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st, fine);
         launch_residual<T>(g, H.dim, A.coef, A.u, f, A.r, nullptr, 0, st);
@@ -245,9 +290,43 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
         TimedScope t(c->timer, dbl ? MHS_KT_PROLONG64 : MHS_KT_PROLONG32, (2 * N + Nc) * s, 4.0 * N, st, fine);
         launch_prolong<T>(H.g[l + 1], g, H.dim, C.u, A.u, st);
     }
-    for (int q = 0; q < c->opts.nu2; ++q) {
-        TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, N * (2 * s + fs), N * upd_flops, st, fine);
-        launch_smooth<T>(g, H.dim, A.coef, A.u, f, st);
+    smooth_n<T>(c, H, l, f, c->opts.nu2, fine, N * (2 * s + fs), N * upd_flops);
+}
+
+template <typename T>
+void smooth_hook(mhs_ctx* c, Hierarchy& H, int l) {
+    const Geom& g = H.g[l];
+    smooth_n<T>(c, H, l, arrays<T>(H, l).f, 1, false, 0.0, 0.0);
+    (void)g;
+}
+template void smooth_hook<double>(mhs_ctx*, Hierarchy&, int);
+template void smooth_hook<float>(mhs_ctx*, Hierarchy&, int);
+
+// Full multigrid for the correction equation A e = r0 of level 0 (standard
+// FMG with one V-cycle per level): r0 is restricted down the hierarchy
+// (full weighting, coarse iterates zeroed), the coarsest part is solved by
+// one V-cycle from the sub-cycle cut-off (or the coarsest level), and on the
+// way up each level starts from the interpolated coarser solution and runs
+// one V-cycle.  Level 0 adds the interpolated correction to its iterate
+// (FP64: P itself with f; mixed: the FP32 correction e, zeroed beforehand)
+// and runs its V-cycle on its own right-hand side.
+template <typename T>
+void fmg(mhs_ctx* c, Hierarchy& H, const T* r0) {
+    const int L = H.nlev();
+    if (L < 2) {
+        vcycle<T>(c, H, 0);
+        return;
+    }
+    cudaStream_t st = c->stream;
+    launch_restrict<T>(H.g[0], H.g[1], H.dim, r0, arrays<T>(H, 1).f, arrays<T>(H, 1).u, st);
+    const int top = std::min(std::max(cut_of<T>(H), 1), L - 1);
+    for (int l = 1; l < top; ++l)
+        launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, arrays<T>(H, l).f, arrays<T>(H, l + 1).f,
+                           arrays<T>(H, l + 1).u, st);
+    vcycle<T>(c, H, top);
+    for (int l = top - 1; l >= 0; --l) {
+        launch_prolong<T>(H.g[l + 1], H.g[l], H.dim, arrays<T>(H, l + 1).u, arrays<T>(H, l).u, st);
+        vcycle<T>(c, H, l);
     }
 }
 
@@ -284,8 +363,12 @@ static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
     const double fb = (H.dim == 3 && c->f_zero_finest) ? 0.0 : 8.0;
     const double fl = H.dim == 3 ? 11.0 : 8.0;
     if (mode == MHS_MIXED) {
-        TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + fb + 4.0), N * fl, c->stream, H.dim == 3);
-        return launch_residual_to_f32(g, H.dim, A.coef, A.u, A.f, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
+        // double-float residual of P = hi + lo, rounded into the FP32 right-hand side
+        const bool fz = H.dim == 3 && c->f_zero_finest;
+        TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + (fz ? 0.0 : 8.0) + 4.0), N * 70.0, c->stream,
+                     H.dim == 3);
+        return launch_df_residual(g, H.dim, H.df.coef, H.df.hi, H.df.lo, fz ? nullptr : H.df.fh,
+                                  fz ? nullptr : H.df.fl, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
     }
     TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream, H.dim == 3);
     return launch_residual<double>(g, H.dim, A.coef, A.u, A.f, A.r, c->ns.partial, c->ns.max_blocks, c->stream);
@@ -297,9 +380,9 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     if (e.mode == MHS_MIXED) {
         MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
         for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
-        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()), c->stream,
+        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()) * 8.0, c->stream,
                      H.dim == 3);
-        launch_add_correction(g, H.dim, H.s[0].u, H.d[0].u, c->stream);
+        launch_df_correct(g, H.dim, H.s[0].u, H.df.hi, H.df.lo, c->stream);
     } else {
         vcycle<double>(c, H, 0);
     }
@@ -307,31 +390,86 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     launch_check(c->ns.partial, nb, ctl, 0, e.hnd, e.graph ? 1 : 0, c->stream);
 }
 
+// First cycle of a solve by full multigrid (skipped with MHS_FLAG_NO_FMG):
+// FP64 mode corrects P from its residual in A.r, mixed mode builds the FP32
+// correction from the double-float residual in S.f.  It runs right after the
+// first convergence test; when that test already passed, the kernels still
+// run (a zero or tiny correction) but no cycle is counted.
+static void fmg_cycle(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
+    mhs_ctx* c = e.c;
+    if (c->opts.flags & MHS_FLAG_NO_FMG) return;
+    const Geom& g = H.g[0];
+    if (e.mode == MHS_MIXED) {
+        MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
+        fmg<float>(c, H, H.s[0].f);
+        TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()) * 8.0, c->stream,
+                     H.dim == 3);
+        launch_df_correct(g, H.dim, H.s[0].u, H.df.hi, H.df.lo, c->stream);
+    } else {
+        fmg<double>(c, H, H.d[0].r);
+    }
+    const int nb = residual_partials(c, H, e.mode);
+    launch_check(c->ns.partial, nb, ctl, 2, e.hnd, e.graph ? 1 : 0, c->stream);
+}
+
 static void prologue_2d(const Enq& e) {
     mhs_ctx* c = e.c;
     Hierarchy& H = c->h2;
     const Geom& g = H.g[0];
-    TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
-    MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
-    launch_lower_rhs(g, c->bz, H.d[0].f, c->stream);
-    // with u = 0 the residual is the right-hand side: its norm is ||b||
-    const int nb = residual_partials(c, H, e.mode);
-    launch_bnorm(c->ns.partial, nb, c->ctl + 0, c->stream);
-    launch_check(c->ns.partial, nb, c->ctl + 0, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+    {
+        TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
+        MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
+        launch_lower_rhs(g, c->bz, H.d[0].f, c->stream);
+        if (e.mode == MHS_MIXED) {
+            MHS_CUDA(cudaMemsetAsync(H.df.hi, 0, g.n * sizeof(float), c->stream));
+            MHS_CUDA(cudaMemsetAsync(H.df.lo, 0, g.n * sizeof(float), c->stream));
+            launch_df_split(g, 2, H.d[0].f, H.df.fh, H.df.fl, c->stream);
+        }
+        // with u = 0 the residual is the right-hand side: its norm is ||b||
+        const int nb = residual_partials(c, H, e.mode);
+        launch_bnorm(c->ns.partial, nb, c->ctl + 0, c->stream);
+        launch_check(c->ns.partial, nb, c->ctl + 0, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+    }
+    // the first cycle's kernels are timed under their own kinds
+    fmg_cycle(e, H, c->ctl + 0);
 }
 
 static void prologue_3d(const Enq& e) {
     mhs_ctx* c = e.c;
     Hierarchy& H = c->h3;
     const Geom& g = H.g[0];
-    TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
-    // P = 0 everywhere (Sect. 2.2, step 1), unless a warm start keeps the resident iterate
-    if (!(c->opts.flags & MHS_FLAG_WARM)) MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
-    launch_copy_plane(c->h2.g[0], c->h2.d[0].u, g, H.d[0].u, c->stream);
-    const int nl = launch_lift_norm(g, H.d[0].coef, H.d[0].u, c->ns.partial, c->stream);
-    launch_bnorm(c->ns.partial, nl, c->ctl + 1, c->stream);
-    const int nb = residual_partials(c, H, e.mode);
-    launch_check(c->ns.partial, nb, c->ctl + 1, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+    {
+        TimedScope t(c->timer, MHS_KT_OTHER, 0.0, 0.0, c->stream);
+        // P = 0 everywhere (Sect. 2.2, step 1), unless a warm start keeps the resident iterate
+        const bool warm = c->opts.flags & MHS_FLAG_WARM;
+        if (!warm) MHS_CUDA(cudaMemsetAsync(H.d[0].u, 0, g.n * sizeof(double), c->stream));
+        launch_copy_plane(c->h2.g[0], c->h2.d[0].u, g, H.d[0].u, c->stream);
+        // the twin of u used by out-of-place sweeps carries the same Dirichlet data
+        launch_copy_plane(c->h2.g[0], c->h2.d[0].u, g, H.d[0].t, c->stream);
+        if (e.mode == MHS_MIXED) {
+            if (warm) {
+                launch_df_split(g, 3, H.d[0].u, H.df.hi, H.df.lo, c->stream);
+            } else {
+                MHS_CUDA(cudaMemsetAsync(H.df.hi, 0, g.n * sizeof(float), c->stream));
+                MHS_CUDA(cudaMemsetAsync(H.df.lo, 0, g.n * sizeof(float), c->stream));
+            }
+            launch_df_copy_plane(c->h2.g[0], c->h2.df.hi, c->h2.df.lo, g, H.df.hi, H.df.lo, c->stream);
+            if (!c->f_zero_finest) launch_df_split(g, 3, H.d[0].f, H.df.fh, H.df.fl, c->stream);
+        }
+        const int nl = launch_lift_norm(g, H.d[0].coef, H.d[0].u, c->ns.partial, c->stream);
+        launch_bnorm(c->ns.partial, nl, c->ctl + 1, c->stream);
+        const int nb = residual_partials(c, H, e.mode);
+        launch_check(c->ns.partial, nb, c->ctl + 1, 1, e.hnd, e.graph ? 1 : 0, c->stream);
+    }
+    fmg_cycle(e, H, c->ctl + 1);
+}
+
+// Mixed mode keeps the finest iterate as a double-float pair; after the
+// cycles it becomes the FP64 solution P that the rest of the library reads.
+static void epilogue(const Enq& e, Hierarchy& H) {
+    if (e.mode != MHS_MIXED) return;
+    TimedScope t(e.c->timer, MHS_KT_OTHER, 0.0, 0.0, e.c->stream);
+    launch_df_to_double(H.g[0], H.df.hi, H.df.lo, H.d[0].u, e.c->stream);
 }
 
 // Append a while node to the graph being captured on c->stream whose body
@@ -386,15 +524,18 @@ static void build_graph(mhs_ctx* c, int mode) {
         const long long l1 = launches();
         add_while(c, h2, [&] { cycle_body(e2, c->h2, c->ctl + 0); });
         const long long l2 = launches();
+        epilogue(e2, c->h2);
         prologue_3d(e3);
         const long long l3 = launches();
         add_while(c, h3, [&] { cycle_body(e3, c->h3, c->ctl + 1); });
         const long long l4 = launches();
-        count_launches(-(l4 - l0));   // capture records kernels without running them
-        c->gcount[mode][0] = l1 - l0;
-        c->gcount[mode][1] = l2 - l1;
-        c->gcount[mode][2] = l3 - l2;
-        c->gcount[mode][3] = l4 - l3;
+        epilogue(e3, c->h3);
+        const long long l5 = launches();
+        count_launches(-(l5 - l0));   // capture records kernels without running them
+        c->gcount[mode][0] = (l1 - l0) + (l3 - l2) + (l5 - l4);   // run once per solve
+        c->gcount[mode][1] = l2 - l1;                             // per lower-boundary cycle
+        c->gcount[mode][2] = 0;
+        c->gcount[mode][3] = l4 - l3;                             // per interior cycle
         MHS_CUDA(cudaStreamEndCapture(c->stream, &graph));
         MHS_CUDA(cudaGraphInstantiate(&c->gexec[mode], graph, 0));
         cudaGraphDestroy(graph);
@@ -426,6 +567,7 @@ void solve_begin(mhs_ctx* c, double tol, int mode) {
         c->ctl_host[q].max_cycles = c->opts.max_cycles;
     }
     MHS_CUDA(cudaMemcpyAsync(c->ctl, c->ctl_host, 2 * sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
+    MHS_CUDA(cudaMemsetAsync(c->flag + 1, 0, sizeof(int), st));   // bounded-wait expiry flag of the kernels
     MHS_CUDA(cudaEventRecord(c->ev0, st));
     c->pending_graph = c->use_graphs && !c->timer.enabled && !(c->opts.flags & MHS_FLAG_NO_GRAPH);
     if (c->pending_graph) {
@@ -439,11 +581,14 @@ void solve_begin(mhs_ctx* c, double tol, int mode) {
         Enq e{c, mode, false, 0};
         prologue_2d(e);
         while (read_cont(c, 0)) cycle_body(e, c->h2, c->ctl + 0);
+        epilogue(e, c->h2);
         prologue_3d(e);
         while (read_cont(c, 1)) cycle_body(e, c->h3, c->ctl + 1);
+        epilogue(e, c->h3);
     }
     MHS_CUDA(cudaEventRecord(c->ev1, st));
     MHS_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl, 2 * sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+    MHS_CUDA(cudaMemcpyAsync(c->flag_host + 1, c->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
 }
 
 // Wait for the solve enqueued by solve_begin and report it.
@@ -467,6 +612,7 @@ mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
         info->ms = ms;
     }
     c->have_solution = true;
+    if (c->flag_host[1]) throw Error(MHS_ERR_TIMEOUT, "a kernel's bounded wait for its TMA loads expired");
     if (a.status != MHS_OK || b.status != MHS_OK) throw Error(MHS_ERR_NONFINITE, "non-finite residual norm");
     const bool ok2 = a.bnorm == 0.0 || a.rel < tol;
     const bool ok3 = b.bnorm == 0.0 || b.rel < tol;

@@ -22,6 +22,8 @@ mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info);
 mhs_status batch_solve(mhs_ctx** hs, int n, double tol, int mode, mhs_solve_info* infos, mhs_status* statuses);
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l);
+template <typename T>
+void smooth_hook(mhs_ctx* c, Hierarchy& H, int l);   // one sweep as the V-cycle runs it
 double read_norm2(mhs_ctx* c, int slot);
 void ensure_field_buffers(mhs_ctx* c);
 void ensure_staging(mhs_ctx* c);

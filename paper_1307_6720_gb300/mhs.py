@@ -22,7 +22,8 @@ STATUS_NAMES = ["MHS_OK", "MHS_ERR_INVALID_ARG", "MHS_ERR_NOT_ELLIPTIC", "MHS_ER
  MHS_ERR_NONFINITE, MHS_ERR_BAD_STATE, MHS_ERR_TIMEOUT, MHS_ERR_REJECTED) = range(1, 10)
 MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
 MHS_FP64, MHS_MIXED = 0, 1
-MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH = 1, 2, 4
+MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, MHS_FLAG_NO_TMA, MHS_FLAG_NO_FMG = \
+    1, 2, 4, 8, 16, 32
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
 
@@ -40,7 +41,7 @@ class AtmosParams(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int), ("cut64", ctypes.c_int),
-                ("cut32", ctypes.c_int)]
+                ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -188,8 +189,8 @@ def mhs_set_stream(h, stream) -> None:
     _check(LIB.mhs_set_stream(h, stream))
 
 
-def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0) -> None:
-    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32)
+def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0, fused_min=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min)
     _check(LIB.mhs_set_options(h, ctypes.byref(o)))
 
 

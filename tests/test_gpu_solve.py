@@ -300,3 +300,62 @@ def test_no_graph_flag_matches_graph(M):
         M.mhs_destroy(h)
         out.append(phi)
     assert np.array_equal(out[0], out[1])
+
+
+def test_mixed_mode_reaches_fp64_class_residual(M):
+    """The outer residual of mixed mode is evaluated in double-float
+    arithmetic (pairs of FP32 words), so defect correction with FP32 V-cycles
+    drives the relative residual far below FP32 rounding, to 1e-12, and the
+    result then matches the exact discrete solution like FP64 mode does."""
+    pr, bz = S.linear_mhs(65, seed=15)
+    info, got = _gpu_solve(M, pr, bz, 1e-12, M.MHS_MIXED)
+    assert info["rel_res_3d"] < 1e-12 and info["rel_res_2d"] < 1e-12
+    _compare(got, _oracle(pr, bz), 2e-10)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_multigrid_start_saves_cycles_same_solution(M, mode):
+    """The full-multigrid first cycle (default) reaches the tolerance in fewer
+    cycles than plain V-cycles from P = 0, and both match the exact discrete
+    solution."""
+    pr, bz = S.linear_mhs(129, seed=18)
+    want = _oracle(pr, bz)
+    info_f, got_f = _gpu_solve(M, pr, bz, 1e-12, mode)
+    info_v, got_v = _gpu_solve(M, pr, bz, 1e-12, mode, opts=dict(flags=M.MHS_FLAG_NO_FMG))
+    assert info_f["cycles_3d"] < info_v["cycles_3d"], (info_f, info_v)
+    assert info_f["cycles_2d"] <= info_v["cycles_2d"]
+    _compare(got_f, want, 1e-9)
+    _compare(got_v, want, 1e-9)
+
+
+_PAPER_XI = {"xi1": dict(xi_kind=1, xi_a=0.7, xi_kappa=0.2),
+             "xi2": dict(xi_kind=2, xi_a=0.7, xi_b=0.3, xi_omega=np.pi, xi_kappa=0.1)}
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("xi", ["xi1", "xi2"])
+def test_paper_two_footpoint_workload(M, xi, mode):
+    """The workload of Sect. 3.2: 129^3 nodes on [-5.5,5.5]^2 x [0,12] (the
+    whole background atmosphere, transition region included), both xi
+    families of Sect. 3.2, alpha = 0.2, two opposite footpoints of width 0.3.
+    Phi, B, p and rho match the exact discrete solution."""
+    n = 129
+    pr = S.problem(n, n, n, Lx=11.0, Ly=11.0, Lz=12.0, alpha=0.2, **_PAPER_XI[xi])
+    sp = [S.Spot(1.0, -1.0, -1.0, 0.3), S.Spot(-1.0, 1.0, 1.0, 0.3)]
+    bz = S.spots_field(n, n, 11.0, 11.0, sp, -5.5, -5.5)
+    info, got = _gpu_solve(M, pr, bz, 1e-13 if mode == 0 else 1e-10, mode, opts=dict(max_cycles=200))
+    _compare(got, _oracle(pr, bz), 1e-10 if mode == 0 else 1e-8)
+
+
+def test_paper_three_source_force_free(M):
+    """Sect. 3.1: xi = 0, alpha = 0.4, three Gaussian sources of width 0.3 on
+    [-5.5,5.5]^2 x [0,12], 65^3 nodes; with xi = 0 the plasma terms vanish and
+    p, rho equal the background atmosphere exactly."""
+    n = 65
+    pr = S.problem(n, n, n, Lx=11.0, Ly=11.0, Lz=12.0, alpha=0.4)
+    bz = S.magnetogram_three_sources(n, n)
+    info, got = _gpu_solve(M, pr, bz, 1e-13, M.MHS_FP64)
+    want = _oracle(pr, bz)
+    _compare(got, want, 1e-10)
+    assert not np.any(want["dp"]) and not np.any(want["drho"])
+    assert rel(got["p"], want["p"]) < 1e-13 and rel(got["rho"], want["rho"]) < 1e-13
