@@ -69,6 +69,8 @@ def _load():
                 "orc_residual3d": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
                 "orc_rbgs3d": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]),
                 "orc_rbgs3d_colour": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]),
+                "orc_zline3d": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]),
+                "orc_zline3d_colour": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]),
                 "orc_residual2d": (None, [_PP, ctypes.c_int, ctypes.c_int, _D, _D, _D]),
                 "orc_rbgs2d": (None, [_PP, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]),
                 "orc_restrict": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
@@ -77,11 +79,17 @@ def _load():
                                                ctypes.c_int, _D, _D]),
                 "orc_solve3d": (ctypes.c_int, [_PP, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, _D, _D, _D]),
+                "orc_solve3d_s": (ctypes.c_int, [_PP, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, _D, _D, _D]),
                 "orc_solve": (ctypes.c_int, [_PP, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(Info)]),
+                "orc_solve_s": (ctypes.c_int, [_PP, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Info)]),
                 "orc_num_levels": (ctypes.c_int, [_PP, ctypes.c_int]),
                 "orc_vcycle": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
                                       ctypes.c_int, ctypes.c_int]),
+                "orc_vcycle_s": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_fields": (None, [_PP, _D, _D, _D, _D, _D, _D, ctypes.c_int]),
                 "orc_profiles": (None, [_PP, _D, _D, _D, _D, _D]),
             }
@@ -160,6 +168,27 @@ def rbgs3d_colour(pr, u, f=None, colour=0):
     return u
 
 
+def zline3d(pr, u, f=None, sweeps=1):
+    """Zebra z-line Gauss-Seidel sweeps (columns with i + j even, then odd,
+    each solved exactly along z); returns the new u."""
+    u = _f64(u).copy(); f = _f64(f)
+    nz, ny, nx = u.shape
+    p = _prob(pr)
+    _load().orc_zline3d(ctypes.byref(p), nx, ny, nz, _ptr(u), _ptr(f), int(sweeps))
+    return u
+
+
+def zline3d_colour(pr, u, f=None, colour=0):
+    u = _f64(u).copy(); f = _f64(f)
+    nz, ny, nx = u.shape
+    p = _prob(pr)
+    _load().orc_zline3d_colour(ctypes.byref(p), nx, ny, nz, _ptr(u), _ptr(f), int(colour))
+    return u
+
+
+SMOOTHERS = {"point": 0, "zline": 1}
+
+
 def residual2d(pr, u, f=None):
     u = _f64(u); f = _f64(f)
     ny, nx = u.shape
@@ -218,42 +247,43 @@ def solve2d(pr, bz, tol=1e-12, max_cycles=200, nu1=2, nu2=2, P0=None):
     return P0, c, rel.value, hist[: c + 1]
 
 
-def solve3d(pr, P, f=None, tol=1e-12, max_cycles=200, nu1=2, nu2=2):
+def solve3d(pr, P, f=None, tol=1e-12, max_cycles=200, nu1=2, nu2=2, smoother="point"):
     """Multigrid solve of eq. (scalar_pot) with Dirichlet data in P's boundary
     entries and optional right-hand side f.  Returns (P, cycles, rel, history, conv)."""
     p = _prob(pr)
     P = _f64(P).copy(); f = _f64(f)
     rel = ctypes.c_double(); conv = ctypes.c_double()
     hist = np.zeros(max_cycles + 1)
-    c = _load().orc_solve3d(ctypes.byref(p), _ptr(P), _ptr(f), tol, max_cycles, nu1, nu2,
-                            ctypes.byref(rel), _ptr(hist), ctypes.byref(conv))
+    c = _load().orc_solve3d_s(ctypes.byref(p), _ptr(P), _ptr(f), tol, max_cycles, nu1, nu2, SMOOTHERS[smoother],
+                              ctypes.byref(rel), _ptr(hist), ctypes.byref(conv))
     return P, c, rel.value, hist[: c + 1], conv.value
 
 
-def solve(pr, bz, tol2d=1e-12, tol3d=1e-12, max_cycles=200, nu1=2, nu2=2):
+def solve(pr, bz, tol2d=1e-12, tol3d=1e-12, max_cycles=200, nu1=2, nu2=2, smoother="point"):
     """The three-step procedure of Sect. 2.2.  Returns (P, info dict)."""
     p = _prob(pr)
     bz = _f64(bz)
     assert bz.shape == (p.ny, p.nx)
     P = np.zeros((p.nz, p.ny, p.nx))
     info = Info()
-    status = _load().orc_solve(ctypes.byref(p), _ptr(bz), _ptr(P), tol2d, tol3d, max_cycles, nu1, nu2,
-                               ctypes.byref(info))
+    status = _load().orc_solve_s(ctypes.byref(p), _ptr(bz), _ptr(P), tol2d, tol3d, max_cycles, nu1, nu2,
+                                 SMOOTHERS[smoother], ctypes.byref(info))
     return P, dict(status=status, cycles_2d=info.cycles_2d, cycles_3d=info.cycles_3d,
                    rel_res_2d=info.rel_res_2d, rel_res_3d=info.rel_res_3d,
                    conv_factor_3d=info.conv_factor_3d)
 
 
-def vcycle(pr, u, f=None, nu1=2, nu2=2):
+def vcycle(pr, u, f=None, nu1=2, nu2=2, smoother="point"):
     """One V-cycle on the grid of u (2D [ny][nx] or 3D [nz][ny][nx]); returns the new u."""
     u = _f64(u).copy(); f = _f64(f)
     p = _prob(pr)
+    sm = SMOOTHERS[smoother]
     if u.ndim == 2:
         ny, nx = u.shape
-        _load().orc_vcycle(ctypes.byref(p), 2, nx, ny, 1, _ptr(u), _ptr(f), nu1, nu2)
+        _load().orc_vcycle_s(ctypes.byref(p), 2, nx, ny, 1, _ptr(u), _ptr(f), nu1, nu2, sm)
     else:
         nz, ny, nx = u.shape
-        _load().orc_vcycle(ctypes.byref(p), 3, nx, ny, nz, _ptr(u), _ptr(f), nu1, nu2)
+        _load().orc_vcycle_s(ctypes.byref(p), 3, nx, ny, nz, _ptr(u), _ptr(f), nu1, nu2, sm)
     return u
 
 

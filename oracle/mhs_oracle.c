@@ -224,6 +224,55 @@ static void rbgs2d(const orc_level* L, double* u, const double* f) {
     rbgs2d_colour(L, u, f, 1);
 }
 
+/* Zebra z-line Gauss-Seidel, the line-relaxation form of the Sect. 4
+ * smoother for strong vertical coupling (xi(z) near 1, or h_z < h_x, where
+ * [1 - xi] (P_xx + P_yy) is small next to P_zz).  The columns (i, j) are
+ * coloured by the parity of i + j.  For every column of the colour, the
+ * nz - 2 interior rows of A u = f along the column are solved exactly for
+ * u(i, j, 1 .. nz-2), with the neighbouring columns and the Dirichlet values
+ * u(i, j, 0), u(i, j, nz-1) held at their current values:
+ *   cz u[k-1] + diag[k] u[k] + cz u[k+1] = f[k] - cx[k] (u_E + u_W) - cy[k] (u_N + u_S).
+ * The tridiagonal system is solved by Gaussian elimination without pivoting
+ * (the Thomas algorithm); -A is symmetric positive definite, so no pivot
+ * vanishes. */
+static void zline3d_colour(const orc_level* L, double* u, const double* f, int colour) {
+    const int nx = L->nx, ny = L->ny, nz = L->nz, m = nz - 2;
+    const size_t plane = (size_t)nx * ny;
+    if (m < 1) return;
+#pragma omp parallel
+    {
+        double* sup = (double*)malloc(sizeof(double) * m);   /* eliminated super-diagonal */
+        double* rhs = (double*)malloc(sizeof(double) * m);   /* eliminated right-hand side */
+#pragma omp for schedule(static)
+        for (int j = 1; j < ny - 1; ++j)
+            for (int i = 1; i < nx - 1; ++i) {
+                if (((i + j) & 1) != colour) continue;
+                for (int t = 0; t < m; ++t) {
+                    const int k = t + 1;
+                    const size_t c = IDX(i, j, k, nx, ny);
+                    double b = (f ? f[c] : 0.0) - L->cx[k] * (u[c + 1] + u[c - 1]) - L->cy[k] * (u[c + nx] + u[c - nx]);
+                    if (k == 1) b -= L->cz * u[c - plane];
+                    if (k == nz - 2) b -= L->cz * u[c + plane];
+                    const double pivot = L->diag[k] - (t > 0 ? L->cz * sup[t - 1] : 0.0);
+                    sup[t] = L->cz / pivot;
+                    rhs[t] = (b - (t > 0 ? L->cz * rhs[t - 1] : 0.0)) / pivot;
+                }
+                for (int t = m - 1; t >= 0; --t) {
+                    const size_t c = IDX(i, j, t + 1, nx, ny);
+                    u[c] = rhs[t] - (t < m - 1 ? sup[t] * u[c + plane] : 0.0);
+                }
+            }
+        free(sup);
+        free(rhs);
+    }
+}
+
+/* A zebra sweep: columns with i + j even first, then odd. */
+static void zline3d(const orc_level* L, double* u, const double* f) {
+    zline3d_colour(L, u, f, 0);
+    zline3d_colour(L, u, f, 1);
+}
+
 /* Full weighting: tensor product of the 1D weights (1/4, 1/2, 1/4) around
  * the coincident fine node; coarse boundary nodes are set to 0. */
 static void restrict3d(const orc_level* F, const double* rf, const orc_level* C, double* fc) {
@@ -329,6 +378,7 @@ typedef struct {
     double* u[ORC_MAX_LEVELS]; /* level 0's u is the caller's array */
     double* f[ORC_MAX_LEVELS];
     double* r[ORC_MAX_LEVELS];
+    int smoother; /* 0: red-black point Gauss-Seidel; 1: zebra z-line Gauss-Seidel (3D levels) */
 } orc_mg;
 
 static int coarsenable(int n) { return n >= 5 && ((n - 1) % 2) == 0; }
@@ -337,6 +387,7 @@ static void mg_build(orc_mg* mg, const orc_problem* p, int dim) {
     int nx = p->nx, ny = p->ny, nz = (dim == 3) ? p->nz : 1;
     mg->dim = dim;
     mg->nlev = 0;
+    mg->smoother = 0;
     for (;;) {
         orc_level* L = &mg->L[mg->nlev];
         if (dim == 3) level_init3d(L, p, nx, ny, nz); else level_init2d(L, p, nx, ny);
@@ -364,7 +415,11 @@ static void mg_residual(const orc_mg* mg, int l, const double* u, const double* 
 }
 
 static void mg_smooth(const orc_mg* mg, int l, double* u, const double* f) {
-    if (mg->dim == 3) rbgs3d(&mg->L[l], u, f); else rbgs2d(&mg->L[l], u, f);
+    if (mg->dim == 3) {
+        if (mg->smoother == 1) zline3d(&mg->L[l], u, f); else rbgs3d(&mg->L[l], u, f);
+    } else {
+        rbgs2d(&mg->L[l], u, f);
+    }
 }
 
 static double mg_norm(const orc_mg* mg, int l, const double* v) {
@@ -497,6 +552,22 @@ void orc_rbgs3d_colour(const orc_problem* p, int nx, int ny, int nz, double* u, 
     level_free(&L);
 }
 
+void orc_zline3d(const orc_problem* p, int nx, int ny, int nz, double* u, const double* f, int sweeps) {
+    orc_problem q = with_size(p, nx, ny, nz);
+    orc_level L;
+    level_init3d(&L, &q, nx, ny, nz);
+    for (int s = 0; s < sweeps; ++s) zline3d(&L, u, f);
+    level_free(&L);
+}
+
+void orc_zline3d_colour(const orc_problem* p, int nx, int ny, int nz, double* u, const double* f, int colour) {
+    orc_problem q = with_size(p, nx, ny, nz);
+    orc_level L;
+    level_init3d(&L, &q, nx, ny, nz);
+    zline3d_colour(&L, u, f, colour);
+    level_free(&L);
+}
+
 void orc_residual2d(const orc_problem* p, int nx, int ny, const double* u, const double* f, double* r) {
     orc_problem q = with_size(p, nx, ny, 1);
     orc_level L;
@@ -551,13 +622,19 @@ int orc_solve2d(const orc_problem* p, const double* bz, double* P0, double tol, 
  * boundary entries are the Dirichlet data (plane k = 0 from the lower
  * boundary solve, 0 elsewhere for the paper's problem); its interior is the
  * initial guess. */
-int orc_solve3d(const orc_problem* p, double* P, const double* f, double tol, int max_cycles, int nu1, int nu2,
-                double* rel_out, double* history, double* conv_out) {
+int orc_solve3d_s(const orc_problem* p, double* P, const double* f, double tol, int max_cycles, int nu1, int nu2,
+                  int smoother, double* rel_out, double* history, double* conv_out) {
     orc_mg mg;
     mg_build(&mg, p, 3);
+    mg.smoother = smoother;
     const int cyc = mg_solve(&mg, P, f, tol, max_cycles, nu1, nu2, rel_out, history, conv_out);
     mg_free(&mg);
     return cyc;
+}
+
+int orc_solve3d(const orc_problem* p, double* P, const double* f, double tol, int max_cycles, int nu1, int nu2,
+                double* rel_out, double* history, double* conv_out) {
+    return orc_solve3d_s(p, P, f, tol, max_cycles, nu1, nu2, 0, rel_out, history, conv_out);
 }
 
 int orc_num_levels(const orc_problem* p, int dim) {
@@ -572,19 +649,24 @@ int orc_num_levels(const orc_problem* p, int dim) {
  * on z = 0 for eq. (lower_bound); (3) multigrid in the interior for
  * eq. (scalar_pot) with the plane k = 0 from step 2 and P = 0 on the top and
  * sides.  P has nx*ny*nz entries. */
-int orc_solve(const orc_problem* p, const double* bz, double* P, double tol2d, double tol3d, int max_cycles,
-              int nu1, int nu2, orc_info* info) {
+int orc_solve_s(const orc_problem* p, const double* bz, double* P, double tol2d, double tol3d, int max_cycles,
+                int nu1, int nu2, int smoother, orc_info* info) {
     const size_t plane = (size_t)p->nx * p->ny;
     memset(P, 0, sizeof(double) * plane * p->nz);
     double rel2 = 0.0, rel3 = 0.0, conv = 0.0;
     const int c2 = orc_solve2d(p, bz, P, tol2d, max_cycles, nu1, nu2, &rel2, NULL);
-    const int c3 = orc_solve3d(p, P, NULL, tol3d, max_cycles, nu1, nu2, &rel3, NULL, &conv);
+    const int c3 = orc_solve3d_s(p, P, NULL, tol3d, max_cycles, nu1, nu2, smoother, &rel3, NULL, &conv);
     if (info) {
         info->cycles_2d = c2; info->cycles_3d = c3;
         info->rel_res_2d = rel2; info->rel_res_3d = rel3;
         info->conv_factor_3d = conv;
     }
     return (rel2 < tol2d && rel3 < tol3d) ? 0 : 1;
+}
+
+int orc_solve(const orc_problem* p, const double* bz, double* P, double tol2d, double tol3d, int max_cycles,
+              int nu1, int nu2, orc_info* info) {
+    return orc_solve_s(p, bz, P, tol2d, tol3d, max_cycles, nu1, nu2, 0, info);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -698,15 +780,21 @@ void orc_profiles(const orc_problem* p, double* xi, double* dxi, double* pb, dou
 /* One V(nu1,nu2)-cycle for A u = f on the grid of u (dim 3: nx*ny*nz,
  * dim 2: nx*ny), from that grid down to the coarsest level.  u is updated
  * in place; its boundary entries are the Dirichlet data. */
-void orc_vcycle(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
-                int nu2) {
+void orc_vcycle_s(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
+                  int nu2, int smoother) {
     orc_problem q = with_size(p, nx, ny, dim == 3 ? nz : 1);
     orc_mg mg;
     mg_build(&mg, &q, dim);
+    mg.smoother = smoother;
     const size_t n = level_size(&mg.L[0]);
     double* fz = NULL;
     if (!f) fz = (double*)calloc(n, sizeof(double));
     vcycle(&mg, 0, u, f ? f : fz, nu1, nu2);
     free(fz);
     mg_free(&mg);
+}
+
+void orc_vcycle(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
+                int nu2) {
+    orc_vcycle_s(p, dim, nx, ny, nz, u, f, nu1, nu2, 0);
 }

@@ -31,6 +31,11 @@ MUTANTS = {
     "pressure_xi_dropped": ("pr[c] = pb - xi * B2;", "pr[c] = pb - B2;"),
     "pb_transition_exponent": ("(1.0 - pow(p->T_cor, -(z - p->z1) / d))", "(1.0 - pow(p->T_cor, (z - p->z1) / d))"),
     "dxi_sign": ("case 1: return -p->xi_kappa * p->xi_a", "case 1: return p->xi_kappa * p->xi_a"),
+    "zline_top_dirichlet_dropped": ("if (k == nz - 2) b -= L->cz * u[c + plane];", "if (k == nz - 1) b -= L->cz * u[c + plane];"),
+    "zline_wrong_columns": ("if (((i + j) & 1) != colour) continue;\n                for (int t = 0; t < m; ++t) {",
+                            "if (((i + j + 1) & 1) != colour) continue;\n                for (int t = 0; t < m; ++t) {"),
+    "zline_back_substitution": ("u[c] = rhs[t] - (t < m - 1 ? sup[t] * u[c + plane] : 0.0);",
+                                "u[c] = rhs[t] + (t < m - 1 ? sup[t] * u[c + plane] : 0.0);"),
     "gs_divides_wrong_diag": ("u[c] = ((f ? f[c] : 0.0) - off) / L->diag[k];", "u[c] = ((f ? f[c] : 0.0) - off) / L->diag[0];"),
 }
 

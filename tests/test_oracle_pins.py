@@ -211,6 +211,83 @@ def test_gauss_seidel_converges_to_direct_solution():
     assert np.abs(u - exact.separable_solve3d(pr, P0)).max() < 1e-12
 
 
+def test_zline_sweep_solves_its_columns_exactly():
+    """Zebra z-line Gauss-Seidel: after the pass over the columns with i + j
+    even, the residual vanishes on every interior node of those columns (an
+    exact solve of their rows), the other columns are untouched; then the
+    same for the odd columns.  Since -A restricted to a column is
+    nonsingular, this property determines the pass uniquely."""
+    nx, ny, nz = 9, 11, 13
+    pr = S.problem(nx, ny, nz, Lx=1.0, Ly=1.3, Lz=0.9, alpha=0.6, **XI2)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx))
+    K, J, I = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    interior = (I > 0) & (I < nx - 1) & (J > 0) & (J < ny - 1) & (K > 0) & (K < nz - 1)
+    even = interior & ((I + J) % 2 == 0)
+    odd = interior & ((I + J) % 2 == 1)
+    scale = np.abs(f).max() * 400
+    u1 = oracle.zline3d_colour(pr, u, f, 0)
+    r1 = oracle.residual3d(pr, u1, f)
+    assert np.abs(r1[even]).max() < 1e-11 * scale
+    assert np.abs(r1[odd]).max() > 1e-3
+    assert np.array_equal(u1[~even], u[~even])
+    u2 = oracle.zline3d_colour(pr, u1, f, 1)
+    r2 = oracle.residual3d(pr, u2, f)
+    assert np.abs(r2[odd]).max() < 1e-11 * scale
+    assert np.array_equal(u2[~odd], u1[~odd])
+    assert np.array_equal(oracle.zline3d(pr, u, f, 1), u2)
+
+
+def test_zline_single_column_is_a_direct_solve():
+    """With one interior column (3 x 3 x nz nodes) a single zebra sweep solves
+    the whole system: the result equals a dense solve of the column's
+    tridiagonal equations written out from the stencil's coefficients."""
+    nz = 17
+    pr = S.problem(3, 3, nz, Lx=0.2, Ly=0.3, Lz=1.0, alpha=0.7, **XI1)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal((nz, 3, 3))
+    f = rng.standard_normal((nz, 3, 3))
+    got = oracle.zline3d(pr, u, f, 1)
+    # the column (1, 1): its four horizontal neighbours are boundary nodes
+    hx, hy, hz = 0.2 / 2, 0.3 / 2, 1.0 / (nz - 1)
+    z = np.arange(nz) * hz
+    xi = XI1["xi_a"] * np.exp(-XI1["xi_kappa"] * z)        # the xi_1 family, a exp(-kappa z)
+    m = nz - 2
+    A = np.zeros((m, m)); b = np.zeros(m)
+    for t in range(m):
+        k = t + 1
+        cx, cy, cz = (1 - xi[k]) / hx**2, (1 - xi[k]) / hy**2, 1 / hz**2
+        A[t, t] = -2 * (cx + cy + cz) + pr["alpha"] ** 2
+        if t > 0: A[t, t - 1] = cz
+        if t < m - 1: A[t, t + 1] = cz
+        b[t] = f[k, 1, 1] - cx * (u[k, 1, 0] + u[k, 1, 2]) - cy * (u[k, 0, 1] + u[k, 2, 1])
+    b[0] -= u[0, 1, 1] / hz**2
+    b[-1] -= u[-1, 1, 1] / hz**2
+    want = np.linalg.solve(A, b)
+    assert np.allclose(got[1:-1, 1, 1], want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+    assert np.array_equal(got[:, [0, 2], :], u[:, [0, 2], :])
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9, 0.999])
+def test_zline_multigrid_robust_to_strong_vertical_coupling(a):
+    """With xi(z) = a exp(-z/2) close to 1 the horizontal coupling nearly
+    vanishes; V(2,2) cycles with the zebra z-line smoother still reduce the
+    residual by more than 10x per cycle (point red-black Gauss-Seidel does
+    not: its factor grows past 0.3 at a = 0.999), and converge to the direct
+    solution."""
+    pr = S.problem(33, 33, 33, alpha=0.5, xi_kind=1, xi_a=a, xi_kappa=0.5)
+    bz = S.magnetogram_random(33, 33, seed=6)
+    P, info = oracle.solve(pr, bz, 1e-12, 1e-12, smoother="zline")
+    assert info["status"] == 0 and info["conv_factor_3d"] < 0.1, info
+    P0 = exact.separable_solve2d(pr, bz)
+    want = exact.separable_solve3d(pr, P0)
+    assert np.abs(P - want).max() < 1e-9 * np.abs(want).max()
+    if a > 0.99:
+        _, info_p = oracle.solve(pr, bz, 1e-12, 1e-12)
+        assert info_p["conv_factor_3d"] > 0.3
+
+
 @pytest.mark.parametrize("shape", [(9, 17, 9), (17, 9)])
 def test_restriction_is_scaled_adjoint_of_prolongation(shape):
     """Full weighting R and (bi/tri)linear interpolation I satisfy
