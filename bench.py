@@ -211,7 +211,8 @@ def run_gpu(args):
     xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
     h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
     M.mhs_set_stream(h, stream)
-    flags = (M.MHS_FLAG_NO_GRAPH if args.eager else 0) | (M.MHS_FLAG_NO_FMG if args.no_fmg else 0)
+    flags = (M.MHS_FLAG_NO_GRAPH if args.eager else 0) | (M.MHS_FLAG_NO_FMG if args.no_fmg else 0) | \
+        (M.MHS_FLAG_ZLINE if args.zline else 0)
     if flags:
         M.mhs_set_options(h, flags=flags)
     shape = (pr["nz"], pr["ny"], pr["nx"])
@@ -613,6 +614,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving leg")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven kernel-by-kernel solve instead of the captured graph (for launch lists)")
+    ap.add_argument("--zline", action="store_true",
+                    help="smooth the interior levels by zebra z-line Gauss-Seidel instead of red-black point sweeps")
     ap.add_argument("--no-fmg", action="store_true",
                     help="start each solve from zero with a plain V-cycle instead of a full-multigrid cycle")
     args = ap.parse_args()

@@ -92,7 +92,8 @@ typedef struct {
 
 typedef enum {
     MHS_FP64 = 0,        /* every multigrid operation in FP64 */
-    MHS_MIXED = 1        /* FP64 residual and update around FP32 V-cycles (defect correction) */
+    MHS_MIXED = 1        /* FP32 V-cycles inside a defect-correction loop whose iterate and residual are
+                            double-float (pairs of FP32 words, about 48 bits); P returned in FP64 */
 } mhs_precision;
 
 /* Solver options.  Zero-initialised fields take the defaults in brackets. */
@@ -107,16 +108,22 @@ typedef struct {
     int cut32;           /* same for FP32 levels [4000] */
     int fused_min;       /* FP32 3D levels with at least this many interior nodes use the fused, TMA-staged
                             red-black sweep (one pass per sweep, HBM-bound); smaller, cache-resident levels use the
-                            two colour passes, which have less latency [8000000] */
+                            two colour passes, which have less latency [32000000] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
 #define MHS_FLAG_BZ_MIMETIC 2   /* B_z = -(D_x D_x + D_y D_y) P with the first-difference operators,
                                    which makes the central-difference div B vanish to rounding */
 #define MHS_FLAG_FUSED_SWEEP64 8 /* FP64 3D levels also use the fused out-of-place red-black sweep (one pass per
-                                    sweep; FP32 levels always do); default: the two in-place colour passes, which
-                                    spend no FP64 work on redundant halo updates */
+                                    sweep; FP32 levels do from fused_min interior nodes up); default: the two
+                                    in-place colour passes, which spend no FP64 work on redundant halo updates */
 #define MHS_FLAG_NO_FMG 32      /* start from P = 0 with plain V-cycles instead of a full-multigrid first cycle */
+#define MHS_FLAG_ZLINE 64       /* smooth the interior levels by zebra z-line Gauss-Seidel (columns with i + j
+                                   even, then odd, each solved exactly along z) instead of red-black point
+                                   Gauss-Seidel: robust when 1 - xi(z) is small or h_z < h_x; same solution.
+                                   Without this flag or MHS_FLAG_POINT the smoother is chosen from the problem:
+                                   z-line when the anisotropy class (see mhs_autotune) is 5 or more */
+#define MHS_FLAG_POINT 128      /* always smooth by red-black point Gauss-Seidel */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
@@ -187,6 +194,41 @@ MHS_API mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info*
 MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solve_info* infos,
                                    mhs_status* statuses);
 
+/* ---- autotuner ----------------------------------------------------------
+ * mhs_autotune picks the solver options for h's problem by timing whole
+ * solves of its resident B_z to tol in the given mode (CUDA events, the
+ * captured-graph path).  Coordinate descent from h's current options over
+ * the smoother (red-black point or zebra z-line, MHS_FLAG_ZLINE), the sweep
+ * counts (nu1, nu2), the sub-cycle cut-off (cut64 in FP64 mode, cut32 in
+ * mixed mode; one candidate per level), the fused-sweep threshold of FP32
+ * levels (fused_min, mixed mode) and the full-multigrid first cycle
+ * (MHS_FLAG_NO_FMG); at most two rounds, a change kept when it saves at
+ * least 3 %.  Each candidate costs one untimed solve (graph capture) plus
+ * `repeats` timed solves (1..20), of which the fastest counts; candidates
+ * that do not converge are dropped.  The winner is applied to h (as by
+ * mhs_set_options) and stored in a process-wide table under the class
+ * (nx, ny, nz, mode, anisotropy class), where mhs_tune_lookup finds it for
+ * other handles of the class.  h's P afterwards is the solution of its last
+ * timed solve.  The anisotropy class is floor(log2(max_k max(h_x,h_y)^2 /
+ * ((1 - xi(z_k)) h_z^2))), at least 0: vertical over horizontal coupling.
+ * Errors: MHS_ERR_BAD_STATE (no B_z), MHS_ERR_INVALID_ARG (tol, mode,
+ * repeats), MHS_ERR_CUDA.  Thread-safe across handles. */
+typedef struct {
+    mhs_solver_opts opts;   /* chosen options (applied to the handle) */
+    double ms;              /* fastest timed solve with them */
+    double ms_start;        /* fastest timed solve with the options h had on entry */
+    int candidates;         /* option sets timed */
+    int aniso_class;        /* anisotropy class of the problem */
+} mhs_tune_result;
+
+MHS_API mhs_status mhs_autotune(mhs_handle h, double tol, int mode, int repeats, mhs_tune_result* out);
+/* Options stored by mhs_autotune for the class of h's current problem in
+ * `mode`: *found = 1 and *opts filled, or *found = 0 (opts untouched).
+ * Errors: MHS_ERR_INVALID_ARG. */
+MHS_API mhs_status mhs_tune_lookup(mhs_handle h, int mode, mhs_solver_opts* opts, int* found);
+/* Forget every stored option set. */
+MHS_API void mhs_tune_clear(void);
+
 /* ---- request server (continuous batching) ----------------------------
  * A server owns a worker thread and a pool of resident solver hierarchies
  * (one pool per grid shape).  Submitted requests are admitted in arrival
@@ -246,6 +288,43 @@ MHS_API mhs_status mhs_get_phi(mhs_handle h, double* phi);
  * differences on the first and last node of each axis.
  * Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_CUDA. */
 MHS_API mhs_status mhs_fields(mhs_handle h, double* Bx, double* By, double* Bz, double* p, double* rho);
+
+/* ---- post-processing: the quantities of the paper's figures (Sect. 3) ----
+ * mhs_current: the current density j = curl B / mu0 of the latest solve's B
+ * (recomputed as by mhs_fields), with the same difference operators
+ * (central inside, second-order one-sided on the first and last node of
+ * each axis), its magnitude |j| and |B|; each [nz][ny][nx], host or device,
+ * any may be NULL.  Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_current(mhs_handle h, double* jx, double* jy, double* jz, double* jmag, double* bmag);
+
+/* mhs_trace: magnetic field lines of the latest solve's B.  From each of the
+ * n seeds (x, y, z; node (i, j, k) sits at (i h_x, j h_y, k h_z)), classical
+ * fourth-order Runge-Kutta steps of arc length ds along dr/ds = direction *
+ * B/|B| (direction +1 or -1), B interpolated trilinearly in its cell (along
+ * x, then y, then z), at most max_steps steps.  A step is taken only when
+ * its four stage points and its end point lie in the closed box
+ * [0,Lx]x[0,Ly]x[0,Lz] and |B| does not vanish at the stage points;
+ * otherwise the line ends.  points: n x (max_steps + 1) x 3 doubles, the
+ * seed first (entries past a line's end are left as they were); lengths: n
+ * ints, the number of points of each line, 0 for a seed outside the box.
+ * seeds, points and lengths may be host or device memory; host buffers are
+ * staged through temporary device memory and the call then returns after
+ * the copies.  The arithmetic is IEEE FP64 with every operation rounded
+ * separately (no fused multiply-add), in a fixed order.
+ * Errors: MHS_ERR_BAD_STATE (no solve yet), MHS_ERR_INVALID_ARG (n < 0,
+ * max_steps < 0, ds <= 0, direction not +1/-1, NULL buffers, output over
+ * 64 GB), MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_trace(mhs_handle h, const double* seeds, int n, double ds, int max_steps, int direction,
+                             double* points, int* lengths);
+
+/* mhs_trace_field: the same tracer on caller-supplied device arrays Bx, By,
+ * Bz, dense [nz][ny][nx], on the box [0,Lx]x[0,Ly]x[0,Lz] (nx, ny, nz >= 2),
+ * enqueued on `stream` (a cudaStream_t, NULL for the default stream).
+ * Errors: MHS_ERR_INVALID_ARG (as mhs_trace, or B not in device memory),
+ * MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_trace_field(int nx, int ny, int nz, double Lx, double Ly, double Lz, const double* Bx,
+                                   const double* By, const double* Bz, const double* seeds, int n, double ds,
+                                   int max_steps, int direction, double* points, int* lengths, void* stream);
 
 /* Number of multigrid levels of the interior (dim = 3) or lower-boundary
  * (dim = 2) hierarchy, and the node counts of one level (level 0 finest). */

@@ -92,6 +92,9 @@ def _load():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_fields": (None, [_PP, _D, _D, _D, _D, _D, _D, ctypes.c_int]),
                 "orc_profiles": (None, [_PP, _D, _D, _D, _D, _D]),
+                "orc_current": (None, [_PP, _D, _D, _D, _D, _D, _D, _D, _D]),
+                "orc_trace": (None, [_PP, _D, _D, _D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, _D, ctypes.POINTER(ctypes.c_int)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -299,3 +302,26 @@ def fields(pr, P, bz_mode=0):
     out = [np.zeros_like(P) for _ in range(5)]
     _load().orc_fields(ctypes.byref(p), _ptr(P), *[_ptr(a) for a in out], int(bz_mode))
     return dict(zip(["Bx", "By", "Bz", "p", "rho"], out))
+
+
+def current(pr, Bx, By, Bz):
+    """j = curl B / mu0 (the field-recovery difference operators), |j| and |B|."""
+    p = _prob(pr)
+    Bx, By, Bz = _f64(Bx), _f64(By), _f64(Bz)
+    out = [np.zeros_like(Bx) for _ in range(5)]
+    _load().orc_current(ctypes.byref(p), _ptr(Bx), _ptr(By), _ptr(Bz), *[_ptr(a) for a in out])
+    return dict(zip(["jx", "jy", "jz", "jmag", "bmag"], out))
+
+
+def trace(pr, Bx, By, Bz, seeds, ds, max_steps, direction=1):
+    """RK4 field lines along direction * B/|B| from seeds [n][3] (x, y, z).
+    Returns (points [n][max_steps+1][3], lengths [n])."""
+    p = _prob(pr)
+    Bx, By, Bz = _f64(Bx), _f64(By), _f64(Bz)
+    seeds = np.ascontiguousarray(seeds, dtype=np.float64).reshape(-1, 3)
+    n = seeds.shape[0]
+    pts = np.zeros((n, max_steps + 1, 3))
+    lens = np.zeros(n, dtype=np.int32)
+    _load().orc_trace(ctypes.byref(p), _ptr(Bx), _ptr(By), _ptr(Bz), _ptr(seeds), n, float(ds), int(max_steps),
+                      float(direction), _ptr(pts), lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return pts, lens

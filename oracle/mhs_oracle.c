@@ -798,3 +798,115 @@ void orc_vcycle(const orc_problem* p, int dim, int nx, int ny, int nz, double* u
                 int nu2) {
     orc_vcycle_s(p, dim, nx, ny, nz, u, f, nu1, nu2, 0);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing for the paper's figure quantities (Sect. 3): current     */
+/* density and magnetic field lines.                                         */
+/* ------------------------------------------------------------------------ */
+
+/* j = curl B / mu0 with the difference operators of the field recovery
+ * (central inside, second-order one-sided at the first and last node of an
+ * axis), and the magnitudes |j|, |B|.  Any output may be NULL. */
+void orc_current(const orc_problem* p, const double* Bx, const double* By, const double* Bz, double* jx, double* jy,
+                 double* jz, double* jmag, double* bmag) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const double hx = p->Lx / (nx - 1), hy = p->Ly / (ny - 1), hz = p->Lz / (nz - 1);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t c = IDX(i, j, k, nx, ny);
+                const double cx = (d1(Bz, nx, ny, nz, i, j, k, 1, hy) - d1(By, nx, ny, nz, i, j, k, 2, hz)) / p->mu0;
+                const double cy = (d1(Bx, nx, ny, nz, i, j, k, 2, hz) - d1(Bz, nx, ny, nz, i, j, k, 0, hx)) / p->mu0;
+                const double cz = (d1(By, nx, ny, nz, i, j, k, 0, hx) - d1(Bx, nx, ny, nz, i, j, k, 1, hy)) / p->mu0;
+                if (jx) jx[c] = cx;
+                if (jy) jy[c] = cy;
+                if (jz) jz[c] = cz;
+                if (jmag) jmag[c] = sqrt(cx * cx + cy * cy + cz * cz);
+                if (bmag) bmag[c] = sqrt(Bx[c] * Bx[c] + By[c] * By[c] + Bz[c] * Bz[c]);
+            }
+}
+
+/* Unit field direction dir * B/|B| at the point r of the box [0,Lx]x[0,Ly]x[0,Lz]
+ * (node (i,j,k) at (i hx, j hy, k hz)), B interpolated trilinearly from the
+ * eight nodes of the cell holding r (the last cell for points on an upper
+ * face), first along x, then y, then z.  Returns 0 when r lies outside the
+ * closed box or |B| vanishes there. */
+static int trace_dir(const orc_problem* p, const double* B[3], double dir, const double r[3], double v[3]) {
+    const int n[3] = {p->nx, p->ny, p->nz};
+    const double L[3] = {p->Lx, p->Ly, p->Lz};
+    int c[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(r[a] >= 0.0 && r[a] <= L[a])) return 0;
+        const double h = L[a] / (n[a] - 1);
+        const double s = r[a] / h;
+        int i = (int)floor(s);
+        if (i > n[a] - 2) i = n[a] - 2;
+        if (i < 0) i = 0;
+        c[a] = i;
+        f[a] = s - i;
+    }
+    const int nx = p->nx, ny = p->ny;
+    double b[3];
+    for (int q = 0; q < 3; ++q) {
+        const double* F = B[q];
+        double e[2][2];
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy) {
+                const double f0 = F[IDX(c[0], c[1] + dy, c[2] + dz, nx, ny)];
+                const double f1 = F[IDX(c[0] + 1, c[1] + dy, c[2] + dz, nx, ny)];
+                e[dz][dy] = f0 * (1.0 - f[0]) + f1 * f[0];
+            }
+        const double e0 = e[0][0] * (1.0 - f[1]) + e[0][1] * f[1];
+        const double e1 = e[1][0] * (1.0 - f[1]) + e[1][1] * f[1];
+        b[q] = e0 * (1.0 - f[2]) + e1 * f[2];
+    }
+    const double m = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    if (!(m > 0.0)) return 0;
+    for (int q = 0; q < 3; ++q) v[q] = dir * b[q] / m;
+    return 1;
+}
+
+/* Field lines: for each of the n seeds (x, y, z), classical fourth-order
+ * Runge-Kutta steps of length ds along dr/ds = dir B/|B| (dir = +1 along B,
+ * -1 against it), at most max_steps of them.  A step is taken only when all
+ * four stage points and its end point lie in the closed box and |B| does not
+ * vanish at the stage points; otherwise the line ends.  points holds
+ * n x (max_steps + 1) x 3 coordinates, the seed first; lengths[q] is the
+ * number of points of line q (0 for a seed outside the box). */
+void orc_trace(const orc_problem* p, const double* Bx, const double* By, const double* Bz, const double* seeds, int n,
+               double ds, int max_steps, double dir, double* points, int* lengths) {
+    const double* B[3] = {Bx, By, Bz};
+    const double L[3] = {p->Lx, p->Ly, p->Lz};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int q = 0; q < n; ++q) {
+        double r[3] = {seeds[3 * q], seeds[3 * q + 1], seeds[3 * q + 2]};
+        double* out = points + (size_t)q * (max_steps + 1) * 3;
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) inside = inside && r[a] >= 0.0 && r[a] <= L[a];
+        if (!inside) { lengths[q] = 0; continue; }
+        out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
+        int len = 1;
+        const double hs = 0.5 * ds, s6 = ds / 6.0;
+        for (int step = 0; step < max_steps; ++step) {
+            double k1[3], k2[3], k3[3], k4[3], t[3], e[3];
+            if (!trace_dir(p, B, dir, r, k1)) break;
+            for (int a = 0; a < 3; ++a) t[a] = r[a] + hs * k1[a];
+            if (!trace_dir(p, B, dir, t, k2)) break;
+            for (int a = 0; a < 3; ++a) t[a] = r[a] + hs * k2[a];
+            if (!trace_dir(p, B, dir, t, k3)) break;
+            for (int a = 0; a < 3; ++a) t[a] = r[a] + ds * k3[a];
+            if (!trace_dir(p, B, dir, t, k4)) break;
+            int ok = 1;
+            for (int a = 0; a < 3; ++a) {
+                e[a] = r[a] + s6 * (((k1[a] + 2.0 * k2[a]) + 2.0 * k3[a]) + k4[a]);
+                ok = ok && e[a] >= 0.0 && e[a] <= L[a];
+            }
+            if (!ok) break;
+            for (int a = 0; a < 3; ++a) { r[a] = e[a]; out[3 * len + a] = e[a]; }
+            ++len;
+        }
+        lengths[q] = len;
+    }
+}

@@ -50,7 +50,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 8000000}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 32000000}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -63,14 +63,6 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->cut32 > 0) o->cut32 = in->cut32;
     if (in->fused_min > 0) o->fused_min = in->fused_min;
     o->flags = in->flags;
-}
-
-double xi_host(const mhs_xi_params& x, double z) {
-    switch (x.kind) {
-    case MHS_XI_EXP: return x.a * std::exp(-x.kappa * z);
-    case MHS_XI_EXP_SIN: return (x.a + x.b * std::sin(x.omega * z)) * std::exp(-x.kappa * z);
-    default: return 0.0;
-    }
 }
 
 // Argument checks shared by mhs_create and mhs_set_params.
@@ -86,7 +78,7 @@ mhs_status check_physics(int nx, int ny, int nz, double Lx, double Ly, double Lz
     const double hz = Lz / (nz - 1);
     double min_om = 1.0;
     for (int k = 1; k < nz - 1; ++k) {
-        const double om = 1.0 - xi_host(xi, k * hz);
+        const double om = 1.0 - mhs::xi_host(xi, k * hz);
         if (!(om > 0.0)) {
             char buf[160];
             std::snprintf(buf, sizeof buf, "xi(z) = %.6g >= 1 at z = %.6g: eq. (scalar_pot) is not elliptic",
@@ -275,6 +267,27 @@ mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solv
     return guarded([&] { return mhs::batch_solve(hs, n, tol, mode, infos, statuses); });
 }
 
+mhs_status mhs_autotune(mhs_handle h, double tol, int mode, int repeats, mhs_tune_result* out) {
+    if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(MHS_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
+    if (repeats < 1 || repeats > 20) return fail(MHS_ERR_INVALID_ARG, "repeats must be in [1, 20]");
+    if (!h->have_bz) return fail(MHS_ERR_BAD_STATE, "mhs_set_lower_bz must come before mhs_autotune");
+    return guarded([&] {
+        mhs::autotune(h, tol, mode, repeats, out);
+        return MHS_OK;
+    });
+}
+
+mhs_status mhs_tune_lookup(mhs_handle h, int mode, mhs_solver_opts* opts, int* found) {
+    if (!h || !opts || !found) return fail(MHS_ERR_INVALID_ARG, "NULL argument");
+    if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
+    *found = mhs::tune_lookup(h, mode, opts) ? 1 : 0;
+    return MHS_OK;
+}
+
+void mhs_tune_clear(void) { mhs::tune_clear(); }
+
 mhs_status mhs_get_phi(mhs_handle h, double* phi) {
     if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
     if (!phi) return fail(MHS_ERR_INVALID_ARG, "phi is NULL");
@@ -307,6 +320,112 @@ mhs_status mhs_fields(mhs_handle h, double* Bx, double* By, double* Bz, double* 
             host = host || !is_device_ptr(outs[q]);
         }
         if (host) MHS_CUDA(cudaStreamSynchronize(h->stream));
+        return MHS_OK;
+    });
+}
+
+// B of the latest solve into h->fld (the field recovery of mhs_fields)
+static void compute_fields(mhs_handle h) {
+    mhs::ensure_field_buffers(h);
+    const mhs::Geom& g = h->h3.g[0];
+    const double nodes = double(g.nx) * g.ny * g.nz;
+    mhs::TimedScope t(h->timer, MHS_KT_FIELDS, 48.0 * nodes, 60.0 * nodes, h->stream);
+    mhs::launch_fields(g, h->alpha, h->atm, h->prof, h->h3.d[0].u, h->fld[0], h->fld[1], h->fld[2], h->fld[3],
+                       h->fld[4], (h->opts.flags & MHS_FLAG_BZ_MIMETIC) ? 1 : 0, h->stream);
+}
+
+mhs_status mhs_current(mhs_handle h, double* jx, double* jy, double* jz, double* jmag, double* bmag) {
+    if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->have_solution) return fail(MHS_ERR_BAD_STATE, "no solution yet (call mhs_solve)");
+    return guarded([&] {
+        compute_fields(h);
+        mhs::ensure_post_buffers(h);
+        const mhs::Geom& g = h->h3.g[0];
+        mhs::launch_current(g, h->atm.mu0, h->fld[0], h->fld[1], h->fld[2], h->post[0], h->post[1], h->post[2],
+                            h->post[3], h->post[4], h->stream);
+        double* outs[5] = {jx, jy, jz, jmag, bmag};
+        bool host = false;
+        for (int q = 0; q < 5; ++q) {
+            if (!outs[q]) continue;
+            from_pitched(g, outs[q], h->post[q], size_t(g.ny) * g.nz, h->stream);
+            host = host || !is_device_ptr(outs[q]);
+        }
+        if (host) MHS_CUDA(cudaStreamSynchronize(h->stream));
+        return MHS_OK;
+    });
+}
+
+// Field lines on B arrays with strides (px, plane); seeds, points and lengths
+// may be host or device memory (host ones are staged through the device).
+static void trace_any(int nx, int ny, int nz, double Lx, double Ly, double Lz, size_t px, size_t plane,
+                      const double* Bx, const double* By, const double* Bz, const double* seeds, int n, double ds,
+                      int max_steps, int direction, double* points, int* lengths, cudaStream_t st) {
+    const size_t seed_bytes = size_t(n) * 3 * sizeof(double);
+    const size_t pts_bytes = size_t(n) * size_t(max_steps + 1) * 3 * sizeof(double);
+    const size_t len_bytes = size_t(n) * sizeof(int);
+    const bool ds_dev = is_device_ptr(seeds), dp_dev = is_device_ptr(points), dl_dev = is_device_ptr(lengths);
+    double* d_seeds = const_cast<double*>(seeds);
+    double* d_pts = points;
+    int* d_len = lengths;
+    if (!ds_dev) MHS_CUDA(cudaMalloc(&d_seeds, seed_bytes));
+    if (!dp_dev) MHS_CUDA(cudaMalloc(&d_pts, pts_bytes));
+    if (!dl_dev) MHS_CUDA(cudaMalloc(&d_len, len_bytes));
+    try {
+        if (!ds_dev) MHS_CUDA(cudaMemcpyAsync(d_seeds, seeds, seed_bytes, cudaMemcpyHostToDevice, st));
+        mhs::launch_trace(nx, ny, nz, Lx, Ly, Lz, px, plane, Bx, By, Bz, d_seeds, n, ds, max_steps,
+                          direction > 0 ? 1.0 : -1.0, d_pts, d_len, st);
+        if (!dp_dev) MHS_CUDA(cudaMemcpyAsync(points, d_pts, pts_bytes, cudaMemcpyDeviceToHost, st));
+        if (!dl_dev) MHS_CUDA(cudaMemcpyAsync(lengths, d_len, len_bytes, cudaMemcpyDeviceToHost, st));
+        if (!ds_dev || !dp_dev || !dl_dev) MHS_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        if (!ds_dev) cudaFree(d_seeds);
+        if (!dp_dev) cudaFree(d_pts);
+        if (!dl_dev) cudaFree(d_len);
+        throw;
+    }
+    if (!ds_dev) cudaFree(d_seeds);
+    if (!dp_dev) cudaFree(d_pts);
+    if (!dl_dev) cudaFree(d_len);
+}
+
+static mhs_status check_trace_args(const double* seeds, int n, double ds, int max_steps, int direction,
+                                   const double* points, const int* lengths) {
+    if (n < 0 || max_steps < 0 || !(ds > 0.0) || !std::isfinite(ds) || (direction != 1 && direction != -1))
+        return fail(MHS_ERR_INVALID_ARG, "trace: need n >= 0, max_steps >= 0, ds > 0, direction +1 or -1");
+    if (n > 0 && (!seeds || !points || !lengths)) return fail(MHS_ERR_INVALID_ARG, "trace: NULL buffer");
+    if (double(n) * double(max_steps + 1) * 24.0 > 64e9)
+        return fail(MHS_ERR_INVALID_ARG, "trace: output larger than 64 GB");
+    return MHS_OK;
+}
+
+mhs_status mhs_trace(mhs_handle h, const double* seeds, int n, double ds, int max_steps, int direction,
+                     double* points, int* lengths) {
+    if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->have_solution) return fail(MHS_ERR_BAD_STATE, "no solution yet (call mhs_solve)");
+    const mhs_status s = check_trace_args(seeds, n, ds, max_steps, direction, points, lengths);
+    if (s != MHS_OK) return s;
+    return guarded([&] {
+        compute_fields(h);
+        const mhs::Geom& g = h->h3.g[0];
+        trace_any(g.nx, g.ny, g.nz, h->Lx, h->Ly, h->Lz, size_t(g.px), g.plane, h->fld[0], h->fld[1], h->fld[2],
+                  seeds, n, ds, max_steps, direction, points, lengths, h->stream);
+        return MHS_OK;
+    });
+}
+
+mhs_status mhs_trace_field(int nx, int ny, int nz, double Lx, double Ly, double Lz, const double* Bx,
+                           const double* By, const double* Bz, const double* seeds, int n, double ds, int max_steps,
+                           int direction, double* points, int* lengths, void* stream) {
+    if (nx < 2 || ny < 2 || nz < 2 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0))
+        return fail(MHS_ERR_INVALID_ARG, "trace: need at least 2 nodes and a positive length per axis");
+    if (!Bx || !By || !Bz || !is_device_ptr(Bx) || !is_device_ptr(By) || !is_device_ptr(Bz))
+        return fail(MHS_ERR_INVALID_ARG, "trace: Bx, By, Bz must be device arrays");
+    const mhs_status s = check_trace_args(seeds, n, ds, max_steps, direction, points, lengths);
+    if (s != MHS_OK) return s;
+    return guarded([&] {
+        trace_any(nx, ny, nz, Lx, Ly, Lz, size_t(nx), size_t(nx) * ny, Bx, By, Bz, seeds, n, ds, max_steps,
+                  direction, points, lengths, static_cast<cudaStream_t>(stream));
         return MHS_OK;
     });
 }

@@ -125,6 +125,58 @@ __device__ void sub_smooth(const SubSmem<T, D3>& S, int l) {
     }
 }
 
+// one zebra z-line sweep (columns with i + j even first): each thread solves
+// the tridiagonal system of one column exactly (elimination factors lm, lsup
+// of the level's coefficient records), the eliminated right-hand side held
+// in the column's own entries of u until the back substitution
+template <typename T>
+__device__ void sub_zline(const SubSmem<T, true>& S, int l) {
+    const SubGeom g = S.g[l];
+    T* u = S.a + g.off_u;
+    const T* f = S.a + g.off_f;
+    const PlaneCoef<T>* cf = S.c + g.off_c;
+    const int ncol = g.hx * g.nyi, nzi = g.nz - 2;
+    const int tid = threadIdx.x + SX * threadIdx.y;
+    for (int colour = 0; colour < 2; ++colour) {
+        for (int q = tid; q < ncol; q += SX * SY) {
+            const int jj = fdiv(q, g.inv_hx);
+            const int t = q - jj * g.hx;
+            const int j = 1 + jj;
+            const int i = 1 + (((1 + j) & 1) != colour) + 2 * t;
+            if (i > g.nx - 2) continue;
+            int o = i + g.px * (j + g.ny);
+            T dprev = T(0);
+            for (int k = 1; k <= nzi; ++k, o += g.plane) {
+                const PlaneCoef<T> c = cf[k];
+                T v = f[o] - c.cx * (u[o + 1] + u[o - 1]) - c.cy * (u[o + g.px] + u[o - g.px]);
+                if (k == 1) v -= c.cz * u[o - g.plane];
+                if (k == nzi) v -= c.cz * u[o + g.plane];
+                dprev = (v - c.cz * dprev) * c.lm;
+                u[o] = dprev;
+            }
+            o -= g.plane;   // plane nzi: u = w there
+            T unext = u[o];
+            for (int k = nzi - 1; k >= 1; --k) {
+                o -= g.plane;
+                unext = u[o] - cf[k].lsup * unext;
+                u[o] = unext;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, bool D3>
+__device__ __forceinline__ void sub_relax(const SubSmem<T, D3>& S, int l, int line) {
+    if constexpr (D3) {
+        if (line) {
+            sub_zline<T>(S, l);
+            return;
+        }
+    }
+    sub_smooth<T, D3>(S, l);
+}
+
 // f[l+1] = full weighting of (f - A u) on level l; u[l+1] = 0 at interior nodes
 template <typename T, bool D3>
 __device__ void sub_restrict_residual(const SubSmem<T, D3>& S, int l) {
@@ -221,11 +273,11 @@ __device__ double sub_norm2(const SubSmem<T, D3>& S, int l, bool res) {
 // coarsest level: one exact update when it has a single unknown, else sweep
 // until ||f - A u|| <= tol ||f|| (checked every 4 sweeps, at most 2000)
 template <typename T, bool D3>
-__device__ void sub_coarsest(const SubSmem<T, D3>& S, int l) {
+__device__ void sub_coarsest(const SubSmem<T, D3>& S, int l, int line) {
     const SubGeom g = S.g[l];
     const int nint = (g.nx - 2) * (g.ny - 2) * (D3 ? g.nz - 2 : 1);
     if (nint == 1) {
-        sub_smooth<T, D3>(S, l);
+        sub_relax<T, D3>(S, l, line);
         return;
     }
     const double tol = sizeof(T) == 8 ? 1e-10 : 1e-5;
@@ -239,7 +291,7 @@ __device__ void sub_coarsest(const SubSmem<T, D3>& S, int l) {
     }
     __syncthreads();
     for (int sweep = 0; sweep < 2000 && !s_done; ++sweep) {
-        sub_smooth<T, D3>(S, l);
+        sub_relax<T, D3>(S, l, line);
         if ((sweep & 3) == 3) {
             const double rr = sub_norm2<T, D3>(S, l, true);
             if (tid == 0) s_done = rr <= tol * tol * s_fn;
@@ -288,13 +340,13 @@ __global__ void __launch_bounds__(SX * SY) subcycle_kernel(const SubParams<T> p)
     __syncthreads();
     const SubSmem<T, D3> S{sa, sc, sg};
     for (int l = 0; l < p.nlev - 1; ++l) {
-        for (int q = 0; q < p.nu1; ++q) sub_smooth<T, D3>(S, l);
+        for (int q = 0; q < p.nu1; ++q) sub_relax<T, D3>(S, l, p.line);
         sub_restrict_residual<T, D3>(S, l);
     }
-    sub_coarsest<T, D3>(S, p.nlev - 1);
+    sub_coarsest<T, D3>(S, p.nlev - 1, p.line);
     for (int l = p.nlev - 2; l >= 0; --l) {
         sub_prolong<T, D3>(S, l);
-        for (int q = 0; q < p.nu2; ++q) sub_smooth<T, D3>(S, l);
+        for (int q = 0; q < p.nu2; ++q) sub_relax<T, D3>(S, l, p.line);
     }
     const SubGeom g0 = sg[0];
     const T* u0 = sa + g0.off_u;

@@ -5,8 +5,8 @@
 // The paper parallelises every multigrid stage with one thread per node
 // (Sect. 4: relaxation, residual, restriction and prolongation).  These are
 // the plain per-node kernels of that design, adapted to red-black
-// Gauss-Seidel; the fused, shared-memory-staged fine-level kernels live in
-// kernels_fine.cu.
+// Gauss-Seidel; the fused sweeps live in kernels_sweep.cu and kernels_tma.cu,
+// the z-line smoother in kernels_line.cu.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -44,11 +44,8 @@ __device__ double dxi_of(const mhs_xi_params& x, double z) {
     }
 }
 
-template <typename T>
-__global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.nz) return;
-    double cx, cy, cz, d;
+__device__ void plane_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, int k, double& cx,
+                           double& cy, double& cz, double& d) {
     if (dim == 3) {
         const double om = 1.0 - xi_of(xi, k * g.hz);
         cx = om / (g.hx * g.hx);
@@ -61,7 +58,31 @@ __global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, Pla
         cz = 0.0;
         d = -2.0 * (cx + cy);
     }
-    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d), T(cx / d), T(cy / d), T(cz / d)};
+}
+
+template <typename T>
+__global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nz) return;
+    double cx, cy, cz, d;
+    plane_coef(g, dim, alpha, xi, k, cx, cy, cz, d);
+    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d), T(cx / d), T(cy / d), T(cz / d), T(0), T(0)};
+}
+
+// Elimination factors of the z-line smoother's column systems, a sequential
+// recursion over the interior planes (FP64, rounded to T at the end).
+template <typename T>
+__global__ void line_coef_kernel(Geom g, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sup = 0.0;
+    for (int k = 1; k <= g.nz - 2; ++k) {
+        double cx, cy, cz, d;
+        plane_coef(g, 3, alpha, xi, k, cx, cy, cz, d);
+        const double lm = 1.0 / (d - (k > 1 ? cz * sup : 0.0));
+        sup = cz * lm;
+        coef[k].lm = T(lm);
+        coef[k].lsup = T(sup);
+    }
 }
 
 // Background atmosphere: T_b piecewise (1, T_cor^((z-z1)/(z2-z1)), T_cor);
@@ -379,6 +400,10 @@ void launch_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, 
                  cudaStream_t st) {
     coef_kernel<T><<<(g.nz + 127) / 128, 128, 0, st>>>(g, dim, alpha, xi, coef);
     count_launches(1);
+    if (dim == 3 && g.nz > 2) {
+        line_coef_kernel<T><<<1, 32, 0, st>>>(g, alpha, xi, coef);
+        count_launches(1);
+    }
     MHS_CUDA(cudaGetLastError());
 }
 

@@ -40,6 +40,10 @@ __host__ __device__ inline size_t round_up(size_t a, size_t b) { return (a + b -
 template <typename T>
 struct PlaneCoef {
     T cx, cy, cz, d, inv_d, ax, ay, az;
+    // forward-elimination factors of the tridiagonal column systems solved by
+    // the z-line smoother (the same for every column of the level):
+    // lm = 1 / pivot_k, lsup = cz * lm, pivot_1 = d_1, pivot_k = d_k - cz lsup_{k-1}
+    T lm, lsup;
 };
 
 // Geometry of one level.  Device arrays are pitched: element (i,j,k) at
@@ -118,6 +122,7 @@ constexpr int MAX_SUB_LEVELS = 12;
 template <typename T>
 struct SubParams {
     int nlev, dim, nu1, nu2;
+    int line;            // 1: zebra z-line smoothing on 3D levels, 0: red-black point smoothing
     SubLevel<T> L[MAX_SUB_LEVELS];
     T* u_g;              // iterate of the top level in global memory (in/out)
     const T* f_g;        // right-hand side of the top level in global memory
@@ -177,6 +182,7 @@ struct mhs_ctx {
     mhs_xi_params xi;
     mhs_atmos_params atm;
     mhs_solver_opts opts;
+    int aniso = 0;                 // anisotropy class of the interior operator (set with the coefficients)
     cudaStream_t stream = nullptr;
     mhs::Hierarchy h3, h2;
     mhs::NormScratch ns;
@@ -186,6 +192,7 @@ struct mhs_ctx {
     int* flag_host = nullptr;      // pinned mirror
     double* staging = nullptr;     // FP64 staging buffer of the finest size (level hooks, lazily allocated)
     double* fld[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // pitched Bx, By, Bz, p, rho
+    double* post[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}; // pitched jx, jy, jz, |j|, |B| (on first use)
     bool have_bz = false, have_solution = false;
     bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
     std::vector<void*> allocations;
@@ -240,6 +247,17 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
 // ---- fused out-of-place red-black sweep (kernels_sweep.cu) ----
 template <typename T>
 void launch_sweep(const Geom& g, const PlaneCoef<T>* coef, const T* uin, const T* f, T* uout, cudaStream_t st);
+
+// ---- zebra z-line Gauss-Seidel sweep, both colours (kernels_line.cu); scratch holds g.n elements ----
+template <typename T>
+void launch_zline(const Geom& g, const PlaneCoef<T>* coef, T* u, const T* f, T* scratch, cudaStream_t st);
+
+// ---- post-processing (kernels_post.cu) ----
+void launch_current(const Geom& g, double mu0, const double* Bx, const double* By, const double* Bz, double* jx,
+                    double* jy, double* jz, double* jmag, double* bmag, cudaStream_t st);
+void launch_trace(int nx, int ny, int nz, double Lx, double Ly, double Lz, size_t px, size_t plane, const double* Bx,
+                  const double* By, const double* Bz, const double* seeds, int n, double ds, int max_steps,
+                  double dir, double* points, int* lengths, cudaStream_t st);
 
 // ---- TMA-staged fused sweep for FP32 levels (kernels_tma.cu) ----
 void make_plane_map(CUtensorMap* map, const Geom& g, const float* base);

@@ -158,6 +158,13 @@ void Server::start(const std::shared_ptr<Request>& q) {
     c->stream = c->bstream;
     mhs_status s = mhs_set_params(c, r.alpha, &r.xi, &r.atm);
     if (s != MHS_OK) throw Error(s, mhs_last_error());
+    // options stored by the autotuner for this problem class, if any
+    mhs_solver_opts tuned;
+    if (tune_lookup(c, r.mode, &tuned) && std::memcmp(&tuned, &c->opts, sizeof tuned) != 0) {
+        c->opts = tuned;
+        invalidate_graphs(c);
+        choose_cuts(c);
+    }
     const Geom& g2 = c->h2.g[0];
     MHS_CUDA(cudaMemcpy2DAsync(c->bz, g2.px * sizeof(double), q->bz.data(), g2.nx * sizeof(double),
                                g2.nx * sizeof(double), g2.ny, cudaMemcpyHostToDevice, c->stream));

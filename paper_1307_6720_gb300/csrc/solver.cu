@@ -60,7 +60,7 @@ static int choose_cut(const Hierarchy& H, size_t elem, size_t max_interior) {
     int cut = H.nlev() - 1;
     for (int l = H.nlev() - 1; l >= 0; --l) {
         size_t bytes = 0;
-        for (int m = l; m < H.nlev(); ++m) bytes += 2 * round_up(H.g[m].n, 4) * elem + H.g[m].nz * 8 * elem;
+        for (int m = l; m < H.nlev(); ++m) bytes += 2 * round_up(H.g[m].n, 4) * elem + H.g[m].nz * 10 * elem;
         // the sub-cycle decodes node indices with float reciprocals (exact for rows of <= 1024 nodes)
         if (bytes > subcycle_smem_limit() || H.g[l].interior() > max_interior || H.g[l].nx - 2 > 1024 ||
             H.g[l].ny - 2 > 1024)
@@ -136,6 +136,8 @@ void compute_coefficients(mhs_ctx* c) {
         launch_df_coef(H->g[0], H->d[0].coef, H->df.coef, c->stream);
     }
     launch_profiles(c->h3.g[0], c->xi, c->atm, c->prof, c->stream);
+    c->aniso = aniso_class(c);
+    invalidate_graphs(c);   // the smoother may follow the anisotropy class
 }
 
 void create(mhs_ctx* c) {
@@ -206,6 +208,7 @@ void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
     p.dim = H.dim;
     p.nu1 = c->opts.nu1;
     p.nu2 = c->opts.nu2;
+    p.line = H.dim == 3 && use_zline(c) ? 1 : 0;
     size_t off = 0;
     for (int m = 0; m < p.nlev; ++m) {
         const Geom& g = H.g[l + m];
@@ -227,14 +230,23 @@ void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
     launch_subcycle<T>(p, c->stream);
 }
 
-// n red-black sweeps on level l.  3D levels use the fused out-of-place sweep
-// (always for FP32, for FP64 with MHS_FLAG_FUSED_SWEEP64), alternating between
-// u and its twin t; otherwise the two colour passes run in place.
+// n smoothing sweeps on level l.  With z-line smoothing (use_zline), 3D
+// levels run zebra z-line sweeps (in place, the level's r as scratch).  Otherwise red-black
+// sweeps: 3D levels use the fused out-of-place sweep (FP32 levels of at least
+// fused_min interior nodes, FP64 with MHS_FLAG_FUSED_SWEEP64), alternating
+// between u and its twin t; the rest the two colour passes in place.
 template <typename T>
 static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fine, double bytes, double flops) {
     LevelArrays<T>& A = arrays<T>(H, l);
     const Geom& g = H.g[l];
     const bool dbl = sizeof(T) == 8;
+    if (H.dim == 3 && use_zline(c)) {
+        for (int q = 0; q < n; ++q) {
+            TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, bytes, flops, c->stream, fine);
+            launch_zline<T>(g, A.coef, A.u, f, A.r, c->stream);
+        }
+        return;
+    }
     const bool fused = H.dim == 3 && A.t &&
                        (dbl ? (c->opts.flags & MHS_FLAG_FUSED_SWEEP64) != 0
                             : g.interior() >= size_t(c->opts.fused_min));
@@ -501,7 +513,8 @@ static void add_while(mhs_ctx* c, cudaGraphConditionalHandle hnd, F&& fn) {
 
 static long long graph_key(mhs_ctx* c) {
     return (long long)c->opts.nu1 | (long long)c->opts.nu2 << 8 | (long long)c->opts.inner_cycles << 16 |
-           (long long)(c->opts.flags & MHS_FLAG_WARM) << 24 | (long long)c->f_zero_finest << 25;
+           (long long)(c->opts.flags & MHS_FLAG_WARM) << 24 | (long long)c->f_zero_finest << 25 |
+           (long long)use_zline(c) << 26;
 }
 
 static void build_graph(mhs_ctx* c, int mode) {
@@ -678,6 +691,11 @@ mhs_status batch_solve(mhs_ctx** hs, int n, double tol, int mode, mhs_solve_info
 void ensure_field_buffers(mhs_ctx* c) {
     if (c->fld[0]) return;
     for (int q = 0; q < 5; ++q) c->fld[q] = static_cast<double*>(dev_alloc(c, c->h3.g[0].n * sizeof(double)));
+}
+
+void ensure_post_buffers(mhs_ctx* c) {
+    if (c->post[0]) return;
+    for (int q = 0; q < 5; ++q) c->post[q] = static_cast<double*>(dev_alloc(c, c->h3.g[0].n * sizeof(double)));
 }
 
 void ensure_staging(mhs_ctx* c) {

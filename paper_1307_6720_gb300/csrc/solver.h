@@ -1,9 +1,34 @@
 // Driver entry points used by the C-ABI layer.
 #pragma once
 
+#include <cmath>
+
 #include "mhs_internal.h"
 
 namespace mhs {
+
+// xi(z) of Sect. 3.2 on the host (the device copy is xi_of in kernels_mg.cu)
+inline double xi_host(const mhs_xi_params& x, double z) {
+    switch (x.kind) {
+    case MHS_XI_EXP: return x.a * std::exp(-x.kappa * z);
+    case MHS_XI_EXP_SIN: return (x.a + x.b * std::sin(x.omega * z)) * std::exp(-x.kappa * z);
+    default: return 0.0;
+    }
+}
+
+// Autotuner (tune.cu): anisotropy class of a handle's interior operator,
+// floor(log2(max_k  weakest horizontal spacing^2 / ((1 - xi_k) h_z^2))), at least 0
+int aniso_class(const mhs_ctx* c);
+void autotune(mhs_ctx* c, double tol, int mode, int repeats, mhs_tune_result* out);
+// z-line smoothing on the interior levels: forced by MHS_FLAG_ZLINE, excluded by
+// MHS_FLAG_POINT, otherwise chosen when the anisotropy class is 5 or more
+inline bool use_zline(const mhs_ctx* c) {
+    if (c->opts.flags & MHS_FLAG_ZLINE) return true;
+    if (c->opts.flags & MHS_FLAG_POINT) return false;
+    return c->aniso >= 5;
+}
+bool tune_lookup(const mhs_ctx* c, int mode, mhs_solver_opts* o);
+void tune_clear();
 
 // slots of NormScratch::result
 constexpr int NORM_B_SLOT = 0;        // ||b||^2 of the current solve
@@ -26,6 +51,7 @@ template <typename T>
 void smooth_hook(mhs_ctx* c, Hierarchy& H, int l);   // one sweep as the V-cycle runs it
 double read_norm2(mhs_ctx* c, int slot);
 void ensure_field_buffers(mhs_ctx* c);
+void ensure_post_buffers(mhs_ctx* c);
 void ensure_staging(mhs_ctx* c);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)

@@ -24,6 +24,7 @@ MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
 MHS_FP64, MHS_MIXED = 0, 1
 MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, MHS_FLAG_NO_TMA, MHS_FLAG_NO_FMG = \
     1, 2, 4, 8, 16, 32
+MHS_FLAG_ZLINE, MHS_FLAG_POINT = 64, 128
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
 
@@ -50,6 +51,16 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("opts", SolverOpts), ("ms", ctypes.c_double), ("ms_start", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("aniso_class", ctypes.c_int)]
+
+    def as_dict(self):
+        o = self.opts
+        return {"opts": {k: getattr(o, k) for k, _ in SolverOpts._fields_}, "ms": self.ms,
+                "ms_start": self.ms_start, "candidates": self.candidates, "aniso_class": self.aniso_class}
 
 
 class Request(ctypes.Structure):
@@ -92,7 +103,13 @@ _SIGS = {
     "mhs_set_lower_bz": [_H, _P],
     "mhs_solve": [_H, _D, _I, ctypes.POINTER(SolveInfo)],
     "mhs_batch_solve": [ctypes.POINTER(_H), _I, _D, _I, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
+    "mhs_autotune": [_H, _D, _I, _I, ctypes.POINTER(TuneResult)],
+    "mhs_tune_lookup": [_H, _I, ctypes.POINTER(SolverOpts), ctypes.POINTER(_I)],
+    "mhs_tune_clear": [],
     "mhs_get_phi": [_H, _P],
+    "mhs_current": [_H, _P, _P, _P, _P, _P],
+    "mhs_trace": [_H, _P, _I, _D, _I, _I, _P, _P],
+    "mhs_trace_field": [_I, _I, _I, _D, _D, _D, _P, _P, _P, _P, _I, _D, _I, _I, _P, _P, _P],
     "mhs_fields": [_H, _P, _P, _P, _P, _P],
     "mhs_num_levels": [_H, _I, ctypes.POINTER(_I)],
     "mhs_level_shape": [_H, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -129,7 +146,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        if name in ("mhs_destroy", "mhs_server_destroy"):
+        if name in ("mhs_destroy", "mhs_server_destroy", "mhs_tune_clear"):
             fn.restype = None
         elif name in ("mhs_status_string", "mhs_last_error", "mhs_version", "mhs_kernel_kind_name"):
             fn.restype = ctypes.c_char_p
@@ -159,6 +176,25 @@ def ptr(a) -> int | None:
     import numpy as np
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "expected a contiguous float64 array"
     return a.ctypes.data
+
+
+def iptr(a) -> int | None:
+    """Data pointer of a contiguous int32 torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.int32 and a.is_contiguous(), "expected a contiguous int32 tensor"
+        return a.data_ptr()
+    import numpy as np
+    assert a.dtype == np.int32 and a.flags["C_CONTIGUOUS"], "expected a contiguous int32 array"
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return stream
 
 
 def xi_params(kind=MHS_XI_NONE, a=0.0, kappa=0.0, b=0.0, omega=0.0) -> XiParams:
@@ -225,12 +261,59 @@ def mhs_batch_solve(handles, tol, mode=MHS_FP64):
     return [i.as_dict() for i in infos], list(sts)
 
 
+def mhs_autotune(h, tol, mode=MHS_FP64, repeats=2) -> dict:
+    """Time candidate option sets on h's problem, apply and store the fastest."""
+    r = TuneResult()
+    _check(LIB.mhs_autotune(h, tol, mode, repeats, ctypes.byref(r)))
+    return r.as_dict()
+
+
+def mhs_tune_lookup(h, mode=MHS_FP64):
+    """Stored options (a dict of SolverOpts fields) for h's problem class, or None."""
+    o = SolverOpts()
+    found = _I()
+    _check(LIB.mhs_tune_lookup(h, mode, ctypes.byref(o), ctypes.byref(found)))
+    return {k: getattr(o, k) for k, _ in SolverOpts._fields_} if found.value else None
+
+
+def mhs_tune_clear() -> None:
+    LIB.mhs_tune_clear()
+
+
 def mhs_get_phi(h, phi) -> None:
     _check(LIB.mhs_get_phi(h, ptr(phi)))
 
 
 def mhs_fields(h, Bx=None, By=None, Bz=None, p=None, rho=None) -> None:
     _check(LIB.mhs_fields(h, ptr(Bx), ptr(By), ptr(Bz), ptr(p), ptr(rho)))
+
+
+def mhs_current(h, jx=None, jy=None, jz=None, jmag=None, bmag=None) -> None:
+    _check(LIB.mhs_current(h, ptr(jx), ptr(jy), ptr(jz), ptr(jmag), ptr(bmag)))
+
+
+def mhs_trace(h, seeds, ds, max_steps, direction=1, points=None, lengths=None):
+    """Field lines from seeds [n][3]; returns (points [n][max_steps+1][3], lengths [n]).
+    points/lengths may be given (host numpy or device torch buffers)."""
+    import numpy as np
+    n = int(seeds.shape[0])
+    if points is None:
+        points = np.zeros((n, max_steps + 1, 3))
+    if lengths is None:
+        lengths = np.zeros(n, dtype=np.int32)
+    _check(LIB.mhs_trace(h, ptr(seeds), n, float(ds), int(max_steps), int(direction), ptr(points), iptr(lengths)))
+    return points, lengths
+
+
+def mhs_trace_field(shape, box, Bx, By, Bz, seeds, ds, max_steps, direction=1, points=None, lengths=None,
+                    stream=None):
+    """The tracer on device arrays Bx, By, Bz [nz][ny][nx] of the box (Lx, Ly, Lz)."""
+    nz, ny, nx = shape
+    n = int(seeds.shape[0])
+    _check(LIB.mhs_trace_field(nx, ny, nz, box[0], box[1], box[2], ptr(Bx), ptr(By), ptr(Bz), ptr(seeds), n,
+                               float(ds), int(max_steps), int(direction), ptr(points), iptr(lengths),
+                               _stream_ptr(stream)))
+    return points, lengths
 
 
 def mhs_num_levels(h, dim=3) -> int:

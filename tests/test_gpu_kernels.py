@@ -254,3 +254,53 @@ def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
     assert np.array_equal(out[0], out[1])
     u32, f32 = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
     assert _rel(out[0], oracle.rbgs3d(pr, u32, f32, 5)) < 1e-4
+
+
+XI_STRONG = dict(xi_kind=1, xi_a=0.99, xi_kappa=0.5)   # 1 - xi(0) = 0.01: strong vertical coupling
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5), (129, 9, 65), (7, 67, 21)])
+def test_zline_sweep_parity(M, shape, prec):
+    """Zebra z-line sweeps (one thread per column, Thomas elimination with
+    precomputed pivots) against the oracle's line sweeps, three sweeps with
+    non-zero Dirichlet data on every face."""
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz, xi=XI_STRONG)
+    M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE)
+    rng = np.random.default_rng(5 * nx + ny + 3 * nz)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 30
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    for _ in range(3):
+        M.mhs_level_op(h, 3, 0, M.MHS_OP_SMOOTH, prec)
+    got = _read(M, h, 3, 0, M.MHS_FIELD_U, prec)
+    want = oracle.zline3d(pr, u, f, 3)
+    assert _rel(got, want) < (1e-12 if prec == 0 else 2e-5)
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("cut", [0, 40])
+def test_zline_vcycle_parity(M, prec, cut):
+    """One V(2,2)-cycle with z-line smoothing on every 3D level against the
+    oracle's: with the default sub-cycle cut-off, and with a cut-off of 40
+    nodes so that the global-memory line kernel runs on four levels."""
+    nx, ny, nz = 65, 33, 33
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=0.5, Lz=0.5, xi=XI_STRONG)
+    M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE, cut64=cut, cut32=cut)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 100
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    M.mhs_level_op(h, 3, 0, M.MHS_OP_VCYCLE, prec)
+    got = _read(M, h, 3, 0, M.MHS_FIELD_U, prec)
+    want = oracle.vcycle(pr, u, f, smoother="zline")
+    assert _rel(got, want) < (1e-11 if prec == 0 else 1e-5)
+    M.mhs_destroy(h)

@@ -36,6 +36,12 @@ MUTANTS = {
                             "if (((i + j + 1) & 1) != colour) continue;\n                for (int t = 0; t < m; ++t) {"),
     "zline_back_substitution": ("u[c] = rhs[t] - (t < m - 1 ? sup[t] * u[c + plane] : 0.0);",
                                 "u[c] = rhs[t] + (t < m - 1 ? sup[t] * u[c + plane] : 0.0);"),
+    "curl_y_sign": ("const double cy = (d1(Bx, nx, ny, nz, i, j, k, 2, hz) - d1(Bz, nx, ny, nz, i, j, k, 0, hx)) / p->mu0;",
+                    "const double cy = (d1(Bx, nx, ny, nz, i, j, k, 2, hz) + d1(Bz, nx, ny, nz, i, j, k, 0, hx)) / p->mu0;"),
+    "curl_mu0": ("const double cz = (d1(By, nx, ny, nz, i, j, k, 0, hx) - d1(Bx, nx, ny, nz, i, j, k, 1, hy)) / p->mu0;",
+                 "const double cz = (d1(By, nx, ny, nz, i, j, k, 0, hx) - d1(Bx, nx, ny, nz, i, j, k, 1, hy));"),
+    "trace_interp_weight": ("e[dz][dy] = f0 * (1.0 - f[0]) + f1 * f[0];", "e[dz][dy] = f0 * f[0] + f1 * (1.0 - f[0]);"),
+    "rk4_stage_weight": ("(((k1[a] + 2.0 * k2[a]) + 2.0 * k3[a]) + k4[a])", "(((k1[a] + 2.0 * k2[a]) + k3[a]) + 2.0 * k4[a])"),
     "gs_divides_wrong_diag": ("u[c] = ((f ? f[c] : 0.0) - off) / L->diag[k];", "u[c] = ((f ? f[c] : 0.0) - off) / L->diag[0];"),
 }
 
@@ -52,6 +58,7 @@ def test_pins_catch_mutant(name, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib), str(csrc), "-lm"])
     env = dict(os.environ, MHS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_paper_examples.py"],
+                        "tests/test_oracle_pins.py", "tests/test_oracle_paper_examples.py",
+                        "tests/test_oracle_postproc.py"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived every pin:\n{r.stdout[-2000:]}"
