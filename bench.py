@@ -453,9 +453,12 @@ def batched_instances(count=256):
     return inst
 
 
-def batched_leg(M, reps=3, count=256):
-    """All instances in one mhs_batch_solve (mixed, graphs) against solving them one after another in
-    FP64 and in mixed mode."""
+def batched_leg(M, reps=3, count=256, tune=True):
+    """The 256 uneven instances solved together in mixed precision: as one grouped solve (one launch per
+    multigrid operation and level for all instances, one CUDA graph) and as mhs_batch_solve (every
+    instance's own graph on its own stream), against solving them one after another in FP64 and in mixed
+    mode.  Then the autotuner picks options per problem class (untimed set-up) and the grouped solve is
+    timed again with them."""
     import torch
     inst = batched_instances(count)
     hs = []
@@ -475,9 +478,16 @@ def batched_leg(M, reps=3, count=256):
         assert all(s == 0 for s in sts), sts
         return infos
 
+    groups = {}
+
+    def grp(key):
+        infos, sts = M.mhs_group_solve(groups[key], count, TOL)
+        assert all(s == 0 for s in sts), sts
+        return infos
+
     res = {}
-    for name, fn in (("batched_mixed", bat), ("sequential_fp64", lambda: seq(M.MHS_FP64)),
-                     ("sequential_mixed", lambda: seq(M.MHS_MIXED))):
+
+    def run(name, fn):
         fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -486,11 +496,31 @@ def batched_leg(M, reps=3, count=256):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         res[name] = {"solves_per_s": count / dt, "unknowns_per_s": unknowns / dt, "s_per_batch": dt}
-        if name == "batched_mixed":
+        if out is not None:
             res[name]["max_cycles_3d"] = max(i["cycles_3d"] for i in out)
             res[name]["max_rel_res_3d"] = max(i["rel_res_3d"] for i in out)
+
+    groups["default"] = M.mhs_group_create(hs, M.MHS_MIXED)
+    run("grouped_mixed", lambda: grp("default"))
+    run("batched_mixed", bat)
+    run("sequential_fp64", lambda: seq(M.MHS_FP64))
+    run("sequential_mixed", lambda: seq(M.MHS_MIXED))
+    if tune:
+        t0 = time.perf_counter()
+        tuned_classes = 0
+        for h in hs:
+            if M.mhs_tune_lookup(h, M.MHS_MIXED) is None:
+                M.mhs_autotune(h, TOL, M.MHS_MIXED, repeats=1)
+                tuned_classes += 1
+            M.mhs_set_options(h, **M.mhs_tune_lookup(h, M.MHS_MIXED))
+        res["autotune"] = {"classes": tuned_classes, "seconds": time.perf_counter() - t0}
+        groups["tuned"] = M.mhs_group_create(hs, M.MHS_MIXED)
+        run("grouped_mixed_tuned", lambda: grp("tuned"))
     res["instances"] = count
-    res["speedup_vs_sequential_fp64"] = res["batched_mixed"]["solves_per_s"] / res["sequential_fp64"]["solves_per_s"]
+    best = max(v["solves_per_s"] for k, v in res.items() if k.startswith("grouped") or k == "batched_mixed")
+    res["speedup_vs_sequential_fp64"] = best / res["sequential_fp64"]["solves_per_s"]
+    for g in groups.values():
+        M.mhs_group_destroy(g)
     for h in hs:
         M.mhs_destroy(h)
     torch.cuda.empty_cache()

@@ -194,6 +194,41 @@ MHS_API mhs_status mhs_solve(mhs_handle h, double tol, int mode, mhs_solve_info*
 MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solve_info* infos,
                                    mhs_status* statuses);
 
+/* ---- grouped solves ------------------------------------------------------
+ * A group solves n independent instances (handles with any grids,
+ * parameters and options) together: every multigrid operation on one
+ * level is a single kernel launch for all instances that have that level,
+ * and the whole solve (lower-boundary and interior problems, both with the
+ * full-multigrid first cycle and V-cycles until each instance reaches the
+ * tolerance) is one captured CUDA graph whose loops run while any instance
+ * still iterates; converged instances drop out of the launches.  Each
+ * instance runs the operations of its solo mhs_solve with the same block
+ * decomposition, so its P is bitwise identical to solving it alone.
+ *
+ * mhs_group_create snapshots the handles' options, cut-offs and smoother
+ * choice (recreate the group after changing a member's options, or its
+ * parameters when that moves it to another anisotropy class) and captures
+ * the graph.  The handles must outlive the group and must not be used for
+ * other work while a group solve runs.  Not supported: MHS_FLAG_WARM,
+ * inner_cycles other than 1 (MHS_ERR_INVALID_ARG).
+ * Errors: MHS_ERR_INVALID_ARG (n < 1, NULL or repeated handle, bad mode),
+ * MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA. */
+typedef struct mhs_group* mhs_group_t;
+MHS_API mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out);
+/* Solve every instance of the group to tol with its current B_z (set by
+ * mhs_set_lower_bz, which must have returned for every member).  infos and
+ * statuses (n entries each) may be NULL; infos[q].ms is the group's device
+ * time.  Returns MHS_OK or the first failing instance's status
+ * (MHS_ERR_NO_CONVERGENCE, MHS_ERR_NONFINITE); MHS_ERR_BAD_STATE when a
+ * member has no B_z; MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_group_solve(mhs_group_t g, double tol, mhs_solve_info* infos, mhs_status* statuses);
+MHS_API void mhs_group_destroy(mhs_group_t g);
+/* eager != 0: later group solves launch the same kernels from the host, the
+ * loops reading the continuation flags back after each cycle, instead of
+ * the captured graph (same results; for profilers that cannot see kernels
+ * inside conditional graph nodes).  Errors: MHS_ERR_INVALID_ARG. */
+MHS_API mhs_status mhs_group_set_eager(mhs_group_t g, int eager);
+
 /* ---- autotuner ----------------------------------------------------------
  * mhs_autotune picks the solver options for h's problem by timing whole
  * solves of its resident B_z to tol in the given mode (CUDA events, the

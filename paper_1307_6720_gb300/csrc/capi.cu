@@ -7,6 +7,7 @@
 #include <new>
 #include <string>
 
+#include "group.h"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -265,6 +266,43 @@ mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solv
             if (hs[r] == hs[q]) return fail(MHS_ERR_INVALID_ARG, "a handle appears twice in the batch");
     }
     return guarded([&] { return mhs::batch_solve(hs, n, tol, mode, infos, statuses); });
+}
+
+mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out) {
+    if (!out) return fail(MHS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!hs || n < 1) return fail(MHS_ERR_INVALID_ARG, "group: need at least one handle");
+    if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
+    for (int q = 0; q < n; ++q) {
+        if (!hs[q]) return fail(MHS_ERR_INVALID_ARG, "NULL handle in group");
+        for (int r = 0; r < q; ++r)
+            if (hs[r] == hs[q]) return fail(MHS_ERR_INVALID_ARG, "a handle appears twice in the group");
+    }
+    return guarded([&] {
+        *out = mhs::group_create(hs, n, mode);
+        return MHS_OK;
+    });
+}
+
+mhs_status mhs_group_solve(mhs_group_t g, double tol, mhs_solve_info* infos, mhs_status* statuses) {
+    if (!g) return fail(MHS_ERR_INVALID_ARG, "group is NULL");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(MHS_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    for (mhs_ctx* c : g->hs)
+        if (!c->have_bz) return fail(MHS_ERR_BAD_STATE, "every group member needs mhs_set_lower_bz before a solve");
+    return guarded([&] {
+        const mhs_status s = mhs::group_solve(g, tol, infos, statuses, nullptr);
+        if (s != MHS_OK) return fail(s, s == MHS_ERR_NO_CONVERGENCE ? "an instance did not converge"
+                                                                    : "an instance has a non-finite residual");
+        return MHS_OK;
+    });
+}
+
+void mhs_group_destroy(mhs_group_t g) { mhs::group_destroy(g); }
+
+mhs_status mhs_group_set_eager(mhs_group_t g, int eager) {
+    if (!g) return fail(MHS_ERR_INVALID_ARG, "group is NULL");
+    g->eager = eager != 0;
+    return MHS_OK;
 }
 
 mhs_status mhs_autotune(mhs_handle h, double tol, int mode, int repeats, mhs_tune_result* out) {

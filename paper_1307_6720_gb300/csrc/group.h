@@ -1,0 +1,110 @@
+// Grouped launches: one kernel launch performs one multigrid operation for
+// many independent instances (uneven grids), each instance with the block
+// decomposition of its own solo launch, so that a grouped solve is bitwise
+// identical to solving every instance alone.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "mhs_internal.h"
+
+namespace mhs {
+
+// One (instance, level) of a grouped launch.  Pointers and integers are
+// interpreted by the operation (see the launchers in kernels_group.cu).
+struct GItem {
+    int q;                 // instance index within the group
+    int first;             // first block of the item in the grouped grid
+    int gx, gy, gz;        // the item's own grid (the solo launch's)
+    Geom g, g2;            // level, and its partner (coarse or fine level, or the 3D level of a plane copy)
+    const void* coef;      // PlaneCoef<T> / PlaneCoefDF of the level
+    void* p[6];            // arrays
+    int ia[4];             // integers: sweep count, FMG top level, partial count, ...
+    SolveCtl* ctl;         // the instance's control block of the current problem
+};
+
+// gate of a grouped launch: run every item, or only items whose instance still iterates
+enum GGate { G_ALL = 0, G_ACTIVE = 1 };
+
+// Device table of items with its total block count.
+struct GTable {
+    GItem* items = nullptr;   // device
+    int n = 0;                // items
+    int blocks = 0;           // sum of the items' grid sizes
+};
+
+// launchers (kernels_group.cu); `sweep` gates smoothing items by ia[0] > sweep,
+// `fmg_step` (>= 0) gates items by ia[1] >= fmg_step (the instance's FMG top level)
+template <typename T>
+void glaunch_colour(const GTable& t, int d3, int colour, int sweep, int fmg_step, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_zline(const GTable& t, int colour, int sweep, int fmg_step, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_residual(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_residual_norm(const GTable& t, int d3, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_prolong(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
+template <typename T>
+void glaunch_subcycle(const GTable& t, const SubParams<T>* params, int d3, int start, int fmg_step, int gate,
+                      size_t smem, cudaStream_t st);
+void glaunch_zero(const GTable& t, int gate, cudaStream_t st);
+void glaunch_lower_rhs(const GTable& t, cudaStream_t st);
+void glaunch_copy_plane(const GTable& t, cudaStream_t st);
+void glaunch_lift_norm(const GTable& t, cudaStream_t st);
+void glaunch_df_split(const GTable& t, int d3, cudaStream_t st);
+void glaunch_df_copy_plane(const GTable& t, cudaStream_t st);
+void glaunch_df_residual(const GTable& t, int d3, int gate, cudaStream_t st);
+void glaunch_df_correct(const GTable& t, int d3, int gate, cudaStream_t st);
+void glaunch_df_to_double(const GTable& t, cudaStream_t st);
+void glaunch_bnorm(const GTable& t, cudaStream_t st);
+void glaunch_check(const GTable& t, int first, int gate, cudaStream_t st);
+void glaunch_any(SolveCtl* const* ctls, int n, cudaGraphConditionalHandle handle, int use_handle, int* any_out,
+                 cudaStream_t st);
+void glaunch_gather_ctl(SolveCtl* const* ctls, int n, SolveCtl* out, cudaStream_t st);
+void gsubcycle_prepare();
+
+// tables of one problem (lower boundary or interior) of a group
+struct GDim {
+    int dim = 3;
+    int L = 0;                                   // most levels of any instance
+    int max_nu1 = 0, max_nu2 = 0, max_top = -1;  // largest sweep counts and FMG top level
+    // per level l (items of the instances for which l is a global level)
+    std::vector<GTable> pre_pt, post_pt, pre_ln, post_ln, res, restr, prol;
+    // full multigrid: restriction of the residual and prolongation of the
+    // coarse solution, per level, for the instances using it
+    std::vector<GTable> fmg_restr, fmg_prol;
+    GTable sub;                                  // sub-cycle: one item per instance
+    void* params = nullptr;                      // SubParams<T>[], device
+    size_t sub_smem = 0;
+    // once per solve
+    GTable zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1;
+    // cycle end (every instance), and after the full-multigrid cycle (instances using it)
+    GTable res_norm, check, fmg_res_norm, fmg_check;
+    // mixed mode
+    GTable zero_e, correct, fmg_zero_e, fmg_correct, to_double;
+};
+
+}  // namespace mhs
+
+struct mhs_group {
+    std::vector<mhs_ctx*> hs;
+    int mode = MHS_MIXED;
+    cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void*> allocs;
+    mhs::GDim d2, d3;
+    mhs::SolveCtl** ctls = nullptr;     // device: [2n] = n lower-boundary then n interior control blocks
+    mhs::SolveCtl* gathered = nullptr;  // device copy of the 2n control blocks after a solve
+    mhs::SolveCtl* gathered_host = nullptr;   // pinned
+    cudaGraphExec_t exec = nullptr;
+    long long n_fixed = 0, n_cycle2 = 0, n_cycle3 = 0;   // kernel launches of the graph's sections
+    bool eager = false;                 // host-driven launches instead of the graph
+    int* any_dev = nullptr;             // OR of the continuation flags (eager loop)
+    int* any_host = nullptr;            // pinned
+};
+

@@ -1,151 +1,40 @@
-// Double-float outer loop of mixed-precision defect correction.
+// Double-float outer loop of mixed-precision defect correction: the kernels
+// over the bodies of df_bodies.cuh, and their launchers.
 //
-// The iterate of the finest level is carried as an unevaluated sum of two
-// FP32 words, P = hi + lo (|lo| <= ulp(hi)/2, about 48 significant bits), and
-// the outer residual r = f - A P is evaluated with error-free
-// transformations instead of FP64 instructions:
-//   - TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e = a + b exactly;
-//   - Fast2Sum (Dekker 1971): the same when |a| >= |b|;
-//   - TwoProd with a fused multiply-add: p + e = a * b exactly.
 // On GB300 the FP64 pipe runs at about 1/70 of the FP32 rate, so the ~70 FP32
-// instructions per node here cost far less than the ~10 FP64 ones they
-// replace.  The residual is exact up to about 1e-14 of |A||P|, far below
-// what the 1e-10 stopping test needs; it is then rounded to FP32, the
-// right-hand side of the FP32 V-cycles.  Intrinsics with explicit rounding
-// (__fadd_rn, ...) keep the compiler from contracting or reassociating the
-// transformations.
+// instructions per node of the double-float residual cost far less than the
+// ~10 FP64 ones they replace.  The residual is exact up to about 1e-14 of
+// |A||P|, far below what the 1e-10 stopping test needs; it is then rounded
+// to FP32, the right-hand side of the FP32 V-cycles.
 #include "device_util.cuh"
+#include "df_bodies.cuh"
 #include "mhs_internal.h"
 
 namespace mhs {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-
-// r = f - A (hi + lo) for one interior node o of plane k.
-template <bool D3>
-__device__ __forceinline__ float df_node_residual(const Geom& g, const PlaneCoefDF& c, const float* __restrict__ hi,
-                                                  const float* __restrict__ lo, float fh, float fl, size_t o) {
-    const ptrdiff_t sy = g.px, sz = (ptrdiff_t)g.plane;
-    // neighbour pair sums of the high words, exactly as (sum, error)
-    float s1, e1, s2, e2, s3 = 0.f, e3 = 0.f;
-    two_sum(hi[o + 1], hi[o - 1], s1, e1);
-    two_sum(hi[o + sy], hi[o - sy], s2, e2);
-    if (D3) two_sum(hi[o + sz], hi[o - sz], s3, e3);
-    const float ch = hi[o];
-    // leading products, exactly as (product, error)
-    float px, qx, py, qy, pz = 0.f, qz = 0.f, pd, qd;
-    two_prod(c.cxh, s1, px, qx);
-    two_prod(c.cyh, s2, py, qy);
-    if (D3) two_prod(c.czh, s3, pz, qz);
-    two_prod(c.dh, ch, pd, qd);
-    // second-order terms (each ~2^-24 of its leading product): plain FP32
-    float t = qx + qy + qd;
-    t = __fmaf_rn(c.cxh, e1, t);
-    t = __fmaf_rn(c.cxl, s1, t);
-    t = __fmaf_rn(c.cyh, e2, t);
-    t = __fmaf_rn(c.cyl, s2, t);
-    t = __fmaf_rn(c.dl, ch, t);
-    if (D3) {
-        t += qz;
-        t = __fmaf_rn(c.czh, e3, t);
-        t = __fmaf_rn(c.czl, s3, t);
-    }
-    // A applied to the low words (about 2^-24 of the total): plain FP32
-    float al = c.cxh * (lo[o + 1] + lo[o - 1]) + c.cyh * (lo[o + sy] + lo[o - sy]) + c.dh * lo[o];
-    if (D3) al += c.czh * (lo[o + sz] + lo[o - sz]);
-    t += al;
-    // exact sum of the leading products, which cancel down to the residual
-    float s, e, err;
-    two_sum(px, py, s, err);
-    if (D3) {
-        two_sum(s, pz, s, e);
-        err += e;
-    }
-    two_sum(s, pd, s, e);
-    err += e;
-    // r = (fh - s) + (fl - err - t)
-    float a, b;
-    two_sum(fh, -s, a, b);
-    return a + (b + (fl - (err + t)));
-}
-
 template <bool D3>
 __global__ void df_residual_kernel(Geom g, const PlaneCoefDF* __restrict__ cdf, const float* __restrict__ hi,
                                    const float* __restrict__ lo, const float* __restrict__ fh,
                                    const float* __restrict__ fl, float* __restrict__ r32,
                                    double* __restrict__ partial) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    float acc = 0.f;
-    if (i <= g.nx - 2 && j <= g.ny - 2) {
-        for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
-            const size_t o = at(g, i, j, k);
-            const float r = df_node_residual<D3>(g, cdf[k], hi, lo, fh ? fh[o] : 0.f, fl ? fl[o] : 0.f, o);
-            r32[o] = r;
-            acc = __fmaf_rn(r, r, acc);
-        }
-    }
-    const double s = block_sum(double(acc));
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    df_residual_body<D3>(g, cdf, hi, lo, fh, fl, r32, partial, blockIdx, gridDim);
 }
 
-// (hi, lo) += e: TwoSum of the high word and e, the low word folded into the
-// error, then renormalised with Fast2Sum.
 __global__ void df_correct_kernel(Geom g, int d3, const float* __restrict__ e, float* __restrict__ hi,
                                   float* __restrict__ lo) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    for (int k = d3 ? 1 + blockIdx.z : 0; k <= (d3 ? g.nz - 2 : 0); k += gridDim.z) {
-        const size_t o = at(g, i, j, k);
-        float s, t;
-        two_sum(hi[o], e[o], s, t);
-        t = __fadd_rn(t, lo[o]);
-        float h, l;
-        fast_two_sum(s, t, h, l);
-        hi[o] = h;
-        lo[o] = l;
-    }
+    df_correct_body(g, d3, e, hi, lo, blockIdx, gridDim);
 }
 
-// split a double into hi = fl32(x), lo = fl32(x - hi) at interior nodes (zero when f is absent)
 __global__ void df_split_kernel(Geom g, int d3, const double* __restrict__ f, float* __restrict__ hi,
                                 float* __restrict__ lo) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    for (int k = d3 ? 1 + blockIdx.z : 0; k <= (d3 ? g.nz - 2 : 0); k += gridDim.z) {
-        const size_t o = at(g, i, j, k);
-        const double x = f ? f[o] : 0.0;
-        const float h = float(x);
-        hi[o] = h;
-        lo[o] = float(x - double(h));
-    }
+    df_split_body(g, d3, f, hi, lo, blockIdx, gridDim);
 }
 
 __global__ void df_to_double_kernel(size_t n, const float* __restrict__ hi, const float* __restrict__ lo,
                                     double* __restrict__ P) {
-    for (size_t o = blockIdx.x * size_t(blockDim.x) + threadIdx.x; o < n; o += size_t(gridDim.x) * blockDim.x)
-        P[o] = double(hi[o]) + double(lo[o]);
+    df_to_double_body(n, hi, lo, P, blockIdx, gridDim);
 }
 
 __global__ void df_coef_kernel(int nz, const PlaneCoef<double>* __restrict__ c, PlaneCoefDF* __restrict__ out) {
@@ -165,23 +54,7 @@ __global__ void df_coef_kernel(int nz, const PlaneCoef<double>* __restrict__ c, 
 
 __global__ void df_copy_plane_kernel(Geom g2, const float* __restrict__ hi2, const float* __restrict__ lo2, Geom g3,
                                      float* __restrict__ hi3, float* __restrict__ lo3) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g2.nx || j >= g2.ny) return;
-    hi3[at(g3, i, j, 0)] = hi2[at(g2, i, j, 0)];
-    lo3[at(g3, i, j, 0)] = lo2[at(g2, i, j, 0)];
-}
-
-dim3 df_grid(const Geom& g, int d3, int max_blocks) {
-    const int gx = (g.nx - 2 + BX - 1) / BX;
-    const int gy = (g.ny - 2 + BY - 1) / BY;
-    int gz = d3 ? g.nz - 2 : 1;
-    if (d3 && max_blocks > 0) {
-        const int cap = max_blocks / (gx * gy);
-        gz = gz > cap ? (cap > 0 ? cap : 1) : gz;
-    }
-    if (gz > 65535) gz = 65535;
-    return dim3(gx, gy, gz);
+    df_copy_plane_body(g2, hi2, lo2, g3, hi3, lo3, blockIdx);
 }
 
 }  // namespace
@@ -194,7 +67,7 @@ void launch_df_coef(const Geom& g, const PlaneCoef<double>* coef, PlaneCoefDF* c
 
 void launch_df_split(const Geom& g, int dim, const double* f, float* hi, float* lo, cudaStream_t st) {
     const int d3 = dim == 3;
-    df_split_kernel<<<df_grid(g, d3, 0), dim3(BX, BY), 0, st>>>(g, d3, f, hi, lo);
+    df_split_kernel<<<df_grid(g, d3, 0), dim3(DF_BX, DF_BY), 0, st>>>(g, d3, f, hi, lo);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
@@ -202,9 +75,9 @@ void launch_df_split(const Geom& g, int dim, const double* f, float* hi, float* 
 int launch_df_residual(const Geom& g, int dim, const PlaneCoefDF* cdf, const float* hi, const float* lo,
                        const float* fh, const float* fl, float* r32, double* partial, int max_blocks, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = df_grid(g, d3, max_blocks < 152 * 8 ? max_blocks : 152 * 8);
-    if (d3) df_residual_kernel<true><<<grid, dim3(BX, BY), 0, st>>>(g, cdf, hi, lo, fh, fl, r32, partial);
-    else df_residual_kernel<false><<<grid, dim3(BX, BY), 0, st>>>(g, cdf, hi, lo, fh, fl, r32, partial);
+    const dim3 grid = df_residual_grid(g, d3, max_blocks);
+    if (d3) df_residual_kernel<true><<<grid, dim3(DF_BX, DF_BY), 0, st>>>(g, cdf, hi, lo, fh, fl, r32, partial);
+    else df_residual_kernel<false><<<grid, dim3(DF_BX, DF_BY), 0, st>>>(g, cdf, hi, lo, fh, fl, r32, partial);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     return int(grid.x * grid.y * grid.z);
@@ -212,21 +85,21 @@ int launch_df_residual(const Geom& g, int dim, const PlaneCoefDF* cdf, const flo
 
 void launch_df_correct(const Geom& g, int dim, const float* e, float* hi, float* lo, cudaStream_t st) {
     const int d3 = dim == 3;
-    df_correct_kernel<<<df_grid(g, d3, 0), dim3(BX, BY), 0, st>>>(g, d3, e, hi, lo);
+    df_correct_kernel<<<df_grid(g, d3, 0), dim3(DF_BX, DF_BY), 0, st>>>(g, d3, e, hi, lo);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
 void launch_df_to_double(const Geom& g, const float* hi, const float* lo, double* P, cudaStream_t st) {
-    df_to_double_kernel<<<152 * 8, 256, 0, st>>>(g.n, hi, lo, P);
+    df_to_double_kernel<<<DF_TO_DOUBLE_BLOCKS, DF_TO_DOUBLE_THREADS, 0, st>>>(g.n, hi, lo, P);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
 
 void launch_df_copy_plane(const Geom& g2, const float* hi2, const float* lo2, const Geom& g3, float* hi3, float* lo3,
                           cudaStream_t st) {
-    const dim3 grid((g2.nx + BX - 1) / BX, (g2.ny + BY - 1) / BY);
-    df_copy_plane_kernel<<<grid, dim3(BX, BY), 0, st>>>(g2, hi2, lo2, g3, hi3, lo3);
+    const dim3 grid = df_plane_grid(g2);
+    df_copy_plane_kernel<<<grid, dim3(DF_BX, DF_BY), 0, st>>>(g2, hi2, lo2, g3, hi3, lo3);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "device_util.cuh"
+#include "mg_bodies.cuh"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -20,7 +21,7 @@ namespace mhs {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;
+constexpr int BX = MG_BX, BY = MG_BY;
 
 // -------------------------------------------------------------------------
 // a1: per-plane coefficients and height profiles (Sect. 2.1, eq. scalar_pot;
@@ -131,56 +132,16 @@ __global__ void fill_kernel(T* a, size_t n, T v) {
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) a[i] = v;
 }
 
-// -------------------------------------------------------------------------
-// Red-black Gauss-Seidel colour pass (in place).  Colour c updates the
-// interior nodes with (i + j + k) % 2 == c by solving their own row of
-// A u = f for u_ijk with the current neighbour values.  A thread per node
-// of the colour: thread t of row (j,k) takes i = i0 + 2t.
-// -------------------------------------------------------------------------
-
 template <typename T, bool D3>
 __global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* __restrict__ u,
                               const T* __restrict__ f, int colour) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (j > g.ny - 2) return;
-    for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
-        const int i = 1 + (((1 + j + k) & 1) != colour) + 2 * t;
-        if (i > g.nx - 2) continue;
-        const PlaneCoef<T> c = coef[k];
-        const size_t o = at(g, i, j, k);
-        // u = f/d - ax (E + W) - ay (N + S) - az (U + D); f == nullptr means f = 0
-        T v = f ? f[o] * c.inv_d : T(0);
-        if (D3) v = fma(-c.az, u[o + g.plane] + u[o - g.plane], v);
-        v = fma(-c.ay, u[o + g.px] + u[o - g.px], v);
-        u[o] = fma(-c.ax, u[o + 1] + u[o - 1], v);
-    }
+    colour_body<T, D3>(g, coef, u, f, colour, blockIdx, gridDim);
 }
 
-// r = f - A u at interior nodes; with partial != nullptr also per-block
-// partial sums of r^2 (in double), finished in fixed order by
-// norm_finish_kernel / check_kernel.
 template <typename T, bool D3, bool NORM>
 __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
                                 const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    double acc = 0.0;
-    if (i <= g.nx - 2 && j <= g.ny - 2) {
-        for (int k = D3 ? 1 + blockIdx.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gridDim.z) {
-            const PlaneCoef<T> c = coef[k];
-            const size_t o = at(g, i, j, k);
-            T au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
-            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
-            const T rv = (f ? f[o] : T(0)) - au;
-            r[o] = rv;
-            if (NORM) acc += double(rv) * double(rv);
-        }
-    }
-    if (!NORM) return;
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    residual_body<T, D3, NORM>(g, coef, u, f, r, partial, blockIdx, gridDim);
 }
 
 __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
@@ -191,69 +152,14 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, do
     if (threadIdx.x == 0) *out = s;
 }
 
-// Full weighting: tensor product of (1/4, 1/2, 1/4) around the fine node
-// (2I, 2J, 2K) coincident with coarse interior node (I, J, K).
-// With uc != nullptr the coarse iterate is zeroed at the same nodes (the
-// initial guess of the coarse-grid correction).
 template <typename T, bool D3>
 __global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc, T* __restrict__ uc) {
-    const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (I > gc.nx - 2 || J > gc.ny - 2) return;
-    for (int K = D3 ? 1 + blockIdx.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gridDim.z) {
-        const size_t o = at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
-        T acc = T(0);
-#pragma unroll
-        for (int c = (D3 ? -1 : 0); c <= (D3 ? 1 : 0); ++c) {
-            const T wc = D3 ? (c == 0 ? T(0.5) : T(0.25)) : T(1);
-            const size_t oc = o + (ptrdiff_t)c * (ptrdiff_t)gf.plane;
-            T s = T(0);
-#pragma unroll
-            for (int b = -1; b <= 1; ++b) {
-                const T wb = (b == 0) ? T(0.5) : T(0.25);
-                const size_t ob = oc + (ptrdiff_t)b * gf.px;
-                s += wb * (T(0.25) * rf[ob - 1] + T(0.5) * rf[ob] + T(0.25) * rf[ob + 1]);
-            }
-            acc += wc * s;
-        }
-        fc[at(gc, I, J, K)] = acc;
-        if (uc) uc[at(gc, I, J, K)] = T(0);
-    }
+    restrict_body<T, D3>(gf, gc, rf, fc, uc, blockIdx, gridDim);
 }
 
-// u_f += I u_c at fine interior nodes: along each axis an even fine index
-// takes coarse node i/2, an odd one the mean of (i-1)/2 and (i+1)/2.  One
-// thread per coarse cell (I..I+1, J..J+1, K..K+1) produces its 8 (2D: 4)
-// fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, sharing the partial sums
-// of the corner values; an even fine index is interior only when its coarse
-// index is >= 1.
 template <typename T, bool D3>
 __global__ void prolong_kernel(Geom gc, Geom gf, const T* __restrict__ uc, T* __restrict__ uf) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I > gc.nx - 2 || J > gc.ny - 2) return;
-    const ptrdiff_t cx = 1, cy = gc.px, cz = (ptrdiff_t)gc.plane;
-    const ptrdiff_t fx = 1, fy = gf.px, fz = (ptrdiff_t)gf.plane;
-    const bool ex = I >= 1, ey = J >= 1;
-    for (int K = D3 ? blockIdx.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gridDim.z) {
-        const T* c = uc + at(gc, I, J, K);
-        T* f = uf + at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
-        const T c000 = c[0], c100 = c[cx], c010 = c[cy], c110 = c[cx + cy];
-        const T e100 = c000 + c100, e010 = c000 + c010, e110 = e100 + (c010 + c110);
-        const bool ez = !D3 || K >= 1;
-        if (ex && ey && ez) f[0] += c000;
-        if (ey && ez) f[fx] = fma(T(0.5), e100, f[fx]);
-        if (ex && ez) f[fy] = fma(T(0.5), e010, f[fy]);
-        if (ez) f[fx + fy] = fma(T(0.25), e110, f[fx + fy]);
-        if (D3) {
-            const T c001 = c[cz], c101 = c[cx + cz], c011 = c[cy + cz], c111 = c[cx + cy + cz];
-            const T s01 = c001 + c101, s02 = c001 + c011;
-            if (ex && ey) f[fz] = fma(T(0.5), c000 + c001, f[fz]);
-            if (ey) f[fx + fz] = fma(T(0.25), e100 + s01, f[fx + fz]);
-            if (ex) f[fy + fz] = fma(T(0.25), e010 + s02, f[fy + fz]);
-            f[fx + fy + fz] = fma(T(0.125), e110 + (s01 + (c011 + c111)), f[fx + fy + fz]);
-        }
-    }
+    prolong_body<T, D3>(gc, gf, uc, uf, blockIdx, gridDim);
 }
 
 // Coarsest level: one CTA sweeps red-black Gauss-Seidel in shared memory
@@ -333,11 +239,7 @@ __global__ void coarse_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* 
 }
 
 __global__ void lower_rhs_kernel(Geom g, const double* __restrict__ bz, double* __restrict__ f) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    const size_t o = at(g, i, j, 0);
-    f[o] = -bz[o];
+    lower_rhs_body(g, bz, f, blockIdx);
 }
 
 template <typename T>
@@ -349,10 +251,7 @@ __global__ void zero_interior_kernel(Geom g, int d3, T* __restrict__ u) {
 }
 
 __global__ void copy_plane_kernel(Geom g2, const double* __restrict__ src, Geom g3, double* __restrict__ dst) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g2.nx || j >= g2.ny) return;
-    dst[at(g3, i, j, 0)] = src[at(g2, i, j, 0)];
+    copy_plane_body(g2, src, g3, dst, blockIdx);
 }
 
 __global__ void nonfinite_kernel(Geom g, const double* __restrict__ bz, int* flag) {
@@ -362,33 +261,12 @@ __global__ void nonfinite_kernel(Geom g, const double* __restrict__ bz, int* fla
     if (!isfinite(bz[at(g, i, j, 0)])) atomicExch(flag, 1);
 }
 
-// ||b||^2 of the lifted interior right-hand side: the Dirichlet data on
-// k = 0 enters row (i,j,1) as cz * P(i,j,0).
 __global__ void lift_norm_kernel(Geom g, const PlaneCoef<double>* __restrict__ coef, const double* __restrict__ u,
                                  double* __restrict__ partial) {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    double acc = 0.0;
-    if (i <= g.nx - 2 && j <= g.ny - 2) {
-        const double v = coef[1].cz * u[at(g, i, j, 0)];
-        acc = v * v;
-    }
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x + gridDim.x * blockIdx.y] = s;
+    lift_norm_body(g, coef, u, partial, blockIdx, gridDim);
 }
 
-dim3 grid_for(const Geom& g, int d3, int xcount, int max_blocks) {
-    const int gx = (xcount + BX - 1) / BX;
-    const int gy = (g.ny - 2 + BY - 1) / BY;
-    int gz = 1;
-    if (d3) {
-        gz = g.nz - 2;
-        const int cap = max_blocks > 0 ? max_blocks / (gx * gy) : 65535;
-        if (gz > cap) gz = cap > 0 ? cap : 1;
-        if (gz > 65535) gz = 65535;
-    }
-    return dim3(gx, gy, gz);
-}
+dim3 grid_for(const Geom& g, int d3, int xcount, int max_blocks) { return mg_grid(g, d3, xcount, max_blocks); }
 
 
 }  // namespace
@@ -427,8 +305,7 @@ void launch_fill(T* a, size_t n, T v, cudaStream_t st) {
 template <typename T>
 void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st) {
     const int d3 = dim == 3;
-    const int halfx = (g.nx - 2 + 1) / 2;
-    const dim3 grid = grid_for(g, d3, halfx, 0);
+    const dim3 grid = smooth_grid(g, d3);
     for (int colour = 0; colour < 2; ++colour) {
         if (d3) colour_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
         else colour_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
@@ -443,7 +320,7 @@ int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u
     const int d3 = dim == 3;
     // with norm partials, few enough blocks (a multiple of the SM count) that
     // the fixed-order finish stays short; every thread then covers several planes
-    const dim3 grid = grid_for(g, d3, g.nx - 2, partial ? std::min(max_blocks, 152 * 8) : 0);
+    const dim3 grid = residual_grid(g, d3, partial != nullptr, max_blocks);
     if (partial) {
         if (d3) residual_kernel<T, true, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
         else residual_kernel<T, false, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
@@ -465,7 +342,7 @@ void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t 
 template <typename T>
 void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st) {
     const int d3 = dim == 3;
-    const dim3 grid = grid_for(gc, d3, gc.nx - 2, 0);
+    const dim3 grid = restrict_grid(gc, d3);
     if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
     else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
     count_launches(1);
@@ -475,11 +352,7 @@ void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc
 template <typename T>
 void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st) {
     const int d3 = dim == 3;
-    // one thread per coarse cell: (nc - 1) cells per axis
-    Geom cells = gc;
-    cells.ny = gc.ny + 1;   // grid_for covers ny - 2 rows; cells need ny - 1
-    cells.nz = gc.nz + 1;
-    const dim3 grid = grid_for(cells, d3, gc.nx - 1, 0);
+    const dim3 grid = prolong_grid(gc, d3);   // one thread per coarse cell
     if (d3) prolong_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
     else prolong_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gc, gf, uc, uf);
     count_launches(1);
@@ -520,7 +393,7 @@ void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st) {
 }
 
 void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st) {
-    const dim3 grid((g2.nx + BX - 1) / BX, (g2.ny + BY - 1) / BY);
+    const dim3 grid = plane_grid(g2);
     copy_plane_kernel<<<grid, dim3(BX, BY), 0, st>>>(g2, src2d, g3, dst3d);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
@@ -535,7 +408,7 @@ void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStre
 
 int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double* u, double* partial,
                      cudaStream_t st) {
-    const dim3 grid((g3.nx - 2 + BX - 1) / BX, (g3.ny - 2 + BY - 1) / BY);
+    const dim3 grid = lift_grid(g3);
     lift_norm_kernel<<<grid, dim3(BX, BY), 0, st>>>(g3, coef, u, partial);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());

@@ -1,0 +1,205 @@
+// Per-block bodies of the multigrid building blocks (kernels_mg.cu) for the
+// lower-boundary problem (eq. lower_bound, 5-point stencil) and the interior
+// problem (eq. scalar_pot, 7-point stencil with per-plane coefficients).
+//
+// Each body takes the block's index b and the grid's dimensions gd
+// explicitly, so that the same code runs as a kernel of its own
+// (b = blockIdx, gd = gridDim) and inside a grouped launch that covers many
+// instances, where every instance keeps its own block decomposition: a
+// grouped solve is then bitwise identical to solving each instance alone.
+// Blocks are BX x BY threads.
+#pragma once
+
+#include "device_util.cuh"
+#include "mhs_internal.h"
+
+namespace mhs {
+
+constexpr int MG_BX = 32, MG_BY = 8;
+
+// Red-black Gauss-Seidel colour pass (in place): colour c updates the
+// interior nodes with (i + j + k) % 2 == c by solving their own row of
+// A u = f for u_ijk with the current neighbour values; thread t of row
+// (j, k) takes i = i0 + 2t.  f == nullptr means f = 0.
+template <typename T, bool D3>
+__device__ __forceinline__ void colour_body(const Geom& g, const PlaneCoef<T>* __restrict__ coef,
+                                            T* __restrict__ u, const T* __restrict__ f, int colour, dim3 b,
+                                            dim3 gd) {
+    const int t = b.x * blockDim.x + threadIdx.x;
+    const int j = 1 + b.y * blockDim.y + threadIdx.y;
+    if (j > g.ny - 2) return;
+    for (int k = D3 ? 1 + b.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gd.z) {
+        const int i = 1 + (((1 + j + k) & 1) != colour) + 2 * t;
+        if (i > g.nx - 2) continue;
+        const PlaneCoef<T> c = coef[k];
+        const size_t o = at(g, i, j, k);
+        // u = f/d - ax (E + W) - ay (N + S) - az (U + D)
+        T v = f ? f[o] * c.inv_d : T(0);
+        if (D3) v = fma(-c.az, u[o + g.plane] + u[o - g.plane], v);
+        v = fma(-c.ay, u[o + g.px] + u[o - g.px], v);
+        u[o] = fma(-c.ax, u[o + 1] + u[o - 1], v);
+    }
+}
+
+// r = f - A u at interior nodes; with NORM also this block's sum of r^2 (in
+// double), stored at partial[b.x + gd.x (b.y + gd.y b.z)] and finished in a
+// fixed order by the norm / check kernels.  Every thread of the block must
+// call it.
+template <typename T, bool D3, bool NORM>
+__device__ __forceinline__ void residual_body(const Geom& g, const PlaneCoef<T>* __restrict__ coef,
+                                              const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ r,
+                                              double* __restrict__ partial, dim3 b, dim3 gd) {
+    const int i = 1 + b.x * blockDim.x + threadIdx.x;
+    const int j = 1 + b.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= g.nx - 2 && j <= g.ny - 2) {
+        for (int k = D3 ? 1 + b.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gd.z) {
+            const PlaneCoef<T> c = coef[k];
+            const size_t o = at(g, i, j, k);
+            T au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
+            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
+            const T rv = (f ? f[o] : T(0)) - au;
+            r[o] = rv;
+            if (NORM) acc += double(rv) * double(rv);
+        }
+    }
+    if (!NORM) return;
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[b.x + gd.x * (b.y + gd.y * b.z)] = s;
+}
+
+// Full weighting: tensor product of (1/4, 1/2, 1/4) around the fine node
+// (2I, 2J, 2K) coincident with coarse interior node (I, J, K).  With
+// uc != nullptr the coarse iterate is zeroed at the same nodes (the initial
+// guess of the coarse-grid correction).
+template <typename T, bool D3>
+__device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, const T* __restrict__ rf,
+                                              T* __restrict__ fc, T* __restrict__ uc, dim3 b, dim3 gd) {
+    const int I = 1 + b.x * blockDim.x + threadIdx.x;
+    const int J = 1 + b.y * blockDim.y + threadIdx.y;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    for (int K = D3 ? 1 + b.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gd.z) {
+        const size_t o = at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
+        T acc = T(0);
+#pragma unroll
+        for (int c = (D3 ? -1 : 0); c <= (D3 ? 1 : 0); ++c) {
+            const T wc = D3 ? (c == 0 ? T(0.5) : T(0.25)) : T(1);
+            const size_t oc = o + (ptrdiff_t)c * (ptrdiff_t)gf.plane;
+            T s = T(0);
+#pragma unroll
+            for (int bb = -1; bb <= 1; ++bb) {
+                const T wb = (bb == 0) ? T(0.5) : T(0.25);
+                const size_t ob = oc + (ptrdiff_t)bb * gf.px;
+                s += wb * (T(0.25) * rf[ob - 1] + T(0.5) * rf[ob] + T(0.25) * rf[ob + 1]);
+            }
+            acc += wc * s;
+        }
+        fc[at(gc, I, J, K)] = acc;
+        if (uc) uc[at(gc, I, J, K)] = T(0);
+    }
+}
+
+// u_f += I u_c at fine interior nodes: along each axis an even fine index
+// takes coarse node i/2, an odd one the mean of (i-1)/2 and (i+1)/2.  One
+// thread per coarse cell (I..I+1, J..J+1, K..K+1) produces its 8 (2D: 4)
+// fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, sharing the partial sums
+// of the corner values; an even fine index is interior only when its coarse
+// index is >= 1.
+template <typename T, bool D3>
+__device__ __forceinline__ void prolong_body(const Geom& gc, const Geom& gf, const T* __restrict__ uc,
+                                             T* __restrict__ uf, dim3 b, dim3 gd) {
+    const int I = b.x * blockDim.x + threadIdx.x;
+    const int J = b.y * blockDim.y + threadIdx.y;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    const ptrdiff_t cx = 1, cy = gc.px, cz = (ptrdiff_t)gc.plane;
+    const ptrdiff_t fx = 1, fy = gf.px, fz = (ptrdiff_t)gf.plane;
+    const bool ex = I >= 1, ey = J >= 1;
+    for (int K = D3 ? b.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gd.z) {
+        const T* c = uc + at(gc, I, J, K);
+        T* f = uf + at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
+        const T c000 = c[0], c100 = c[cx], c010 = c[cy], c110 = c[cx + cy];
+        const T e100 = c000 + c100, e010 = c000 + c010, e110 = e100 + (c010 + c110);
+        const bool ez = !D3 || K >= 1;
+        if (ex && ey && ez) f[0] += c000;
+        if (ey && ez) f[fx] = fma(T(0.5), e100, f[fx]);
+        if (ex && ez) f[fy] = fma(T(0.5), e010, f[fy]);
+        if (ez) f[fx + fy] = fma(T(0.25), e110, f[fx + fy]);
+        if (D3) {
+            const T c001 = c[cz], c101 = c[cx + cz], c011 = c[cy + cz], c111 = c[cx + cy + cz];
+            const T s01 = c001 + c101, s02 = c001 + c011;
+            if (ex && ey) f[fz] = fma(T(0.5), c000 + c001, f[fz]);
+            if (ey) f[fx + fz] = fma(T(0.25), e100 + s01, f[fx + fz]);
+            if (ex) f[fy + fz] = fma(T(0.25), e010 + s02, f[fy + fz]);
+            f[fx + fy + fz] = fma(T(0.125), e110 + (s01 + (c011 + c111)), f[fx + fy + fz]);
+        }
+    }
+}
+
+// f = -B_z on the interior of the lower-boundary plane (eq. lower_bound)
+__device__ __forceinline__ void lower_rhs_body(const Geom& g, const double* __restrict__ bz, double* __restrict__ f,
+                                               dim3 b) {
+    const int i = 1 + b.x * blockDim.x + threadIdx.x;
+    const int j = 1 + b.y * blockDim.y + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const size_t o = at(g, i, j, 0);
+    f[o] = -bz[o];
+}
+
+// the lower-boundary solution as the z = 0 plane of a 3D array
+__device__ __forceinline__ void copy_plane_body(const Geom& g2, const double* __restrict__ src, const Geom& g3,
+                                                double* __restrict__ dst, dim3 b) {
+    const int i = b.x * blockDim.x + threadIdx.x;
+    const int j = b.y * blockDim.y + threadIdx.y;
+    if (i >= g2.nx || j >= g2.ny) return;
+    dst[at(g3, i, j, 0)] = src[at(g2, i, j, 0)];
+}
+
+// ||b||^2 partials of the lifted interior right-hand side: the Dirichlet data
+// on k = 0 enters row (i, j, 1) as cz * P(i, j, 0).  Every thread calls it.
+__device__ __forceinline__ void lift_norm_body(const Geom& g, const PlaneCoef<double>* __restrict__ coef,
+                                               const double* __restrict__ u, double* __restrict__ partial, dim3 b,
+                                               dim3 gd) {
+    const int i = 1 + b.x * blockDim.x + threadIdx.x;
+    const int j = 1 + b.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= g.nx - 2 && j <= g.ny - 2) {
+        const double v = coef[1].cz * u[at(g, i, j, 0)];
+        acc = v * v;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[b.x + gd.x * b.y] = s;
+}
+
+// grid of the per-node kernels: xcount threads along x, one row of blocks per
+// BY rows, planes spread over gridDim.z (capped by max_blocks when > 0)
+inline dim3 mg_grid(const Geom& g, int d3, int xcount, int max_blocks) {
+    const int gx = (xcount + MG_BX - 1) / MG_BX;
+    const int gy = (g.ny - 2 + MG_BY - 1) / MG_BY;
+    int gz = 1;
+    if (d3) {
+        gz = g.nz - 2;
+        const int cap = max_blocks > 0 ? max_blocks / (gx * gy) : 65535;
+        if (gz > cap) gz = cap > 0 ? cap : 1;
+        if (gz > 65535) gz = 65535;
+    }
+    return dim3(gx, gy, gz);
+}
+
+// the grids the solver launches each operation with
+inline dim3 smooth_grid(const Geom& g, int d3) { return mg_grid(g, d3, (g.nx - 2 + 1) / 2, 0); }
+inline dim3 residual_grid(const Geom& g, int d3, bool norm, int max_blocks) {
+    return mg_grid(g, d3, g.nx - 2, norm ? (max_blocks < 152 * 8 ? max_blocks : 152 * 8) : 0);
+}
+inline dim3 restrict_grid(const Geom& gc, int d3) { return mg_grid(gc, d3, gc.nx - 2, 0); }
+inline dim3 prolong_grid(const Geom& gc, int d3) {
+    Geom cells = gc;   // one thread per coarse cell: nc - 1 cells per axis
+    cells.ny = gc.ny + 1;
+    cells.nz = gc.nz + 1;
+    return mg_grid(cells, d3, gc.nx - 1, 0);
+}
+inline dim3 plane_grid(const Geom& g2) { return dim3((g2.nx + MG_BX - 1) / MG_BX, (g2.ny + MG_BY - 1) / MG_BY); }
+inline dim3 lift_grid(const Geom& g3) {
+    return dim3((g3.nx - 2 + MG_BX - 1) / MG_BX, (g3.ny - 2 + MG_BY - 1) / MG_BY);
+}
+
+}  // namespace mhs

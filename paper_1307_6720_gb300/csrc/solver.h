@@ -30,6 +30,11 @@ inline bool use_zline(const mhs_ctx* c) {
 bool tune_lookup(const mhs_ctx* c, int mode, mhs_solver_opts* o);
 void tune_clear();
 
+// grouped solves (group.cu)
+mhs_group* group_create(mhs_ctx** hs, int n, int mode);
+void group_destroy(mhs_group* G);
+mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses, double* ms);
+
 // slots of NormScratch::result
 constexpr int NORM_B_SLOT = 0;        // ||b||^2 of the current solve
 constexpr int NORM_RES_SLOT = 1;      // ||f - A u||^2 after the latest cycle

@@ -103,6 +103,10 @@ _SIGS = {
     "mhs_set_lower_bz": [_H, _P],
     "mhs_solve": [_H, _D, _I, ctypes.POINTER(SolveInfo)],
     "mhs_batch_solve": [ctypes.POINTER(_H), _I, _D, _I, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
+    "mhs_group_create": [ctypes.POINTER(_H), _I, _I, ctypes.POINTER(_H)],
+    "mhs_group_solve": [_H, _D, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
+    "mhs_group_destroy": [_H],
+    "mhs_group_set_eager": [_H, _I],
     "mhs_autotune": [_H, _D, _I, _I, ctypes.POINTER(TuneResult)],
     "mhs_tune_lookup": [_H, _I, ctypes.POINTER(SolverOpts), ctypes.POINTER(_I)],
     "mhs_tune_clear": [],
@@ -146,7 +150,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        if name in ("mhs_destroy", "mhs_server_destroy", "mhs_tune_clear"):
+        if name in ("mhs_destroy", "mhs_server_destroy", "mhs_tune_clear", "mhs_group_destroy"):
             fn.restype = None
         elif name in ("mhs_status_string", "mhs_last_error", "mhs_version", "mhs_kernel_kind_name"):
             fn.restype = ctypes.c_char_p
@@ -259,6 +263,33 @@ def mhs_batch_solve(handles, tol, mode=MHS_FP64):
     if st not in (MHS_OK, MHS_ERR_NO_CONVERGENCE, MHS_ERR_NONFINITE):
         _check(st)
     return [i.as_dict() for i in infos], list(sts)
+
+
+def mhs_group_create(handles, mode=MHS_MIXED) -> int:
+    """One grouped solver over the handles (one launch per operation and level for all)."""
+    n = len(handles)
+    arr = (_H * n)(*handles)
+    g = _H()
+    _check(LIB.mhs_group_create(arr, n, mode, ctypes.byref(g)))
+    return g.value
+
+
+def mhs_group_solve(g, n, tol):
+    """Solve the group's n instances; returns (per-instance info dicts, per-instance statuses)."""
+    infos = (SolveInfo * n)()
+    sts = (_I * n)()
+    st = LIB.mhs_group_solve(g, tol, infos, sts)
+    if st not in (MHS_OK, MHS_ERR_NO_CONVERGENCE, MHS_ERR_NONFINITE):
+        _check(st)
+    return [i.as_dict() for i in infos], list(sts)
+
+
+def mhs_group_set_eager(g, eager=True) -> None:
+    _check(LIB.mhs_group_set_eager(g, 1 if eager else 0))
+
+
+def mhs_group_destroy(g) -> None:
+    LIB.mhs_group_destroy(g)
 
 
 def mhs_autotune(h, tol, mode=MHS_FP64, repeats=2) -> dict:

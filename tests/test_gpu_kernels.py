@@ -29,9 +29,12 @@ SHAPES = [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5)]
 
 
 def _make(M, nx, ny, nz, Lx=1.0, Ly=0.6, Lz=0.8, alpha=0.7, xi=XI2):
+    """A handle on red-black point smoothing (the oracle's default smoother),
+    whatever smoother the anisotropy of the grid would select."""
     pr = S.problem(nx, ny, nz, Lx=Lx, Ly=Ly, Lz=Lz, alpha=alpha, **xi)
     h = M.mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha,
                      M.xi_params(xi["xi_kind"], xi["xi_a"], xi["xi_kappa"], xi.get("xi_b", 0), xi.get("xi_omega", 0)))
+    M.mhs_set_options(h, flags=M.MHS_FLAG_POINT)
     return pr, h
 
 
@@ -205,7 +208,7 @@ def test_fused_sweep_equals_colour_passes_bitwise(M, shape):
     out = []
     for flags in (0, M.MHS_FLAG_FUSED_SWEEP64):
         pr, h = _make(M, nx, ny, nz)
-        M.mhs_set_options(h, flags=flags)
+        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, 0, u)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, 0, f)
         for _ in range(3):
@@ -223,7 +226,7 @@ def test_fused_sweep_fp64_solve_matches_default(M):
     for flags in (0, M.MHS_FLAG_FUSED_SWEEP64):
         h = M.mhs_create(65, 65, 65, 1.0, 1.0, 1.0, pr["alpha"],
                          M.xi_params(pr["xi_kind"], pr["xi_a"], pr["xi_kappa"]))
-        M.mhs_set_options(h, flags=flags)
+        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT)
         M.mhs_set_lower_bz(h, bz)
         info = M.mhs_solve(h, 1e-11, M.MHS_FP64)
         phi = np.zeros((65, 65, 65)); M.mhs_get_phi(h, phi)
@@ -244,7 +247,7 @@ def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
     out = []
     for flags in (0, M.MHS_FLAG_NO_TMA):
         pr, h = _make(M, nx, ny, nz)
-        M.mhs_set_options(h, flags=flags, fused_min=1)
+        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT, fused_min=1)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, 1, u)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, 1, f)
         for _ in range(5):
