@@ -124,6 +124,11 @@ typedef struct {
                                    Without this flag or MHS_FLAG_POINT the smoother is chosen from the problem:
                                    z-line when the anisotropy class (see mhs_autotune) is 5 or more */
 #define MHS_FLAG_POINT 128      /* always smooth by red-black point Gauss-Seidel */
+#define MHS_FLAG_SEPARABLE 256  /* mixed mode: each outer step solves the correction equation with the exact
+                                   separable solver (FP32 sine transforms in x and y, one tridiagonal system
+                                   along z per mode; valid because xi depends on z only and the sides are
+                                   Dirichlet) instead of an FP32 V-cycle; same solution, 2-3 outer steps.
+                                   Ignored in FP64 mode; not available in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
@@ -205,20 +210,29 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * instance runs the operations of its solo mhs_solve with the same block
  * decomposition, so its P is bitwise identical to solving it alone.
  *
+ * The instances, ordered by decreasing cycle working set (every level's
+ * arrays in the cycle precision, plus the double-float state in mixed
+ * mode), are packed into parts of at most part_bytes of working set (0:
+ * half the L2 cache), so that a part holds instances of similar size; each
+ * part is one graph, and the parts are launched round-robin on nstreams
+ * streams (0: 16), so that several parts run at once.  part_bytes = SIZE_MAX makes one
+ * part of all instances.
+ *
  * mhs_group_create snapshots the handles' options, cut-offs and smoother
  * choice (recreate the group after changing a member's options, or its
  * parameters when that moves it to another anisotropy class) and captures
- * the graph.  The handles must outlive the group and must not be used for
+ * the graphs.  The handles must outlive the group and must not be used for
  * other work while a group solve runs.  Not supported: MHS_FLAG_WARM,
  * inner_cycles other than 1 (MHS_ERR_INVALID_ARG).
- * Errors: MHS_ERR_INVALID_ARG (n < 1, NULL or repeated handle, bad mode),
- * MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA. */
+ * Errors: MHS_ERR_INVALID_ARG (n < 1, NULL or repeated handle, bad mode,
+ * nstreams outside [0, 64]), MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA. */
 typedef struct mhs_group* mhs_group_t;
-MHS_API mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out);
+MHS_API mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, size_t part_bytes, int nstreams,
+                                    mhs_group_t* out);
 /* Solve every instance of the group to tol with its current B_z (set by
  * mhs_set_lower_bz, which must have returned for every member).  infos and
- * statuses (n entries each) may be NULL; infos[q].ms is the group's device
- * time.  Returns MHS_OK or the first failing instance's status
+ * statuses (n entries each) may be NULL; infos[q].ms is the device time
+ * of the part holding instance q.  Returns MHS_OK or the first failing instance's status
  * (MHS_ERR_NO_CONVERGENCE, MHS_ERR_NONFINITE); MHS_ERR_BAD_STATE when a
  * member has no B_z; MHS_ERR_CUDA. */
 MHS_API mhs_status mhs_group_solve(mhs_group_t g, double tol, mhs_solve_info* infos, mhs_status* statuses);
@@ -418,7 +432,8 @@ MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int pr
 #define MHS_KT_CORRECT 11      /* (hi, lo) += e32, the double-float iterate */
 #define MHS_KT_FIELDS 12       /* B, p, rho */
 #define MHS_KT_OTHER 13        /* set-up, copies, norms of the right-hand side */
-#define MHS_KT_COUNT 14
+#define MHS_KT_SEPARABLE 14    /* separable inner solve (sine transforms, mode tridiagonal solves) */
+#define MHS_KT_COUNT 15
 MHS_API mhs_status mhs_set_kernel_timing(mhs_handle h, int enable);
 MHS_API mhs_status mhs_kernel_timing(mhs_handle h, int kind, double* total_ms, long long* launches,
                                      double* alg_bytes, double* alg_flops);

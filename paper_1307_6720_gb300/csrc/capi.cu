@@ -268,10 +268,11 @@ mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, mhs_solv
     return guarded([&] { return mhs::batch_solve(hs, n, tol, mode, infos, statuses); });
 }
 
-mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out) {
+mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, size_t part_bytes, int nstreams, mhs_group_t* out) {
     if (!out) return fail(MHS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!hs || n < 1) return fail(MHS_ERR_INVALID_ARG, "group: need at least one handle");
+    if (nstreams < 0 || nstreams > 64) return fail(MHS_ERR_INVALID_ARG, "group: nstreams must be in [0, 64]");
     if (mode != MHS_FP64 && mode != MHS_MIXED) return fail(MHS_ERR_INVALID_ARG, "unknown precision mode");
     for (int q = 0; q < n; ++q) {
         if (!hs[q]) return fail(MHS_ERR_INVALID_ARG, "NULL handle in group");
@@ -279,7 +280,7 @@ mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out) {
             if (hs[r] == hs[q]) return fail(MHS_ERR_INVALID_ARG, "a handle appears twice in the group");
     }
     return guarded([&] {
-        *out = mhs::group_create(hs, n, mode);
+        *out = mhs::group_create(hs, n, mode, part_bytes, nstreams);
         return MHS_OK;
     });
 }
@@ -287,10 +288,11 @@ mhs_status mhs_group_create(mhs_handle* hs, int n, int mode, mhs_group_t* out) {
 mhs_status mhs_group_solve(mhs_group_t g, double tol, mhs_solve_info* infos, mhs_status* statuses) {
     if (!g) return fail(MHS_ERR_INVALID_ARG, "group is NULL");
     if (!(tol > 0.0 && tol < 1.0)) return fail(MHS_ERR_INVALID_ARG, "tol must be in (0, 1)");
-    for (mhs_ctx* c : g->hs)
-        if (!c->have_bz) return fail(MHS_ERR_BAD_STATE, "every group member needs mhs_set_lower_bz before a solve");
+    for (const mhs::GPart* p : g->parts)
+        for (const mhs_ctx* c : p->hs)
+            if (!c->have_bz) return fail(MHS_ERR_BAD_STATE, "every group member needs mhs_set_lower_bz before a solve");
     return guarded([&] {
-        const mhs_status s = mhs::group_solve(g, tol, infos, statuses, nullptr);
+        const mhs_status s = mhs::group_solve(g, tol, infos, statuses);
         if (s != MHS_OK) return fail(s, s == MHS_ERR_NO_CONVERGENCE ? "an instance did not converge"
                                                                     : "an instance has a non-finite residual");
         return MHS_OK;
@@ -301,7 +303,7 @@ void mhs_group_destroy(mhs_group_t g) { mhs::group_destroy(g); }
 
 mhs_status mhs_group_set_eager(mhs_group_t g, int eager) {
     if (!g) return fail(MHS_ERR_INVALID_ARG, "group is NULL");
-    g->eager = eager != 0;
+    mhs::group_set_eager(g, eager != 0);
     return MHS_OK;
 }
 
@@ -624,7 +626,8 @@ mhs_status mhs_kernel_timing_reset(mhs_handle h) {
 const char* mhs_kernel_kind_name(int kind) {
     static const char* names[MHS_KT_COUNT] = {"smooth64", "smooth32", "residual64", "residual32", "restrict64",
                                               "restrict32", "prolong64", "prolong32", "coarse64", "coarse32",
-                                              "residual_mixed", "correct", "fields", "other"};
+                                              "residual_mixed", "correct", "fields", "other",
+                                              "separable"};
     return (kind >= 0 && kind < MHS_KT_COUNT) ? names[kind] : "unknown";
 }
 

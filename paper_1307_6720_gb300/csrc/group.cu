@@ -29,7 +29,7 @@ namespace mhs {
 
 namespace {
 
-void* galloc(mhs_group* G, size_t bytes) {
+void* galloc(GPart* G, size_t bytes) {
     void* p = nullptr;
     const cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
@@ -40,7 +40,7 @@ void* galloc(mhs_group* G, size_t bytes) {
     return p;
 }
 
-GTable upload(mhs_group* G, std::vector<GItem>& v) {
+GTable upload(GPart* G, std::vector<GItem>& v) {
     GTable t;
     long long off = 0;
     for (GItem& it : v) {
@@ -94,7 +94,7 @@ dim3 fat(dim3 grid) {
 
 // Build the tables of one problem for cycles in precision T.
 template <typename T>
-void build_dim(mhs_group* G, GDim& D, int dim) {
+void build_dim(GPart* G, GDim& D, int dim) {
     const int n = int(G->hs.size());
     const bool dbl = sizeof(T) == 8, mixed = G->mode == MHS_MIXED;
     const int d3 = dim == 3;
@@ -389,7 +389,7 @@ namespace {
 // fmg_step >= 0 restricts the launch to instances whose full-multigrid top
 // level is at least fmg_step (the up-sweep of the first cycle).
 template <typename T>
-void gvcycle(mhs_group* G, GDim& D, int s, int fmg_step, int gate) {
+void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
     auto smooth = [&](std::vector<GTable>& pt, std::vector<GTable>& ln, int l, int nsweep) {
@@ -414,7 +414,7 @@ void gvcycle(mhs_group* G, GDim& D, int s, int fmg_step, int gate) {
 // without MHS_FLAG_NO_FMG): restrict the first residual to each instance's
 // top level, then up level by level: prolongate and run a V-cycle
 template <typename T>
-void gfmg(mhs_group* G, GDim& D) {
+void gfmg(GPart* G, GDim& D) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
     const bool mixed = G->mode == MHS_MIXED;
@@ -432,7 +432,7 @@ void gfmg(mhs_group* G, GDim& D) {
 }
 
 template <typename T>
-void gprologue(mhs_group* G, GDim& D) {
+void gprologue(GPart* G, GDim& D) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
     const bool mixed = G->mode == MHS_MIXED;
@@ -466,7 +466,7 @@ void gprologue(mhs_group* G, GDim& D) {
 }
 
 template <typename T>
-void gcycle(mhs_group* G, GDim& D, SolveCtl* const* ctls, cudaGraphConditionalHandle h, bool graph = true) {
+void gcycle(GPart* G, GDim& D, SolveCtl* const* ctls, cudaGraphConditionalHandle h, bool graph = true) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
     const bool mixed = G->mode == MHS_MIXED;
@@ -485,7 +485,7 @@ void gcycle(mhs_group* G, GDim& D, SolveCtl* const* ctls, cudaGraphConditionalHa
 // append a while node (condition handle h) to the graph captured on
 // G->stream, its body captured from fn on the second capture stream
 template <typename F>
-void gadd_while(mhs_group* G, cudaGraphConditionalHandle h, F&& fn) {
+void gadd_while(GPart* G, cudaGraphConditionalHandle h, F&& fn) {
     cudaStreamCaptureStatus status;
     cudaGraph_t graph;
     const cudaGraphNode_t* deps = nullptr;
@@ -510,7 +510,7 @@ void gadd_while(mhs_group* G, cudaGraphConditionalHandle h, F&& fn) {
 }
 
 template <typename T>
-void gbuild_graph(mhs_group* G) {
+void gbuild_graph(GPart* G) {
     const int n = int(G->hs.size());
     cudaStream_t user = G->stream;
     G->stream = G->cap;
@@ -560,13 +560,15 @@ void gbuild_graph(mhs_group* G) {
 
 }  // namespace
 
-mhs_group* group_create(mhs_ctx** hs, int n, int mode) {
-    auto G = std::make_unique<mhs_group>();
+GPart* part_create(mhs_ctx** hs, int n, int mode) {
+    auto G = std::make_unique<GPart>();
     G->mode = mode;
     G->hs.assign(hs, hs + n);
     for (mhs_ctx* c : G->hs) {
         if (c->opts.flags & MHS_FLAG_WARM) throw Error(MHS_ERR_INVALID_ARG, "group: warm starts are not supported");
         if (c->opts.inner_cycles != 1) throw Error(MHS_ERR_INVALID_ARG, "group: inner_cycles must be 1");
+        if (c->opts.flags & MHS_FLAG_SEPARABLE)
+            throw Error(MHS_ERR_INVALID_ARG, "group: the separable inner solver is not available in groups");
     }
     gsubcycle_prepare();
     MHS_CUDA(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
@@ -597,7 +599,7 @@ mhs_group* group_create(mhs_ctx** hs, int n, int mode) {
     return G.release();
 }
 
-void group_destroy(mhs_group* G) {
+void part_destroy(GPart* G) {
     if (!G) return;
     if (G->stream) cudaStreamSynchronize(G->stream);
     if (G->exec) cudaGraphExecDestroy(G->exec);
@@ -616,7 +618,7 @@ void group_destroy(mhs_group* G) {
 // read the OR of the continuation flags back after each cycle), for
 // profilers that cannot see kernels inside conditional graph nodes.
 template <typename T>
-void geager(mhs_group* G) {
+void geager(GPart* G) {
     const int n = int(G->hs.size());
     auto any = [&](SolveCtl* const* ctls) {
         glaunch_any(ctls, n, 0, 0, G->any_dev, G->stream);
@@ -633,11 +635,14 @@ void geager(mhs_group* G) {
     glaunch_gather_ctl(G->ctls, 2 * n, G->gathered, G->stream);
 }
 
-// One grouped solve: control blocks initialised on the host and copied in,
-// the graph launched, the control blocks gathered back.  Returns the first
-// failing instance's status (per-instance statuses in `statuses`).
-mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses, double* ms_out) {
+// Enqueue one grouped solve on the group's stream: control blocks
+// initialised on the host and copied in, the graph (or the eager sequence)
+// launched, the control blocks gathered back into pinned memory.
+void part_launch(GPart* G, double tol, cudaStream_t st) {
     const int n = int(G->hs.size());
+    G->tol = tol;
+    const cudaStream_t own = G->stream;
+    G->stream = st;
     for (int q = 0; q < n; ++q) {
         mhs_ctx* c = G->hs[q];
         for (int k = 0; k < 2; ++k) {
@@ -648,18 +653,31 @@ mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_stat
         MHS_CUDA(cudaMemcpyAsync(c->ctl, c->ctl_host, 2 * sizeof(SolveCtl), cudaMemcpyHostToDevice, G->stream));
     }
     MHS_CUDA(cudaEventRecord(G->ev0, G->stream));
-    const long long l0 = launches();
-    if (G->eager) {
-        if (G->mode == MHS_MIXED) geager<float>(G);
-        else geager<double>(G);
-    } else {
-        MHS_CUDA(cudaGraphLaunch(G->exec, G->stream));
+    try {
+        if (G->eager) {
+            if (G->mode == MHS_MIXED) geager<float>(G);
+            else geager<double>(G);
+        } else {
+            MHS_CUDA(cudaGraphLaunch(G->exec, G->stream));
+        }
+    } catch (...) {
+        G->stream = own;
+        throw;
     }
-    const long long eager_launches = launches() - l0;
     MHS_CUDA(cudaEventRecord(G->ev1, G->stream));
     MHS_CUDA(cudaMemcpyAsync(G->gathered_host, G->gathered, 2 * size_t(n) * sizeof(SolveCtl), cudaMemcpyDeviceToHost,
                              G->stream));
-    MHS_CUDA(cudaStreamSynchronize(G->stream));
+    G->launch_stream = st;
+    G->stream = own;
+}
+
+// Wait for the solve enqueued by part_launch and report it.  Returns the
+// first failing instance's status (per-instance statuses in `statuses`).
+mhs_status part_wait(GPart* G, mhs_solve_info* infos, mhs_status* statuses, double* ms_out) {
+    const int n = int(G->hs.size());
+    const double tol = G->tol;
+    MHS_CUDA(cudaEventSynchronize(G->ev1));
+    MHS_CUDA(cudaStreamSynchronize(G->launch_stream));
     float ms = 0.f;
     MHS_CUDA(cudaEventElapsedTime(&ms, G->ev0, G->ev1));
     if (ms_out) *ms_out = ms;
@@ -691,7 +709,111 @@ mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_stat
     }
     // graph: the prologues and epilogues once, each while body once per cycle of the slowest instance
     if (!G->eager) count_launches(G->n_fixed + (long long)max2 * G->n_cycle2 + (long long)max3 * G->n_cycle3);
-    (void)eager_launches;
+    return worst;
+}
+
+// Device bytes one multigrid cycle of a handle's interior problem touches:
+// the arrays of every level in the precision of the cycles, plus the
+// double-float state of the finest level in mixed mode.
+size_t cycle_bytes(const mhs_ctx* c, int mode) {
+    size_t b = 0;
+    const Hierarchy& H = c->h3;
+    const size_t s = mode == MHS_MIXED ? sizeof(float) : sizeof(double);
+    for (int l = 0; l < H.nlev(); ++l) b += 3 * H.g[l].n * s;
+    if (mode == MHS_MIXED) b += 2 * H.g[0].n * sizeof(float);
+    return b;
+}
+
+// ---- groups: parts of L2-sized working sets on a few launch streams ----
+
+mhs_group* group_create(mhs_ctx** hs, int n, int mode, size_t part_bytes, int nstreams) {
+    if (part_bytes == 0) {
+        int dev = 0, l2 = 0;
+        MHS_CUDA(cudaGetDevice(&dev));
+        MHS_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        part_bytes = size_t(l2) / 2;
+    }
+    if (nstreams <= 0) nstreams = 16;
+    auto G = std::make_unique<mhs_group>();
+    G->n = n;
+    // instances by decreasing cycle working set (stable), then greedy: a part
+    // takes instances until the next would push its working set over
+    // part_bytes.  Similar sizes share a part, so a part's lock-step cycles
+    // do not make small instances wait on large ones, large instances get
+    // parts of their own that run concurrently, and small ones pack into
+    // few launches.
+    std::vector<size_t> bytes(n);
+    std::vector<int> order(n);
+    for (int q = 0; q < n; ++q) {
+        bytes[q] = cycle_bytes(hs[q], mode);
+        order[q] = q;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+    std::vector<int> cur;
+    size_t acc = 0;
+    for (int q : order) {
+        const size_t b = bytes[q];
+        if (!cur.empty() && acc + b > part_bytes) {
+            G->members.push_back(cur);
+            cur.clear();
+            acc = 0;
+        }
+        cur.push_back(q);
+        acc += b;
+    }
+    if (!cur.empty()) G->members.push_back(cur);
+    try {
+        for (const auto& m : G->members) {
+            std::vector<mhs_ctx*> part;
+            for (int q : m) part.push_back(hs[q]);
+            G->parts.push_back(part_create(part.data(), int(part.size()), mode));
+        }
+        const int k = std::min<int>(nstreams, int(G->parts.size()));
+        for (int s = 0; s < k; ++s) {
+            cudaStream_t st;
+            MHS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            G->streams.push_back(st);
+        }
+    } catch (...) {
+        group_destroy(G.release());
+        throw;
+    }
+    return G.release();
+}
+
+void group_destroy(mhs_group* G) {
+    if (!G) return;
+    for (GPart* p : G->parts) part_destroy(p);
+    for (cudaStream_t s : G->streams) cudaStreamDestroy(s);
+    delete G;
+}
+
+void group_set_eager(mhs_group* G, bool eager) {
+    G->eager = eager;
+    for (GPart* p : G->parts) p->eager = eager;
+}
+
+mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses) {
+    const size_t P = G->parts.size();
+    for (size_t p = 0; p < P; ++p) part_launch(G->parts[p], tol, G->streams[p % G->streams.size()]);
+    mhs_status worst = MHS_OK;
+    std::vector<mhs_solve_info> pi;
+    std::vector<mhs_status> ps;
+    double ms_max = 0.0;
+    for (size_t p = 0; p < P; ++p) {
+        const auto& m = G->members[p];
+        pi.assign(m.size(), mhs_solve_info{});
+        ps.assign(m.size(), MHS_OK);
+        double ms = 0.0;
+        const mhs_status s = part_wait(G->parts[p], pi.data(), ps.data(), &ms);
+        ms_max = std::max(ms_max, ms);
+        if (s != MHS_OK && worst == MHS_OK) worst = s;
+        for (size_t i = 0; i < m.size(); ++i) {
+            if (infos) infos[m[i]] = pi[i];
+            if (statuses) statuses[m[i]] = ps[i];
+        }
+    }
+    (void)ms_max;
     return worst;
 }
 

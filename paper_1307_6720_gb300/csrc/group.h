@@ -89,22 +89,35 @@ struct GDim {
     GTable zero_e, correct, fmg_zero_e, fmg_correct, to_double;
 };
 
-}  // namespace mhs
-
-struct mhs_group {
+// One part of a group: instances solved by one graph (one launch per
+// operation and level for all of them).
+struct GPart {
     std::vector<mhs_ctx*> hs;
     int mode = MHS_MIXED;
     cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
-    mhs::GDim d2, d3;
-    mhs::SolveCtl** ctls = nullptr;     // device: [2n] = n lower-boundary then n interior control blocks
-    mhs::SolveCtl* gathered = nullptr;  // device copy of the 2n control blocks after a solve
-    mhs::SolveCtl* gathered_host = nullptr;   // pinned
+    GDim d2, d3;
+    SolveCtl** ctls = nullptr;          // device: [2n] = n lower-boundary then n interior control blocks
+    SolveCtl* gathered = nullptr;       // device copy of the 2n control blocks after a solve
+    SolveCtl* gathered_host = nullptr;  // pinned
     cudaGraphExec_t exec = nullptr;
     long long n_fixed = 0, n_cycle2 = 0, n_cycle3 = 0;   // kernel launches of the graph's sections
     bool eager = false;                 // host-driven launches instead of the graph
+    double tol = 0.0;                   // tolerance of the solve in flight
+    cudaStream_t launch_stream = nullptr;   // stream of the solve in flight
     int* any_dev = nullptr;             // OR of the continuation flags (eager loop)
     int* any_host = nullptr;            // pinned
 };
 
+}  // namespace mhs
+
+// A group: its instances split into parts whose working sets fit the L2
+// cache, the parts launched round-robin on a few streams.
+struct mhs_group {
+    std::vector<mhs::GPart*> parts;
+    std::vector<std::vector<int>> members;   // instance indices of each part
+    std::vector<cudaStream_t> streams;       // launch streams
+    int n = 0;
+    bool eager = false;
+};

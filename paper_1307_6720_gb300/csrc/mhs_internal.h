@@ -193,6 +193,10 @@ struct mhs_ctx {
     double* staging = nullptr;     // FP64 staging buffer of the finest size (level hooks, lazily allocated)
     double* fld[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // pitched Bx, By, Bz, p, rho
     double* post[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}; // pitched jx, jy, jz, |j|, |B| (on first use)
+    struct {
+        float *sx = nullptr, *sy = nullptr;    // sine matrices of the x and y interiors (separable solver)
+        float *mux = nullptr, *muy = nullptr;  // their eigenvalues -4 sin^2(pi m / (2 (n - 1)))
+    } sep;
     bool have_bz = false, have_solution = false;
     bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
     std::vector<void*> allocations;

@@ -391,7 +391,13 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     const Geom& g = H.g[0];
     if (e.mode == MHS_MIXED) {
         MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
-        for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
+        if (c->opts.flags & MHS_FLAG_SEPARABLE) {
+            const double N = double(g.interior());
+            TimedScope t(c->timer, MHS_KT_SEPARABLE, N * 4.0 * 2.0, 0.0, c->stream, H.dim == 3);
+            sep_solve(c, H);
+        } else {
+            for (int q = 0; q < c->opts.inner_cycles; ++q) vcycle<float>(c, H, 0);
+        }
         TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()) * 8.0, c->stream,
                      H.dim == 3);
         launch_df_correct(g, H.dim, H.s[0].u, H.df.hi, H.df.lo, c->stream);
@@ -410,6 +416,7 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
 static void fmg_cycle(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     mhs_ctx* c = e.c;
     if (c->opts.flags & MHS_FLAG_NO_FMG) return;
+    if (e.mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_SEPARABLE)) return;   // the first step is already exact
     const Geom& g = H.g[0];
     if (e.mode == MHS_MIXED) {
         MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
@@ -514,7 +521,7 @@ static void add_while(mhs_ctx* c, cudaGraphConditionalHandle hnd, F&& fn) {
 static long long graph_key(mhs_ctx* c) {
     return (long long)c->opts.nu1 | (long long)c->opts.nu2 << 8 | (long long)c->opts.inner_cycles << 16 |
            (long long)(c->opts.flags & MHS_FLAG_WARM) << 24 | (long long)c->f_zero_finest << 25 |
-           (long long)use_zline(c) << 26;
+           (long long)use_zline(c) << 26 | (long long)(c->opts.flags & MHS_FLAG_SEPARABLE) << 27;
 }
 
 static void build_graph(mhs_ctx* c, int mode) {
@@ -574,6 +581,7 @@ static bool read_cont(mhs_ctx* c, int which) {
 // in eager mode (kernel timing enabled) the host drives the cycles.
 void solve_begin(mhs_ctx* c, double tol, int mode) {
     cudaStream_t st = c->stream;
+    if (mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_SEPARABLE)) sep_prepare(c);   // allocations: not in a capture
     for (int q = 0; q < 2; ++q) {
         c->ctl_host[q] = SolveCtl{};
         c->ctl_host[q].tol = tol;

@@ -31,9 +31,11 @@ bool tune_lookup(const mhs_ctx* c, int mode, mhs_solver_opts* o);
 void tune_clear();
 
 // grouped solves (group.cu)
-mhs_group* group_create(mhs_ctx** hs, int n, int mode);
+mhs_group* group_create(mhs_ctx** hs, int n, int mode, size_t part_bytes, int nstreams);
 void group_destroy(mhs_group* G);
-mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses, double* ms);
+void group_set_eager(mhs_group* G, bool eager);
+mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses);
+size_t cycle_bytes(const mhs_ctx* c, int mode);
 
 // slots of NormScratch::result
 constexpr int NORM_B_SLOT = 0;        // ||b||^2 of the current solve
@@ -57,6 +59,9 @@ void smooth_hook(mhs_ctx* c, Hierarchy& H, int l);   // one sweep as the V-cycle
 double read_norm2(mhs_ctx* c, int slot);
 void ensure_field_buffers(mhs_ctx* c);
 void ensure_post_buffers(mhs_ctx* c);
+// separable inner solver (kernels_sep.cu)
+void sep_prepare(mhs_ctx* c);
+void sep_solve(mhs_ctx* c, Hierarchy& H);
 void ensure_staging(mhs_ctx* c);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)

@@ -24,7 +24,7 @@ MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
 MHS_FP64, MHS_MIXED = 0, 1
 MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, MHS_FLAG_NO_TMA, MHS_FLAG_NO_FMG = \
     1, 2, 4, 8, 16, 32
-MHS_FLAG_ZLINE, MHS_FLAG_POINT = 64, 128
+MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE = 64, 128, 256
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
 
@@ -103,7 +103,7 @@ _SIGS = {
     "mhs_set_lower_bz": [_H, _P],
     "mhs_solve": [_H, _D, _I, ctypes.POINTER(SolveInfo)],
     "mhs_batch_solve": [ctypes.POINTER(_H), _I, _D, _I, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
-    "mhs_group_create": [ctypes.POINTER(_H), _I, _I, ctypes.POINTER(_H)],
+    "mhs_group_create": [ctypes.POINTER(_H), _I, _I, ctypes.c_size_t, _I, ctypes.POINTER(_H)],
     "mhs_group_solve": [_H, _D, ctypes.POINTER(SolveInfo), ctypes.POINTER(_I)],
     "mhs_group_destroy": [_H],
     "mhs_group_set_eager": [_H, _I],
@@ -265,12 +265,14 @@ def mhs_batch_solve(handles, tol, mode=MHS_FP64):
     return [i.as_dict() for i in infos], list(sts)
 
 
-def mhs_group_create(handles, mode=MHS_MIXED) -> int:
-    """One grouped solver over the handles (one launch per operation and level for all)."""
+def mhs_group_create(handles, mode=MHS_MIXED, part_bytes=0, nstreams=0) -> int:
+    """A grouped solver over the handles: parts of at most part_bytes cycle working set (0: half the
+    L2; ctypes.c_size_t(-1).value: one part), one launch per operation and level per part, parts
+    launched round-robin on nstreams streams (0: 16)."""
     n = len(handles)
     arr = (_H * n)(*handles)
     g = _H()
-    _check(LIB.mhs_group_create(arr, n, mode, ctypes.byref(g)))
+    _check(LIB.mhs_group_create(arr, n, mode, part_bytes, nstreams, ctypes.byref(g)))
     return g.value
 
 
@@ -371,7 +373,7 @@ def mhs_level_op(h, dim, level, op, prec) -> None:
     _check(LIB.mhs_level_op(h, dim, level, op, prec))
 
 
-MHS_KT_COUNT = 14
+MHS_KT_COUNT = 15
 
 
 def mhs_set_kernel_timing(h, enable: bool) -> None:

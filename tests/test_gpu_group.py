@@ -52,10 +52,17 @@ def _phi(M, h, pr):
     return out
 
 
+ONE_PART = (1 << 64) - 1
+
+
+@pytest.mark.parametrize("parts", ["default", "one", "each"])
 @pytest.mark.parametrize("mode", [1, 0])
-def test_group_solve_bitwise_equals_solo_solves(M, mode):
+def test_group_solve_bitwise_equals_solo_solves(M, mode, parts):
+    """Default partition (half the L2 per part, two launch streams), all
+    instances in one part, and one part per instance on three streams."""
     hs, prs, bzs = _members(M)
-    g = M.mhs_group_create(hs, mode)
+    part_bytes, nstreams = {"default": (0, 0), "one": (ONE_PART, 1), "each": (1, 3)}[parts]
+    g = M.mhs_group_create(hs, mode, part_bytes, nstreams)
     tol = 1e-10
     infos, sts = M.mhs_group_solve(g, len(hs), tol)
     assert all(s == M.MHS_OK for s in sts), sts

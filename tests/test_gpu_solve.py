@@ -384,3 +384,32 @@ def test_zline_solve_with_strong_vertical_coupling(M, shape, mode):
     assert info_l["cycles_3d"] <= 10, info_l
     assert info_p["cycles_3d"] >= 2 * info_l["cycles_3d"], (info_p, info_l)
     _compare(got, _oracle(pr, bz), 1e-10 if mode == 0 else 1e-8)
+
+
+@pytest.mark.parametrize("case", ["lin129", "xi2_aniso", "paper", "strong", "small"])
+def test_separable_inner_solver_reaches_exact_solution(M, case):
+    """Mixed mode with the exact separable inner solver (sine transforms and
+    one tridiagonal system per mode, in FP32): every outer step cuts the
+    error by about the FP32 rounding level, so a few steps reach a 5e-12
+    residual (near the double-float floor of the 129 x 129 lower-boundary
+    plane), and the fields match the exact discrete solution to the FP64
+    bar."""
+    if case == "lin129":
+        pr, bz = S.linear_mhs(129, seed=51)
+    elif case == "xi2_aniso":
+        pr = S.problem(65, 33, 17, Lx=1.0, Ly=0.75, Lz=0.3, alpha=0.3, xi_kind=2, xi_a=0.7, xi_b=0.3,
+                       xi_omega=np.pi, xi_kappa=0.1)
+        bz = S.magnetogram_random(65, 33, 1.0, 0.75, seed=52)
+    elif case == "paper":
+        pr = S.problem(129, 129, 129, Lx=11.0, Ly=11.0, Lz=12.0, alpha=0.2, **_PAPER_XI["xi2"])
+        sp = [S.Spot(1.0, -1.0, -1.0, 0.3), S.Spot(-1.0, 1.0, 1.0, 0.3)]
+        bz = S.spots_field(129, 129, 11.0, 11.0, sp, -5.5, -5.5)
+    elif case == "strong":
+        pr = S.problem(65, 65, 65, alpha=0.5, xi_kind=1, xi_a=0.999, xi_kappa=0.5)
+        bz = S.magnetogram_random(65, 65, seed=53)
+    else:
+        pr = S.problem(5, 9, 5, Ly=2.0, alpha=0.4)
+        bz = S.magnetogram_random(5, 9, 1.0, 2.0, seed=54)
+    info, got = _gpu_solve(M, pr, bz, 5e-12, M.MHS_MIXED, opts=dict(flags=M.MHS_FLAG_SEPARABLE))
+    assert info["cycles_3d"] <= 4 and info["cycles_2d"] <= 4, info
+    _compare(got, _oracle(pr, bz), 1e-10)
