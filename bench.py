@@ -303,6 +303,7 @@ def run_gpu(args):
     ms_o, infos_o = timed(args.steps, other)
     M.mhs_set_options(h, flags=flags | M.MHS_FLAG_SEPARABLE)
     ms_s, infos_s = timed(args.steps, M.MHS_MIXED)
+    ms_s64, infos_s64 = timed(args.steps, M.MHS_FP64)
     M.mhs_set_options(h, flags=flags)
 
     # end to end through the C ABI with pinned host buffers
@@ -343,7 +344,12 @@ def run_gpu(args):
                                           "cycles_3d": infos_s[-1]["cycles_3d"],
                                           "rel_res_3d": infos_s[-1]["rel_res_3d"],
                                           "solver": "exact separable inner solve (sine transforms + tridiagonal "
-                                                    "per mode) in the double-float defect correction"}},
+                                                    "per mode) in the double-float defect correction"},
+                      "fp64_separable": {"value": unknowns * world / (ms_s64 * 1e-3), "ms_per_step": ms_s64,
+                                         "cycles_3d": infos_s64[-1]["cycles_3d"],
+                                         "rel_res_3d": infos_s64[-1]["rel_res_3d"],
+                                         "solver": "FP64 direct separable solves (fast sine transforms + "
+                                                   "tridiagonal per mode)"}},
             "kernels": kernels,
         }
         out.update(extra)
@@ -354,14 +360,19 @@ def run_gpu(args):
 
 
 def run_op(args):
-    """One finest-level operation of the 129^3 interior hierarchy, repeated; prints its mean device time."""
+    """One finest-level operation of an interior hierarchy (the 129^3 workload's parameters on the grid
+    --grid, isotropic spacing), repeated; prints its mean device time."""
     import numpy as np
     import torch
     from paper_1307_6720_gb300 import mhs as M
     pr, mags, cfg = workload(0)
+    nx, ny, nz = args.grid
+    pr = dict(pr, nx=nx, ny=ny, nz=nz, Lx=1.0, Ly=(ny - 1) / (nx - 1), Lz=(nz - 1) / (nx - 1))
     xi = M.xi_params(M.MHS_XI_EXP, pr["xi_a"], pr["xi_kappa"])
     h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
     M.mhs_set_stream(h, torch.cuda.current_stream())
+    M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE if args.smoother == "zline" else M.MHS_FLAG_POINT,
+                      fused_min=1 if args.tma else 0)
     prec = M.MHS_FP64 if args.prec == "fp64" else M.MHS_MIXED
     rng = np.random.default_rng(0)
     shape = (pr["nz"], pr["ny"], pr["nx"])
@@ -376,7 +387,8 @@ def run_op(args):
     for _ in range(args.steps):
         M.mhs_level_op(h, 3, 0, op, prec)
     torch.cuda.synchronize()
-    print(json.dumps({"op": args.op, "prec": args.prec, "ms_per_op_wall": (time.perf_counter() - t0) * 1e3 / args.steps}))
+    print(json.dumps({"op": args.op, "prec": args.prec, "grid": list(args.grid), "smoother": args.smoother,
+                      "tma": bool(args.tma), "ms_per_op_wall": (time.perf_counter() - t0) * 1e3 / args.steps}))
     M.mhs_destroy(h)
 
 
@@ -403,8 +415,9 @@ def _timed_solves(M, h, mode, K, bz_list, outs, stream, flush):
 
 def large_grid_leg(M, steps, with_error=True):
     """Large grids of the mixed-precision configuration: 257^3 on [0,1]^3 and 513x513x257 on
-    [0,1]^2 x [0,0.5], alpha = 0.5, xi = 0.5 exp(-z); FP64 and mixed; error of the last solve of each
-    mode against the oracle's exact discrete solution (relative L2 of Phi, B, p, rho)."""
+    [0,1]^2 x [0,0.5], alpha = 0.5, xi = 0.5 exp(-z); FP64 and mixed with V-cycles, and both with the
+    separable solver; error of the last solve of each against the oracle's exact discrete solution
+    (relative L2 of Phi, B, p, rho)."""
     import numpy as np
     import torch
     out = {}
@@ -428,7 +441,10 @@ def large_grid_leg(M, steps, with_error=True):
             P = exact.exact_solution(pr, bzs[(steps - 1) % 2])
             F = oracle.fields(pr, P)
             want = dict(F, phi=P)
-        for mname, mode in (("fp64", M.MHS_FP64), ("mixed", M.MHS_MIXED)):
+        for mname, mode, flags in (("fp64", M.MHS_FP64, 0), ("mixed", M.MHS_MIXED, 0),
+                                   ("mixed_separable", M.MHS_MIXED, M.MHS_FLAG_SEPARABLE),
+                                   ("fp64_separable", M.MHS_FP64, M.MHS_FLAG_SEPARABLE)):
+            M.mhs_set_options(h, flags=flags)
             _timed_solves(M, h, mode, 1, bz_dev, outs, stream, flush)
             ms, infos = _timed_solves(M, h, mode, steps, bz_dev, outs, stream, flush)
             e = {"value": S.unknowns(pr) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
@@ -439,6 +455,7 @@ def large_grid_leg(M, steps, with_error=True):
                                                for k in got}
             ent[mname] = e
         ent["mixed_speedup_vs_fp64"] = ent["fp64"]["ms_per_step"] / ent["mixed"]["ms_per_step"]
+        ent["mixed_separable_speedup_vs_fp64"] = ent["fp64"]["ms_per_step"] / ent["mixed_separable"]["ms_per_step"]
         out[name] = ent
         M.mhs_destroy(h)
         del outs, bz_dev
@@ -647,6 +664,10 @@ def main():
     ap.add_argument("--op", choices=["smooth", "residual", "restrict", "prolong", "vcycle"], default=None,
                     help="repeat one finest-level operation of the interior hierarchy (--steps times) for kernel capture")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="precision of --op")
+    ap.add_argument("--grid", type=int, nargs=3, default=[129, 129, 129], metavar=("NX", "NY", "NZ"),
+                    help="grid of --op")
+    ap.add_argument("--smoother", choices=["point", "zline"], default="point", help="smoother of --op smooth")
+    ap.add_argument("--tma", action="store_true", help="--op smooth in FP32: the fused TMA-staged sweep")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the large-grid, batched and serving legs")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving leg")

@@ -124,11 +124,12 @@ typedef struct {
                                    Without this flag or MHS_FLAG_POINT the smoother is chosen from the problem:
                                    z-line when the anisotropy class (see mhs_autotune) is 5 or more */
 #define MHS_FLAG_POINT 128      /* always smooth by red-black point Gauss-Seidel */
-#define MHS_FLAG_SEPARABLE 256  /* mixed mode: each outer step solves the correction equation with the exact
-                                   separable solver (FP32 sine transforms in x and y, one tridiagonal system
-                                   along z per mode; valid because xi depends on z only and the sides are
-                                   Dirichlet) instead of an FP32 V-cycle; same solution, 2-3 outer steps.
-                                   Ignored in FP64 mode; not available in groups */
+#define MHS_FLAG_SEPARABLE 256  /* solve the correction equation of each step with the exact separable solver
+                                   (sine transforms in x and y, one tridiagonal system along z per mode; valid
+                                   because xi depends on z only and the sides are Dirichlet) instead of a
+                                   V-cycle; same discrete solution.  Mixed mode: FP32 solves inside the
+                                   double-float loop, 2-3 steps.  FP64 mode: FP64 direct solves, 1-2 steps,
+                                   when nx - 1 and ny - 1 are powers of two (else V-cycles).  Not in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of

@@ -171,6 +171,7 @@ inline dim3 df_grid(const Geom& g, int d3, int max_blocks) {
     if (gz > 65535) gz = 65535;
     return dim3(gx, gy, gz);
 }
+// norm partials: a few blocks per SM, each covering several planes (see residual_grid)
 inline dim3 df_residual_grid(const Geom& g, int d3, int max_blocks) {
     return df_grid(g, d3, max_blocks < 152 * 8 ? max_blocks : 152 * 8);
 }

@@ -1,0 +1,205 @@
+// Fast discrete sine transforms (DST-I) for the separable solver.
+//
+// For a line x_1 .. x_N (N = L - 1, L a power of two) the transform
+//   X_m = sum_i x_i sin(pi m i / L),  m = 1 .. N,
+// follows from a complex FFT of length 2L of the odd extension
+//   y_0 = 0, y_i = x_i, y_L = 0, y_{2L-i} = -x_i:
+// its transform is -2i X_m.  Two real lines a and b go through one complex
+// FFT as y_a + i y_b; since each odd extension transforms to a purely
+// imaginary sequence, the result Z gives X_a = -Im(Z)/2 and X_b = Re(Z)/2.
+// The inverse of the DST-I is the same transform scaled by 2/L.
+//
+// One block handles P pairs of lines in shared memory: the extended pairs
+// are stored in bit-reversed order, then the log2(2L) radix-2
+// decimation-in-time stages (Cooley and Tukey) run three at a time in
+// registers (radix-8 passes), with twiddles e^{-2 pi i q / (2L)} from a table
+// staged in shared memory.  Lines are read contiguously; results are written either as lines
+// (element m of line l at out + l * out_line + m) or transposed (at
+// out + m * out_elem + l), in both cases with consecutive threads on
+// consecutive addresses.
+#include <cmath>
+#include <vector>
+
+#include "device_util.cuh"
+#include "mhs_internal.h"
+#include "solver.h"
+
+namespace mhs {
+
+namespace {
+
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using type = float2;
+};
+template <>
+struct Cplx<double> {
+    using type = double2;
+};
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
+
+// shared-memory position of point i of a pair: one padding element per 8
+// points, which spreads the first passes' strided accesses over the banks
+__device__ __forceinline__ int phys(int i) { return i + (i >> 3); }
+
+template <typename C>
+__device__ __forceinline__ void bfly(C& a, C& b, const C w) {
+    const C t = C{b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x};
+    b = C{a.x - t.x, a.y - t.y};
+    a = C{a.x + t.x, a.y + t.y};
+}
+
+// Q consecutive radix-2 decimation-in-time stages (half-sizes h = 2^s ..
+// 2^(s+Q-1)) in registers: each unit holds the 2^Q points base + j h that
+// those stages combine; sub-stage t pairs j with j + 2^t under the twiddle
+// e^{-2 pi i rr / (2H)}, H = h 2^t, rr = r + (j mod 2^t) h, taken from the
+// table e^{-2 pi i q / (2L)} at q = rr L / H.
+template <int Q, typename C>
+__device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int bits, int L, int s) {
+    constexpr int R = 1 << Q;
+    const int h = 1 << s, ub = bits - Q, L2p = phys(2 * L - 1) + 1;
+    const int units = P << ub;
+    for (int e = threadIdx.x; e < units; e += blockDim.x) {
+        const int pair = e >> ub, u = e & ((1 << ub) - 1);
+        const int r = u & (h - 1);
+        const int base = ((u >> s) << (Q + s)) + r;
+        C* zp = z + pair * L2p;
+        C v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = zp[phys(base + j * h)];
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            const int d = 1 << t;
+            const int tstride = L >> (s + t);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (j & d) continue;
+                const int rr = r + (j & (d - 1)) * h;
+                bfly(v[j], v[j + d], tw[rr * tstride]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) zp[phys(base + j * h)] = v[j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char dst_smem[];
+    const int L2 = 2 * a.L, N = a.L - 1, bits = a.log2n;
+    const int L2p = phys(L2 - 1) + 1;                  // padded points of a pair
+    const int P = a.pairs;
+    C* z = reinterpret_cast<C*>(dst_smem);            // P pairs x L2p points
+    C* tw = z + P * L2p;                               // twiddle table, L entries
+    const int plane = blockIdx.y;
+    const int line0 = blockIdx.x * 2 * P;             // first line of the block in its plane
+    const int nl = min(2 * P, a.lines - line0);       // lines of the block
+    const T* in = a.in + plane * a.in_plane + (long long)line0 * a.in_line;
+    const C* twg = static_cast<const C*>(a.tw);
+    for (int e = threadIdx.x; e < a.L; e += blockDim.x) tw[e] = twg[e];
+    // zero, then scatter the odd extensions into bit-reversed positions
+    for (int e = threadIdx.x; e < P * L2p; e += blockDim.x) z[e] = C{T(0), T(0)};
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+        const int l = e / N, i = 1 + e % N;           // line of the block, element 1 .. N
+        const T v = in[l * a.in_line + (i - 1)];
+        C* zp = z + (l >> 1) * L2p;
+        T* p1 = reinterpret_cast<T*>(&zp[phys(bitrev(i, bits))]) + (l & 1);
+        T* p2 = reinterpret_cast<T*>(&zp[phys(bitrev(L2 - i, bits))]) + (l & 1);
+        *p1 = v;
+        *p2 = -v;
+    }
+    __syncthreads();
+    // radix-8 passes (three stages each), the remaining one or two stages last
+    int s = 0;
+    for (; s + 3 <= bits; s += 3) {
+        fft_pass<3>(z, tw, P, bits, a.L, s);
+        __syncthreads();
+    }
+    if (bits - s == 2) {
+        fft_pass<2>(z, tw, P, bits, a.L, s);
+        __syncthreads();
+    } else if (bits - s == 1) {
+        fft_pass<1>(z, tw, P, bits, a.L, s);
+        __syncthreads();
+    }
+    // X_a = -Im(Z)/2, X_b = Re(Z)/2, m = 1 .. N, scaled
+    const T hs = T(0.5) * a.scale;
+    T* out = a.out + plane * a.out_plane;
+    if (a.out_elem == 1) {
+        for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+            const int l = e / N, m = 1 + e % N;
+            const C zm = z[(l >> 1) * L2p + phys(m)];
+            const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
+            T& o = out[(long long)(line0 + l) * a.out_line + (m - 1)];
+            o = a.accumulate ? o + v : v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+            const int l = e % nl, m = 1 + e / nl;
+            const C zm = z[(l >> 1) * L2p + phys(m)];
+            const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
+            T& o = out[(long long)(m - 1) * a.out_elem + (line0 + l)];
+            o = a.accumulate ? o + v : v;
+        }
+    }
+}
+
+}  // namespace
+
+// shared memory of a block: P pairs of 2L points with one padding element per
+// 8, and the twiddle table of L entries
+template <typename T>
+size_t dst_smem_bytes(int L, int P) {
+    const size_t padded = size_t(2 * L - 1) + ((2 * L - 1) >> 3) + 1;
+    return (size_t(P) * padded + size_t(L)) * 2 * sizeof(T);
+}
+
+template <typename T>
+int dst_pairs(int L) {
+    // up to 16 pairs per block, at most 48 KB of shared memory (several blocks per SM)
+    int p = 16;
+    while (p > 1 && dst_smem_bytes<T>(L, p) > 48 * 1024) p >>= 1;
+    return p;
+}
+
+template <typename T>
+void launch_dst(DstArgs<T> a, cudaStream_t st) {
+    a.pairs = dst_pairs<T>(a.L);
+    const size_t smem = dst_smem_bytes<T>(a.L, a.pairs);
+    static bool configured = false;   // per template instance
+    if (!configured) {
+        MHS_CUDA(cudaFuncSetAttribute(dst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        configured = true;
+    }
+    const dim3 grid((a.lines + 2 * a.pairs - 1) / (2 * a.pairs), a.planes);
+    dst_kernel<T><<<grid, 256, smem, st>>>(a);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
+// twiddles e^{-2 pi i q / (2L)}, q < L, computed in FP64
+template <typename T>
+void* make_twiddles(int L) {
+    using C = typename Cplx<T>::type;
+    std::vector<C> tw(L);
+    for (int q = 0; q < L; ++q) {
+        const double ang = -M_PI * double(q) / double(L);
+        tw[q] = C{T(std::cos(ang)), T(std::sin(ang))};
+    }
+    void* p = nullptr;
+    MHS_CUDA(cudaMalloc(&p, tw.size() * sizeof(C)));
+    MHS_CUDA(cudaMemcpy(p, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice));
+    return p;
+}
+
+template void launch_dst<float>(DstArgs<float>, cudaStream_t);
+template void launch_dst<double>(DstArgs<double>, cudaStream_t);
+template void* make_twiddles<float>(int);
+template void* make_twiddles<double>(int);
+
+}  // namespace mhs

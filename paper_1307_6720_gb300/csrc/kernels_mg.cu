@@ -70,16 +70,26 @@ __global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, Pla
     coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d), T(cx / d), T(cy / d), T(cz / d), T(0), T(0)};
 }
 
-// Elimination factors of the z-line smoother's column systems, a sequential
-// recursion over the interior planes (FP64, rounded to T at the end).
+// Elimination factors of the z-line smoother's column systems: the plane
+// coefficients in FP64 by all threads of the block (into shared memory),
+// then the pivot recursion over the interior planes by one thread; rounded
+// to T at the end.  Levels have at most 1026 planes.
 template <typename T>
 __global__ void line_coef_kernel(Geom g, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double sup = 0.0;
-    for (int k = 1; k <= g.nz - 2; ++k) {
+    __shared__ double sd[1026];
+    __shared__ double scz;
+    for (int k = threadIdx.x; k < g.nz && k < 1026; k += blockDim.x) {
         double cx, cy, cz, d;
         plane_coef(g, 3, alpha, xi, k, cx, cy, cz, d);
-        const double lm = 1.0 / (d - (k > 1 ? cz * sup : 0.0));
+        sd[k] = d;
+        if (k == 0) scz = cz;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double cz = scz;
+    double sup = 0.0;
+    for (int k = 1; k <= g.nz - 2 && k < 1026; ++k) {
+        const double lm = 1.0 / (sd[k] - (k > 1 ? cz * sup : 0.0));
         sup = cz * lm;
         coef[k].lm = T(lm);
         coef[k].lsup = T(sup);
@@ -279,7 +289,7 @@ void launch_coef(const Geom& g, int dim, double alpha, const mhs_xi_params& xi, 
     coef_kernel<T><<<(g.nz + 127) / 128, 128, 0, st>>>(g, dim, alpha, xi, coef);
     count_launches(1);
     if (dim == 3 && g.nz > 2) {
-        line_coef_kernel<T><<<1, 32, 0, st>>>(g, alpha, xi, coef);
+        line_coef_kernel<T><<<1, 256, 0, st>>>(g, alpha, xi, coef);
         count_launches(1);
     }
     MHS_CUDA(cudaGetLastError());

@@ -11,9 +11,10 @@
 //   cz (e[k-1] + e[k+1]) + D_k e[k] = rhat[k],
 //   D_k = (alpha^2 - 2 cz) + cx_k mu_x(m) + cy_k mu_y(n),
 // and the lower-boundary problem (eq. lower_bound) into a division per mode.
-// The sine transforms are dense products with the (symmetric) sine matrices,
-// done as batched FP32 GEMMs over the planes; the inverse is the same
-// product scaled by (2/(nx-1)) (2/(ny-1)).  In FP32 the solve is accurate to
+// The sine transforms are fast transforms (kernels_dst.cu) when nx - 1 and
+// ny - 1 are powers of two, else dense products with the (symmetric) sine
+// matrices done as batched FP32 GEMMs over the planes; the inverse is the
+// same transform scaled by (2/(nx-1)) (2/(ny-1)).  In FP32 the solve is accurate to
 // about 1e-6 relative, which the double-float outer loop of mixed mode then
 // corrects: each outer step cuts the error by about that factor.
 #include <cmath>
@@ -105,41 +106,120 @@ void sgemm(const GemmArgs& g, int batch, cudaStream_t st) {
 // nzi-1 standing for planes 1 .. nzi): Thomas elimination along k with the
 // mode's diagonal, the eliminated super-diagonal kept in w; t is overwritten
 // by the solution.
-__global__ void sep_thomas_kernel(int nxi, int nyi, int nzi, const PlaneCoef<float>* __restrict__ coef,
-                                  const float* __restrict__ mux, const float* __restrict__ muy, float base, float cz,
-                                  float* __restrict__ t, float* __restrict__ w) {
+// (ytrans: the fast index is the y mode, the layout [k][m][n] of the FFT path)
+template <typename T>
+__global__ void sep_thomas_kernel(int nxi, int nyi, int nzi, const PlaneCoef<T>* __restrict__ coef,
+                                  const T* __restrict__ mux, const T* __restrict__ muy, T base, T cz,
+                                  T* __restrict__ t, T* __restrict__ w, int ytrans) {
+    // U planes of right-hand sides (and, going back, of eliminated values)
+    // are loaded before the recursion consumes them, so U memory round trips
+    // overlap; the recursion itself is a chain of a few FMAs per plane
+    constexpr int U = 8;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m >= nxi) return;
     const size_t stride = size_t(nxi) * nyi;
-    float* tc = t + size_t(n) * nxi + m;
-    float* wc = w + size_t(n) * nxi + m;
-    const float ax = mux[m], ay = muy[n];
-    float cp = 0.f, dp = 0.f;
-    for (int k = 0; k < nzi; ++k) {
-        const PlaneCoef<float> c = coef[k + 1];
-        const float d = base + c.cx * ax + c.cy * ay;
-        const float piv = k ? fmaf(-cz, cp, d) : d;
-        const float inv = 1.f / piv;
-        dp = (k ? fmaf(-cz, dp, tc[k * stride]) : tc[k * stride]) * inv;
-        cp = cz * inv;
-        tc[k * stride] = dp;
-        wc[k * stride] = cp;
+    T* tc = t + size_t(n) * nxi + m;
+    T* wc = w + size_t(n) * nxi + m;
+    const T ax = mux[m], ay = muy[n];
+    T cp = T(0), dp = T(0);
+    for (int k0 = 0; k0 < nzi; k0 += U) {
+        T rhs[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 + q < nzi) rhs[q] = tc[(k0 + q) * stride];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int k = k0 + q;
+            if (k < nzi) {
+                const PlaneCoef<T> c = coef[k + 1];
+                const T d = ytrans ? base + c.cy * ax + c.cx * ay : base + c.cx * ax + c.cy * ay;
+                const T piv = k ? fma(-cz, cp, d) : d;
+                const T inv = T(1) / piv;
+                dp = (k ? fma(-cz, dp, rhs[q]) : rhs[q]) * inv;
+                cp = cz * inv;
+                tc[k * stride] = dp;
+                wc[k * stride] = cp;
+            }
+        }
     }
-    float x = dp;
-    for (int k = nzi - 2; k >= 0; --k) {
-        x = fmaf(-wc[k * stride], x, tc[k * stride]);
-        tc[k * stride] = x;
+    T x = dp;
+    for (int k0 = nzi - 2; k0 >= 0; k0 -= U) {
+        T dd[U], cc[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 - q >= 0) {
+                dd[q] = tc[(k0 - q) * stride];
+                cc[q] = wc[(k0 - q) * stride];
+            }
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 - q >= 0) {
+                x = fma(-cc[q], x, dd[q]);
+                tc[(k0 - q) * stride] = x;
+            }
     }
 }
 
 // lower-boundary plane: that = rhat / (cx mu_x(m) + cy mu_y(n))
-__global__ void sep_divide_kernel(int nxi, int nyi, float cx, float cy, const float* __restrict__ mux,
-                                  const float* __restrict__ muy, float* __restrict__ t) {
+template <typename T>
+__global__ void sep_divide_kernel(int nxi, int nyi, T cx, T cy, const T* __restrict__ mux, const T* __restrict__ muy,
+                                  T* __restrict__ t) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m >= nxi) return;
     t[size_t(n) * nxi + m] /= cx * mux[m] + cy * muy[n];
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return b;
+}
+
+// A e = f on one level through fast sine transforms (nx - 1, ny - 1 powers
+// of two): x lines of f -> t1[k][m][j] (transposed), y lines -> t2[k][m][n],
+// mode solves (t1 as scratch), inverse y -> t1[k][j][m] (transposed), inverse
+// x -> out, scaled, stored or added (accumulate).  f and out are pitched level
+// arrays (interior read / written); t2 may be the array of f.
+template <typename T>
+void sep_fft(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, const T* f, T* t1, T* t2, T* out,
+             bool accumulate, const void* twx, const void* twy, const T* mux, const T* muy) {
+    cudaStream_t st = c->stream;
+    const int nxi = g.nx - 2, nyi = g.ny - 2, nzi = dim == 3 ? g.nz - 2 : 1;
+    const long long pl = (long long)nxi * nyi;
+    const long long off = dim == 3 ? (long long)g.plane + g.px + 1 : (long long)g.px + 1;
+    const long long sA = dim == 3 ? (long long)g.plane : 0;
+    const int Lx = g.nx - 1, Ly = g.ny - 1;
+    DstArgs<T> a;
+    a.L = Lx; a.log2n = ilog2(2 * Lx); a.lines = nyi; a.planes = nzi; a.tw = twx;
+    a.in = f + off; a.in_plane = sA; a.in_line = g.px;
+    a.out = t1; a.out_plane = pl; a.out_line = 1; a.out_elem = nyi;
+    launch_dst<T>(a, st);
+    DstArgs<T> b;
+    b.L = Ly; b.log2n = ilog2(2 * Ly); b.lines = nxi; b.planes = nzi; b.tw = twy;
+    b.in = t1; b.in_plane = pl; b.in_line = nyi;
+    b.out = t2; b.out_plane = pl; b.out_line = nyi; b.out_elem = 1;
+    launch_dst<T>(b, st);
+    if (dim == 3) {
+        // diagonal base alpha^2 - 2 cz in FP64, so that it does not cancel against cx, cy
+        const double czd = 1.0 / (g.hz * g.hz);
+        sep_thomas_kernel<T><<<dim3((nyi + 127) / 128, nxi), 128, 0, st>>>(
+            nyi, nxi, nzi, coef, muy, mux, T(c->alpha * c->alpha - 2.0 * czd), T(czd), t2, t1, 1);
+    } else {
+        sep_divide_kernel<T><<<dim3((nyi + 127) / 128, nxi), 128, 0, st>>>(
+            nyi, nxi, T(1.0 / (g.hy * g.hy)), T(1.0 / (g.hx * g.hx)), muy, mux, t2);
+    }
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+    b.in = t2; b.out = t1; b.out_line = 1; b.out_elem = nxi;
+    launch_dst<T>(b, st);
+    a.in = t1; a.in_plane = pl; a.in_line = nxi;
+    a.out = out + off; a.out_plane = sA; a.out_line = g.px; a.out_elem = 1;
+    a.scale = T((2.0 / (g.nx - 1)) * (2.0 / (g.ny - 1)));
+    a.accumulate = accumulate ? 1 : 0;
+    launch_dst<T>(a, st);
 }
 
 }  // namespace
@@ -181,6 +261,12 @@ void sep_prepare(mhs_ctx* c) {
     MHS_CUDA(cudaMemcpy(c->sep.sy, sy.data(), sy.size() * sizeof(float), cudaMemcpyHostToDevice));
     MHS_CUDA(cudaMemcpy(c->sep.mux, mx.data(), mx.size() * sizeof(float), cudaMemcpyHostToDevice));
     MHS_CUDA(cudaMemcpy(c->sep.muy, my.data(), my.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (pow2(c->nx - 1) && pow2(c->ny - 1)) {
+        c->sep.twx = make_twiddles<float>(c->nx - 1);
+        c->allocations.push_back(c->sep.twx);
+        c->sep.twy = make_twiddles<float>(c->ny - 1);
+        c->allocations.push_back(c->sep.twy);
+    }
 }
 
 // e = A^{-1} f on the finest FP32 level of H (interior; e's boundary is left
@@ -197,6 +283,11 @@ void sep_solve(mhs_ctx* c, Hierarchy& H) {
     float* t2 = A.t;
     const long long off = H.dim == 3 ? (long long)g.plane + g.px + 1 : (long long)g.px + 1;
     const long long sA = H.dim == 3 ? (long long)g.plane : 0;
+    const float scale = float((2.0 / (g.nx - 1)) * (2.0 / (g.ny - 1)));
+    if (c->sep.twx) {
+        sep_fft<float>(c, g, H.dim, A.coef, A.f, t1, t2, A.u, false, c->sep.twx, c->sep.twy, c->sep.mux, c->sep.muy);
+        return;
+    }
     // along x: t1[k][j][m] = sum_i f[k][j][i] Sx[m][i]
     sgemm(GemmArgs{nyi, nxi, nxi, A.f + off, g.px, sA, c->sep.sx, nxi, 0, t1, nxi, pl, 1.f}, nzi, st);
     // along y: t2[k][n][m] = sum_j Sy[n][j] t1[k][j][m]
@@ -205,19 +296,53 @@ void sep_solve(mhs_ctx* c, Hierarchy& H) {
         // mode systems along z; base = alpha^2 - 2 cz from the FP64 coefficients
         const double hz = g.hz, czd = 1.0 / (hz * hz);
         const float base = float(c->alpha * c->alpha - 2.0 * czd);
-        sep_thomas_kernel<<<dim3((nxi + 127) / 128, nyi), 128, 0, st>>>(nxi, nyi, nzi, A.coef, c->sep.mux,
-                                                                        c->sep.muy, base, float(czd), t2, t1);
+        sep_thomas_kernel<float><<<dim3((nxi + 127) / 128, nyi), 128, 0, st>>>(nxi, nyi, nzi, A.coef, c->sep.mux,
+                                                                        c->sep.muy, base, float(czd), t2, t1, 0);
     } else {
         const float cx = float(1.0 / (g.hx * g.hx)), cy = float(1.0 / (g.hy * g.hy));
-        sep_divide_kernel<<<dim3((nxi + 127) / 128, nyi), 128, 0, st>>>(nxi, nyi, cx, cy, c->sep.mux, c->sep.muy, t2);
+        sep_divide_kernel<float><<<dim3((nxi + 127) / 128, nyi), 128, 0, st>>>(nxi, nyi, cx, cy, c->sep.mux, c->sep.muy, t2);
     }
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     // inverse along y: t1[k][j][m] = sum_n Sy[j][n] t2[k][n][m]
     sgemm(GemmArgs{nyi, nxi, nyi, c->sep.sy, nyi, 0, t2, nxi, pl, t1, nxi, pl, 1.f}, nzi, st);
     // inverse along x with the normalisation: e[k][j][i] = s sum_m t1[k][j][m] Sx[m][i]
-    const float scale = float((2.0 / (g.nx - 1)) * (2.0 / (g.ny - 1)));
     sgemm(GemmArgs{nyi, nxi, nxi, t1, nxi, pl, c->sep.sx, nxi, 0, A.u + off, g.px, sA, scale}, nzi, st);
+}
+
+bool sep_fp64_available(const mhs_ctx* c) { return pow2(c->nx - 1) && pow2(c->ny - 1); }
+
+// FP64 mode: mode eigenvalues and twiddles in FP64 (fast transforms only)
+void sep_prepare64(mhs_ctx* c) {
+    if (c->sep.mux64 || !sep_fp64_available(c)) return;
+    auto mu = [](int n) {
+        std::vector<double> v(n - 2);
+        for (int m = 1; m <= n - 2; ++m) {
+            const double s = std::sin(M_PI * m / (2.0 * (n - 1)));
+            v[m - 1] = -4.0 * s * s;
+        }
+        return v;
+    };
+    for (int axis = 0; axis < 2; ++axis) {
+        const std::vector<double> v = mu(axis == 0 ? c->nx : c->ny);
+        double* p = nullptr;
+        MHS_CUDA(cudaMalloc(&p, v.size() * sizeof(double)));
+        c->allocations.push_back(p);
+        MHS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        (axis == 0 ? c->sep.mux64 : c->sep.muy64) = p;
+    }
+    c->sep.twx64 = make_twiddles<double>(c->nx - 1);
+    c->allocations.push_back(c->sep.twx64);
+    c->sep.twy64 = make_twiddles<double>(c->ny - 1);
+    c->allocations.push_back(c->sep.twy64);
+}
+
+// FP64 mode: P += A^{-1} r on the finest level of H, r the residual of the
+// latest check (in A.r, consumed), the level's twin t as scratch
+void sep_correct64(mhs_ctx* c, Hierarchy& H) {
+    LevelArrays<double>& A = H.d[0];
+    sep_fft<double>(c, H.g[0], H.dim, A.coef, A.r, A.t, A.r, A.u, true, c->sep.twx64, c->sep.twy64, c->sep.mux64,
+                    c->sep.muy64);
 }
 
 }  // namespace mhs

@@ -187,6 +187,9 @@ inline dim3 mg_grid(const Geom& g, int d3, int xcount, int max_blocks) {
 
 // the grids the solver launches each operation with
 inline dim3 smooth_grid(const Geom& g, int d3) { return mg_grid(g, d3, (g.nx - 2 + 1) / 2, 0); }
+// with norm partials, a few blocks per SM (each then covers several planes):
+// one block per (tile, plane) was slower, every block paying a block-wide
+// reduction for 256 nodes; the fixed-order finish stays short too
 inline dim3 residual_grid(const Geom& g, int d3, bool norm, int max_blocks) {
     return mg_grid(g, d3, g.nx - 2, norm ? (max_blocks < 152 * 8 ? max_blocks : 152 * 8) : 0);
 }

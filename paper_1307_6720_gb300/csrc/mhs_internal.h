@@ -196,6 +196,9 @@ struct mhs_ctx {
     struct {
         float *sx = nullptr, *sy = nullptr;    // sine matrices of the x and y interiors (separable solver)
         float *mux = nullptr, *muy = nullptr;  // their eigenvalues -4 sin^2(pi m / (2 (n - 1)))
+        void *twx = nullptr, *twy = nullptr;   // FFT twiddles when nx - 1 and ny - 1 are powers of two
+        double *mux64 = nullptr, *muy64 = nullptr;   // FP64 copies for the FP64 direct solve
+        void *twx64 = nullptr, *twy64 = nullptr;
     } sep;
     bool have_bz = false, have_solution = false;
     bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
@@ -251,6 +254,26 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
 // ---- fused out-of-place red-black sweep (kernels_sweep.cu) ----
 template <typename T>
 void launch_sweep(const Geom& g, const PlaneCoef<T>* coef, const T* uin, const T* f, T* uout, cudaStream_t st);
+
+// ---- discrete sine transforms of lines (kernels_dst.cu) ----
+// lines of N = L - 1 elements, L a power of two: element i of line l of plane p
+// at in + p in_plane + l in_line + i; result element m at
+// out + p out_plane + l out_line + m out_elem (out_elem = 1: lines; else transposed, out_line = 1)
+template <typename T>
+struct DstArgs {
+    int L = 0, log2n = 0, lines = 0, planes = 0, pairs = 0;
+    const T* in = nullptr;
+    long long in_plane = 0, in_line = 0;
+    T* out = nullptr;
+    long long out_plane = 0, out_line = 0, out_elem = 1;
+    T scale = T(1);
+    int accumulate = 0;         // 1: out += result instead of out = result
+    const void* tw = nullptr;   // complex twiddles e^{-2 pi i q / (2L)}, q < L
+};
+template <typename T>
+void launch_dst(DstArgs<T> a, cudaStream_t st);
+template <typename T>
+void* make_twiddles(int L);
 
 // ---- zebra z-line Gauss-Seidel sweep, both colours (kernels_line.cu); scratch holds g.n elements ----
 template <typename T>

@@ -136,8 +136,9 @@ void compute_coefficients(mhs_ctx* c) {
         launch_df_coef(H->g[0], H->d[0].coef, H->df.coef, c->stream);
     }
     launch_profiles(c->h3.g[0], c->xi, c->atm, c->prof, c->stream);
+    // the smoother may follow the anisotropy class; the graph key holds the choice,
+    // so a captured solve is rebuilt only when the choice changes
     c->aniso = aniso_class(c);
-    invalidate_graphs(c);   // the smoother may follow the anisotropy class
 }
 
 void create(mhs_ctx* c) {
@@ -401,6 +402,11 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
         TimedScope t(c->timer, MHS_KT_CORRECT, double(g.interior()) * 20.0, double(g.interior()) * 8.0, c->stream,
                      H.dim == 3);
         launch_df_correct(g, H.dim, H.s[0].u, H.df.hi, H.df.lo, c->stream);
+    } else if ((c->opts.flags & MHS_FLAG_SEPARABLE) && sep_fp64_available(c)) {
+        // direct solve of the correction from the residual of the latest check
+        const double N = double(g.interior());
+        TimedScope t(c->timer, MHS_KT_SEPARABLE, N * 8.0 * 3.0, 0.0, c->stream, H.dim == 3);
+        sep_correct64(c, H);
     } else {
         vcycle<double>(c, H, 0);
     }
@@ -416,7 +422,8 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
 static void fmg_cycle(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     mhs_ctx* c = e.c;
     if (c->opts.flags & MHS_FLAG_NO_FMG) return;
-    if (e.mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_SEPARABLE)) return;   // the first step is already exact
+    if ((c->opts.flags & MHS_FLAG_SEPARABLE) && (e.mode == MHS_MIXED || sep_fp64_available(c)))
+        return;   // the first separable step already solves the correction equation
     const Geom& g = H.g[0];
     if (e.mode == MHS_MIXED) {
         MHS_CUDA(cudaMemsetAsync(H.s[0].u, 0, g.n * sizeof(float), c->stream));
@@ -581,7 +588,10 @@ static bool read_cont(mhs_ctx* c, int which) {
 // in eager mode (kernel timing enabled) the host drives the cycles.
 void solve_begin(mhs_ctx* c, double tol, int mode) {
     cudaStream_t st = c->stream;
-    if (mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_SEPARABLE)) sep_prepare(c);   // allocations: not in a capture
+    if (c->opts.flags & MHS_FLAG_SEPARABLE) {   // allocations: not inside a graph capture
+        if (mode == MHS_MIXED) sep_prepare(c);
+        else sep_prepare64(c);
+    }
     for (int q = 0; q < 2; ++q) {
         c->ctl_host[q] = SolveCtl{};
         c->ctl_host[q].tol = tol;

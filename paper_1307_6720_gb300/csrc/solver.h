@@ -62,6 +62,9 @@ void ensure_post_buffers(mhs_ctx* c);
 // separable inner solver (kernels_sep.cu)
 void sep_prepare(mhs_ctx* c);
 void sep_solve(mhs_ctx* c, Hierarchy& H);
+bool sep_fp64_available(const mhs_ctx* c);   // FP64 direct solve: nx - 1 and ny - 1 powers of two
+void sep_prepare64(mhs_ctx* c);
+void sep_correct64(mhs_ctx* c, Hierarchy& H);
 void ensure_staging(mhs_ctx* c);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)

@@ -386,14 +386,16 @@ def test_zline_solve_with_strong_vertical_coupling(M, shape, mode):
     _compare(got, _oracle(pr, bz), 1e-10 if mode == 0 else 1e-8)
 
 
-@pytest.mark.parametrize("case", ["lin129", "xi2_aniso", "paper", "strong", "small"])
-def test_separable_inner_solver_reaches_exact_solution(M, case):
-    """Mixed mode with the exact separable inner solver (sine transforms and
-    one tridiagonal system per mode, in FP32): every outer step cuts the
-    error by about the FP32 rounding level, so a few steps reach a 5e-12
-    residual (near the double-float floor of the 129 x 129 lower-boundary
-    plane), and the fields match the exact discrete solution to the FP64
-    bar."""
+@pytest.mark.parametrize("mode", [1, 0])
+@pytest.mark.parametrize("case", ["lin129", "xi2_aniso", "paper", "strong", "small", "gemm"])
+def test_separable_inner_solver_reaches_exact_solution(M, case, mode):
+    """The exact separable solver (sine transforms and one tridiagonal system
+    per mode) for the correction equation.  Mixed mode, in FP32: every outer
+    step cuts the error by about the FP32 rounding level, so a few steps
+    reach a 5e-12 residual (near the double-float floor of the 129 x 129
+    lower-boundary plane).  FP64 mode: a direct FP64 solve per step (fast
+    transforms only; the 49 x 97 x 25 grid falls back to V-cycles).  Fields
+    match the exact discrete solution to the FP64 bar."""
     if case == "lin129":
         pr, bz = S.linear_mhs(129, seed=51)
     elif case == "xi2_aniso":
@@ -407,9 +409,17 @@ def test_separable_inner_solver_reaches_exact_solution(M, case):
     elif case == "strong":
         pr = S.problem(65, 65, 65, alpha=0.5, xi_kind=1, xi_a=0.999, xi_kappa=0.5)
         bz = S.magnetogram_random(65, 65, seed=53)
-    else:
+    elif case == "small":
         pr = S.problem(5, 9, 5, Ly=2.0, alpha=0.4)
         bz = S.magnetogram_random(5, 9, 1.0, 2.0, seed=54)
-    info, got = _gpu_solve(M, pr, bz, 5e-12, M.MHS_MIXED, opts=dict(flags=M.MHS_FLAG_SEPARABLE))
-    assert info["cycles_3d"] <= 4 and info["cycles_2d"] <= 4, info
+    else:   # nx - 1 = 48, ny - 1 = 96: not powers of two, the sine transforms run as matrix products
+        pr = S.problem(49, 97, 25, Ly=2.0, Lz=0.5, alpha=0.4, xi_kind=1, xi_a=0.6, xi_kappa=1.0)
+        bz = S.magnetogram_random(49, 97, 1.0, 2.0, seed=55)
+    tol = 5e-12 if mode == 1 else 1e-13
+    info, got = _gpu_solve(M, pr, bz, tol, mode, opts=dict(flags=M.MHS_FLAG_SEPARABLE))
+    if mode == 1:
+        assert info["cycles_3d"] <= 4 and info["cycles_2d"] <= 4, info
+    elif case != "gemm":
+        # FP64 direct solves: one step leaves only rounding, a second at most
+        assert info["cycles_3d"] <= 3 and info["cycles_2d"] <= 3, info
     _compare(got, _oracle(pr, bz), 1e-10)
