@@ -131,7 +131,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             const Geom& g = H.g[l];
             const Geom& gc = H.g[l + 1];
             T* f = (fz && l == 0) ? nullptr : A.f;
-            GItem s = item(q, line ? zline_grid(g) : fat(smooth_grid(g, d3)), g, ctl);
+            GItem s = item(q, line ? zline_grid(g) : fat(smooth_grid_t<T>(g, d3)), g, ctl);
             s.coef = A.coef;
             s.p[0] = A.u;
             s.p[1] = f;
@@ -141,7 +141,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             (line ? pre_ln : pre_pt)[l].push_back(s);
             s.ia[0] = nu2;
             (line ? post_ln : post_pt)[l].push_back(s);
-            GItem r = item(q, fat(residual_grid(g, d3, false, 0)), g, ctl);
+            GItem r = item(q, fat(residual_grid_plain_t<T>(g, d3)), g, ctl);
             r.coef = A.coef;
             r.p[0] = A.u;
             r.p[1] = f;

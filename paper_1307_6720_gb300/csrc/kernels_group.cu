@@ -51,6 +51,13 @@ __global__ void g_colour_kernel(const GItem* items, int n, int colour, int sweep
     GBlock k;
     if (!locate(items, n, gate, sweep, fmg_step, k)) return;
     const GItem& it = *k.it;
+    if constexpr (sizeof(T) == 4 && D3) {
+        if (use_v4(it.g)) {   // the quad form the solo launch uses on such levels
+            colour_body_v4(it.g, static_cast<const PlaneCoef<float>*>(it.coef), static_cast<float*>(it.p[0]),
+                           static_cast<const float*>(it.p[1]), colour, k.b, k.gd);
+            return;
+        }
+    }
     colour_body<T, D3>(it.g, static_cast<const PlaneCoef<T>*>(it.coef), static_cast<T*>(it.p[0]),
                        static_cast<const T*>(it.p[1]), colour, k.b, k.gd);
 }
@@ -70,6 +77,13 @@ __global__ void g_residual_kernel(const GItem* items, int n, int fmg_step, int g
     GBlock k;
     if (!locate(items, n, gate, -1, fmg_step, k)) return;
     const GItem& it = *k.it;
+    if constexpr (sizeof(T) == 4 && D3 && !NORM) {
+        if (use_v4(it.g)) {
+            residual_body_v4(it.g, static_cast<const PlaneCoef<float>*>(it.coef), static_cast<const float*>(it.p[0]),
+                             static_cast<const float*>(it.p[1]), static_cast<float*>(it.p[2]), k.b, k.gd);
+            return;
+        }
+    }
     residual_body<T, D3, NORM>(it.g, static_cast<const PlaneCoef<T>*>(it.coef), static_cast<const T*>(it.p[0]),
                                static_cast<const T*>(it.p[1]), static_cast<T*>(it.p[2]),
                                static_cast<double*>(it.p[3]), k.b, k.gd);

@@ -148,6 +148,16 @@ __global__ void colour_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, T* 
     colour_body<T, D3>(g, coef, u, f, colour, blockIdx, gridDim);
 }
 
+__global__ void colour_v4_kernel(Geom g, const PlaneCoef<float>* __restrict__ coef, float* __restrict__ u,
+                                 const float* __restrict__ f, int colour) {
+    colour_body_v4(g, coef, u, f, colour, blockIdx, gridDim);
+}
+
+__global__ void residual_v4_kernel(Geom g, const PlaneCoef<float>* __restrict__ coef, const float* __restrict__ u,
+                                   const float* __restrict__ f, float* __restrict__ r) {
+    residual_body_v4(g, coef, u, f, r, blockIdx, gridDim);
+}
+
 template <typename T, bool D3, bool NORM>
 __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
                                 const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
@@ -315,6 +325,17 @@ void launch_fill(T* a, size_t n, T v, cudaStream_t st) {
 template <typename T>
 void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st) {
     const int d3 = dim == 3;
+    if constexpr (sizeof(T) == 4) {
+        if (d3 && use_v4(g)) {
+            const dim3 grid = quad_grid(g);
+            for (int colour = 0; colour < 2; ++colour) {
+                colour_v4_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+                count_launches(1);
+            }
+            MHS_CUDA(cudaGetLastError());
+            return;
+        }
+    }
     const dim3 grid = smooth_grid(g, d3);
     for (int colour = 0; colour < 2; ++colour) {
         if (d3) colour_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
@@ -330,6 +351,14 @@ int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u
     const int d3 = dim == 3;
     // with norm partials, few enough blocks (a multiple of the SM count) that
     // the fixed-order finish stays short; every thread then covers several planes
+    if constexpr (sizeof(T) == 4) {
+        if (d3 && !partial && use_v4(g)) {
+            residual_v4_kernel<<<quad_grid(g), dim3(BX, BY), 0, st>>>(g, coef, u, f, r);
+            count_launches(1);
+            MHS_CUDA(cudaGetLastError());
+            return int(quad_grid(g).x * quad_grid(g).y * quad_grid(g).z);
+        }
+    }
     const dim3 grid = residual_grid(g, d3, partial != nullptr, max_blocks);
     if (partial) {
         if (d3) residual_kernel<T, true, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
