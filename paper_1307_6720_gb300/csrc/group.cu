@@ -104,7 +104,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     const int L = D.L;
     std::vector<std::vector<GItem>> pre_pt(L), post_pt(L), pre_ln(L), post_ln(L), res(L), restr(L), prol(L),
         fmg_restr(L), fmg_prol(L);
-    std::vector<GItem> sub, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
+    std::vector<GItem> sub, sub8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
         res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
     std::vector<SubParams<T>> params;
     D.max_nu1 = D.max_nu2 = 0;
@@ -190,6 +190,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
         sb.ia[1] = top;
         sb.ia[2] = int(params.size());
         sb.ia[3] = cut;
+        const int rows = subcycle_rows(H.g[std::min(cut, Lq - 1)].interior());
         for (int s0 = cut; s0 < Lq; ++s0) {
             SubParams<T> p{};
             p.nlev = Lq - s0;
@@ -197,6 +198,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             p.nu1 = nu1;
             p.nu2 = nu2;
             p.line = line ? 1 : 0;
+            p.rows = rows;
             size_t off = 0, ncoef = 0;
             for (int m = 0; m < p.nlev; ++m) {
                 const Geom& gm = H.g[s0 + m];
@@ -216,7 +218,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             D.sub_smem = std::max(D.sub_smem, p.smem_bytes);
             params.push_back(p);
         }
-        sub.push_back(sb);
+        (rows == 8 ? sub8 : sub).push_back(sb);
         // ---- prologue, cycle end, epilogue ----
         const Geom& g0 = H.g[0];
         auto words = [](size_t elems, size_t bytes) { return int(elems * bytes / 4); };
@@ -352,6 +354,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     up(fmg_restr, D.fmg_restr);
     up(fmg_prol, D.fmg_prol);
     D.sub = upload(G, sub);
+    D.sub8 = upload(G, sub8);
     D.params = galloc(G, params.size() * sizeof(SubParams<T>));
     MHS_CUDA(cudaMemcpy(D.params, params.data(), params.size() * sizeof(SubParams<T>), cudaMemcpyHostToDevice));
     D.zero_u = upload(G, zero_u);
@@ -403,7 +406,8 @@ void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
         glaunch_residual<T>(D.res[l], d3, fmg_step, gate, st);
         glaunch_restrict<T>(D.restr[l], d3, fmg_step, gate, st);
     }
-    glaunch_subcycle<T>(D.sub, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, st);
+    glaunch_subcycle<T>(D.sub, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 32, st);
+    glaunch_subcycle<T>(D.sub8, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 8, st);
     for (int l = D.L - 2; l >= s; --l) {
         glaunch_prolong<T>(D.prol[l], d3, fmg_step, gate, st);
         smooth(D.post_pt, D.post_ln, l, D.max_nu2);

@@ -51,7 +51,7 @@ template <typename T>
 void glaunch_prolong(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
 template <typename T>
 void glaunch_subcycle(const GTable& t, const SubParams<T>* params, int d3, int start, int fmg_step, int gate,
-                      size_t smem, cudaStream_t st);
+                      size_t smem, int rows, cudaStream_t st);
 void glaunch_zero(const GTable& t, int gate, cudaStream_t st);
 void glaunch_lower_rhs(const GTable& t, cudaStream_t st);
 void glaunch_copy_plane(const GTable& t, cudaStream_t st);
@@ -78,7 +78,7 @@ struct GDim {
     // full multigrid: restriction of the residual and prolongation of the
     // coarse solution, per level, for the instances using it
     std::vector<GTable> fmg_restr, fmg_prol;
-    GTable sub;                                  // sub-cycle: one item per instance
+    GTable sub, sub8;                            // sub-cycle: one item per instance (32 or 8 rows of threads)
     void* params = nullptr;                      // SubParams<T>[], device
     size_t sub_smem = 0;
     // once per solve

@@ -53,7 +53,7 @@ void subcycle_prepare() {
 
 template <typename T>
 void launch_subcycle(const SubParams<T>& p, cudaStream_t st) {
-    const dim3 blk(SX, SY);
+    const dim3 blk(SX, p.rows);
     if (p.dim == 3) subcycle_kernel<T, true><<<1, blk, p.smem_bytes, st>>>(p);
     else subcycle_kernel<T, false><<<1, blk, p.smem_bytes, st>>>(p);
     count_launches(1);

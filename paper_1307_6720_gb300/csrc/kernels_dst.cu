@@ -58,15 +58,15 @@ __device__ __forceinline__ void bfly(C& a, C& b, const C w) {
 // e^{-2 pi i rr / (2H)}, H = h 2^t, rr = r + (j mod 2^t) h, taken from the
 // table e^{-2 pi i q / (2L)} at q = rr L / H.
 template <int Q, typename C>
-__device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int bits, int L, int s) {
+__device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int PS, int bits, int L, int s) {
     constexpr int R = 1 << Q;
-    const int h = 1 << s, ub = bits - Q, L2p = phys(2 * L - 1) + 1;
+    const int h = 1 << s, ub = bits - Q;
     const int units = P << ub;
     for (int e = threadIdx.x; e < units; e += blockDim.x) {
         const int pair = e >> ub, u = e & ((1 << ub) - 1);
         const int r = u & (h - 1);
         const int base = ((u >> s) << (Q + s)) + r;
-        C* zp = z + pair * L2p;
+        C* zp = z + pair * PS;
         C v[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) v[j] = zp[phys(base + j * h)];
@@ -86,65 +86,85 @@ __device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int bits, int
     }
 }
 
+// complex elements between the pairs of a block: the padded 2L points, made
+// odd so that consecutive pairs start on different banks (the output gather
+// reads one element of every pair in a warp)
+__host__ __device__ inline int pair_stride(int L) {
+    const int padded = (2 * L - 1) + ((2 * L - 1) >> 3) + 1;
+    return padded | 1;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char dst_smem[];
     const int L2 = 2 * a.L, N = a.L - 1, bits = a.log2n;
-    const int L2p = phys(L2 - 1) + 1;                  // padded points of a pair
+    const int PS = pair_stride(a.L);
     const int P = a.pairs;
-    C* z = reinterpret_cast<C*>(dst_smem);            // P pairs x L2p points
-    C* tw = z + P * L2p;                               // twiddle table, L entries
+    C* z = reinterpret_cast<C*>(dst_smem);            // P pairs, PS points apart
+    C* tw = z + P * PS;                                // twiddle table, L entries
     const int plane = blockIdx.y;
     const int line0 = blockIdx.x * 2 * P;             // first line of the block in its plane
     const int nl = min(2 * P, a.lines - line0);       // lines of the block
     const T* in = a.in + plane * a.in_plane + (long long)line0 * a.in_line;
     const C* twg = static_cast<const C*>(a.tw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < a.L; e += blockDim.x) tw[e] = twg[e];
-    // zero, then scatter the odd extensions into bit-reversed positions
-    for (int e = threadIdx.x; e < P * L2p; e += blockDim.x) z[e] = C{T(0), T(0)};
+    // positions 0 and L (bit-reversed: 0 and 1) of every pair are zero; a pair
+    // with one line has a zero imaginary part everywhere
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        z[p * PS + phys(0)] = C{T(0), T(0)};
+        z[p * PS + phys(1)] = C{T(0), T(0)};
+    }
+    if (nl & 1)
+        for (int e = threadIdx.x; e < L2; e += blockDim.x) reinterpret_cast<T*>(&z[(nl >> 1) * PS + phys(e)])[1] = T(0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-        const int l = e / N, i = 1 + e % N;           // line of the block, element 1 .. N
-        const T v = in[l * a.in_line + (i - 1)];
-        C* zp = z + (l >> 1) * L2p;
-        T* p1 = reinterpret_cast<T*>(&zp[phys(bitrev(i, bits))]) + (l & 1);
-        T* p2 = reinterpret_cast<T*>(&zp[phys(bitrev(L2 - i, bits))]) + (l & 1);
-        *p1 = v;
-        *p2 = -v;
+    // scatter the odd extensions into bit-reversed positions (a warp per line)
+    for (int l = warp; l < nl; l += nwarps) {
+        C* zp = z + (l >> 1) * PS;
+        const T* src = in + (long long)l * a.in_line;
+        for (int i = 1 + lane; i <= N; i += 32) {
+            const T v = src[i - 1];
+            reinterpret_cast<T*>(&zp[phys(bitrev(i, bits))])[l & 1] = v;
+            reinterpret_cast<T*>(&zp[phys(bitrev(L2 - i, bits))])[l & 1] = -v;
+        }
     }
     __syncthreads();
     // radix-8 passes (three stages each), the remaining one or two stages last
     int s = 0;
     for (; s + 3 <= bits; s += 3) {
-        fft_pass<3>(z, tw, P, bits, a.L, s);
+        fft_pass<3>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     }
     if (bits - s == 2) {
-        fft_pass<2>(z, tw, P, bits, a.L, s);
+        fft_pass<2>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     } else if (bits - s == 1) {
-        fft_pass<1>(z, tw, P, bits, a.L, s);
+        fft_pass<1>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     }
     // X_a = -Im(Z)/2, X_b = Re(Z)/2, m = 1 .. N, scaled
     const T hs = T(0.5) * a.scale;
     T* out = a.out + plane * a.out_plane;
     if (a.out_elem == 1) {
-        for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-            const int l = e / N, m = 1 + e % N;
-            const C zm = z[(l >> 1) * L2p + phys(m)];
-            const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
-            T& o = out[(long long)(line0 + l) * a.out_line + (m - 1)];
-            o = a.accumulate ? o + v : v;
+        for (int l = warp; l < nl; l += nwarps) {
+            const C* zp = z + (l >> 1) * PS;
+            T* dst = out + (long long)(line0 + l) * a.out_line;
+            for (int m = 1 + lane; m <= N; m += 32) {
+                const C zm = zp[phys(m)];
+                const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
+                dst[m - 1] = a.accumulate ? dst[m - 1] + v : v;
+            }
         }
     } else {
-        for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-            const int l = e % nl, m = 1 + e / nl;
-            const C zm = z[(l >> 1) * L2p + phys(m)];
-            const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
-            T& o = out[(long long)(m - 1) * a.out_elem + (line0 + l)];
-            o = a.accumulate ? o + v : v;
+        // transposed: a warp per mode, consecutive lanes on consecutive lines
+        for (int m = 1 + warp; m <= N; m += nwarps) {
+            T* dst = out + (long long)(m - 1) * a.out_elem + line0;
+            for (int l = lane; l < nl; l += 32) {
+                const C zm = z[(l >> 1) * PS + phys(m)];
+                const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
+                dst[l] = a.accumulate ? dst[l] + v : v;
+            }
         }
     }
 }
@@ -155,15 +175,16 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
 // 8, and the twiddle table of L entries
 template <typename T>
 size_t dst_smem_bytes(int L, int P) {
-    const size_t padded = size_t(2 * L - 1) + ((2 * L - 1) >> 3) + 1;
-    return (size_t(P) * padded + size_t(L)) * 2 * sizeof(T);
+    return (size_t(P) * size_t(pair_stride(L)) + size_t(L)) * 2 * sizeof(T);
 }
 
 template <typename T>
 int dst_pairs(int L) {
-    // up to 16 pairs per block, at most 48 KB of shared memory (several blocks per SM)
+    // up to 16 pairs per block within 48 KB of shared memory (several blocks per
+    // SM), but at least 4 pairs (up to 96 KB) where that budget would leave fewer
     int p = 16;
-    while (p > 1 && dst_smem_bytes<T>(L, p) > 48 * 1024) p >>= 1;
+    while (p > 4 && dst_smem_bytes<T>(L, p) > 48 * 1024) p >>= 1;
+    while (p > 1 && dst_smem_bytes<T>(L, p) > 96 * 1024) p >>= 1;
     return p;
 }
 

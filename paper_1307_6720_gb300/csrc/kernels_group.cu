@@ -222,7 +222,7 @@ inline void after_launch() {
     MHS_CUDA(cudaGetLastError());
 }
 
-const dim3 kMG(MG_BX, MG_BY), kDF(DF_BX, DF_BY), kLine(LX, LY), kSub(SX, SY);
+const dim3 kMG(MG_BX, MG_BY), kDF(DF_BX, DF_BY), kLine(LX, LY);
 
 }  // namespace
 
@@ -275,10 +275,11 @@ void glaunch_prolong(const GTable& t, int d3, int fmg_step, int gate, cudaStream
 
 template <typename T>
 void glaunch_subcycle(const GTable& t, const SubParams<T>* params, int d3, int start, int fmg_step, int gate,
-                      size_t smem, cudaStream_t st) {
+                      size_t smem, int rows, cudaStream_t st) {
     if (!t.n) return;
-    if (d3) g_subcycle_kernel<T, true><<<t.blocks, kSub, smem, st>>>(t.items, t.n, params, start, fmg_step, gate);
-    else g_subcycle_kernel<T, false><<<t.blocks, kSub, smem, st>>>(t.items, t.n, params, start, fmg_step, gate);
+    const dim3 blk(SX, rows);
+    if (d3) g_subcycle_kernel<T, true><<<t.blocks, blk, smem, st>>>(t.items, t.n, params, start, fmg_step, gate);
+    else g_subcycle_kernel<T, false><<<t.blocks, blk, smem, st>>>(t.items, t.n, params, start, fmg_step, gate);
     after_launch();
 }
 
@@ -376,7 +377,7 @@ void glaunch_gather_ctl(SolveCtl* const* ctls, int n, SolveCtl* out, cudaStream_
     template void glaunch_residual_norm<T>(const GTable&, int, int, cudaStream_t);                            \
     template void glaunch_restrict<T>(const GTable&, int, int, int, cudaStream_t);                            \
     template void glaunch_prolong<T>(const GTable&, int, int, int, cudaStream_t);                             \
-    template void glaunch_subcycle<T>(const GTable&, const SubParams<T>*, int, int, int, int, size_t, cudaStream_t);
+    template void glaunch_subcycle<T>(const GTable&, const SubParams<T>*, int, int, int, int, size_t, int, cudaStream_t);
 MHS_GINST(double)
 MHS_GINST(float)
 #undef MHS_GINST

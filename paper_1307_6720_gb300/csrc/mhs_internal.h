@@ -122,6 +122,7 @@ constexpr int MAX_SUB_LEVELS = 12;
 template <typename T>
 struct SubParams {
     int nlev, dim, nu1, nu2;
+    int rows;            // the CTA is 32 x rows threads (8 for small sub-hierarchies, 32 otherwise)
     int line;            // 1: zebra z-line smoothing on 3D levels, 0: red-black point smoothing
     SubLevel<T> L[MAX_SUB_LEVELS];
     T* u_g;              // iterate of the top level in global memory (in/out)
@@ -296,6 +297,10 @@ void launch_bnorm(const double* partial, int n, SolveCtl* ctl, cudaStream_t st);
 void launch_check(const double* partial, int n, SolveCtl* ctl, int first, cudaGraphConditionalHandle handle,
                   int use_handle, cudaStream_t st);
 size_t subcycle_smem_limit();
+// rows of 32 threads of the sub-cycle CTA of a hierarchy cut at a level with
+// `interior` interior nodes: small coarse problems pay mostly for block-wide
+// barriers, which are cheaper with fewer warps
+inline int subcycle_rows(size_t interior) { return interior <= 2048 ? 8 : 32; }
 void subcycle_prepare();
 template <typename T>
 void launch_subcycle(const SubParams<T>& p, cudaStream_t st);

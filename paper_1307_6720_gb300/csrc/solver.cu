@@ -210,6 +210,9 @@ void subcycle(mhs_ctx* c, Hierarchy& H, int l) {
     p.nu1 = c->opts.nu1;
     p.nu2 = c->opts.nu2;
     p.line = H.dim == 3 && use_zline(c) ? 1 : 0;
+    // thread count from the cut-off level (not from l), so that every entry
+    // into this hierarchy's sub-cycle uses the same CTA shape
+    p.rows = subcycle_rows(H.g[std::min(cut_of<T>(H), H.nlev() - 1)].interior());
     size_t off = 0;
     for (int m = 0; m < p.nlev; ++m) {
         const Geom& g = H.g[l + m];

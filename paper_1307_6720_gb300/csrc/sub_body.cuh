@@ -66,7 +66,7 @@ __device__ __forceinline__ int check_body(const double* __restrict__ partial, in
 // one-CTA sub-cycle
 // ---------------------------------------------------------------------------
 //
-// Threads are arranged as SX x SY (x fastest).  Every phase walks the rows
+// Threads are arranged as SX x rows (x fastest; rows = blockDim.y, 8 or 32).  Every phase walks the rows
 // (j, k) of a level with threadIdx.y and the x positions with threadIdx.x,
 // so index decoding costs one division per row, and reads only shared
 // memory: the levels' arrays, geometry and per-plane coefficients are
@@ -113,7 +113,7 @@ __device__ void sub_smooth(const SubSmem<T, D3>& S, int l) {
     const int nw = g.hx * g.nyi * (D3 ? g.nz - 2 : 1);
     const int tid = threadIdx.x + SX * threadIdx.y;
     for (int colour = 0; colour < 2; ++colour) {
-        for (int q = tid; q < nw; q += SX * SY) {
+        for (int q = tid; q < nw; q += SX * blockDim.y) {
             const int row = fdiv(q, g.inv_hx);
             const int t = q - row * g.hx;
             const int kk = D3 ? fdiv(row, g.inv_nyi) : 0;
@@ -142,7 +142,7 @@ __device__ void sub_zline(const SubSmem<T, true>& S, int l) {
     const int ncol = g.hx * g.nyi, nzi = g.nz - 2;
     const int tid = threadIdx.x + SX * threadIdx.y;
     for (int colour = 0; colour < 2; ++colour) {
-        for (int q = tid; q < ncol; q += SX * SY) {
+        for (int q = tid; q < ncol; q += SX * blockDim.y) {
             const int jj = fdiv(q, g.inv_hx);
             const int t = q - jj * g.hx;
             const int j = 1 + jj;
@@ -191,7 +191,7 @@ __device__ void sub_restrict_residual(const SubSmem<T, D3>& S, int l) {
     T* uc = S.a + gc.off_u;
     const PlaneCoef<T>* cf = S.c + gf.off_c;
     const int nw = gc.nxi * gc.nyi * (D3 ? gc.nz - 2 : 1);
-    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * SY) {
+    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * blockDim.y) {
         const int row = fdiv(q, gc.inv_nxi);
         const int I = 1 + q - row * gc.nxi;
         const int KK = D3 ? fdiv(row, gc.inv_nyi) : 0;
@@ -228,7 +228,7 @@ __device__ void sub_prolong(const SubSmem<T, D3>& S, int l) {
     T* uf = S.a + gf.off_u;
     const T* uc = S.a + gc.off_u;
     const int nw = gf.nxi * gf.nyi * (D3 ? gf.nz - 2 : 1);
-    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * SY) {
+    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * blockDim.y) {
         const int row = fdiv(q, gf.inv_nxi);
         const int i = 1 + q - row * gf.nxi;
         const int kk = D3 ? fdiv(row, gf.inv_nyi) : 0;
@@ -258,7 +258,7 @@ __device__ double sub_norm2(const SubSmem<T, D3>& S, int l, bool res) {
     const PlaneCoef<T>* cf = S.c + g.off_c;
     const int nw = g.nxi * g.nyi * (D3 ? g.nz - 2 : 1);
     double a = 0.0;
-    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * SY) {
+    for (int q = threadIdx.x + SX * threadIdx.y; q < nw; q += SX * blockDim.y) {
         const int row = fdiv(q, g.inv_nxi);
         const int i = 1 + q - row * g.nxi;
         const int kk = D3 ? fdiv(row, g.inv_nyi) : 0;
@@ -308,7 +308,7 @@ template <typename T, bool D3>
 __device__ __forceinline__ void subcycle_body(const SubParams<T>& p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SubGeom sg[MAX_SUB_LEVELS];
-    const int tid = threadIdx.x + SX * threadIdx.y, nt = SX * SY;
+    const int tid = threadIdx.x + SX * threadIdx.y, nt = SX * blockDim.y;
     // layout: [coefficients of all levels][level arrays]
     PlaneCoef<T>* sc = reinterpret_cast<PlaneCoef<T>*>(smem_raw);
     int ncoef = 0;
