@@ -109,6 +109,13 @@ typedef struct {
     int fused_min;       /* FP32 3D levels with at least this many interior nodes use the fused, TMA-staged
                             red-black sweep (one pass per sweep, HBM-bound); smaller, cache-resident levels use the
                             two colour passes, which have less latency [32000000] */
+    int sep_coarse;      /* coarse-grid solve of the V-cycles: the first level below the finest with at most this
+                            many interior nodes, whose sine transforms are fast (nx - 1 and ny - 1 powers of two)
+                            or short (nx, ny <= 66), is solved exactly by the separable solver (sine transforms
+                            in x and y, one tridiagonal system along z per mode) in the cycle's precision, and
+                            the levels below it are never visited; the one-CTA sub-cycle handles the coarse end
+                            when no level qualifies or when the sub-cycle cut-off lies above it.  -1: never
+                            [300000] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
@@ -129,7 +136,8 @@ typedef struct {
                                    because xi depends on z only and the sides are Dirichlet) instead of a
                                    V-cycle; same discrete solution.  Mixed mode: FP32 solves inside the
                                    double-float loop, 2-3 steps.  FP64 mode: FP64 direct solves, 1-2 steps,
-                                   when nx - 1 and ny - 1 are powers of two (else V-cycles).  Not in groups */
+                                   when nx - 1 and ny - 1 are powers of two or nx, ny <= 66 (else V-cycles).
+                                   Not in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
@@ -207,9 +215,11 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * and the whole solve (lower-boundary and interior problems, both with the
  * full-multigrid first cycle and V-cycles until each instance reaches the
  * tolerance) is one captured CUDA graph whose loops run while any instance
- * still iterates; converged instances drop out of the launches.  Each
- * instance runs the operations of its solo mhs_solve with the same block
- * decomposition, so its P is bitwise identical to solving it alone.
+ * still iterates; converged instances drop out of the launches.  A group's
+ * V-cycles end in the one-CTA sub-cycle (the separable coarse-grid solve,
+ * sep_coarse, is not used); otherwise each instance runs the operations of
+ * its solo mhs_solve with the same block decomposition, so its P is bitwise
+ * identical to solving it alone with sep_coarse = -1.
  *
  * The instances, ordered by decreasing cycle working set (every level's
  * arrays in the cycle precision, plus the double-float state in mixed
@@ -249,8 +259,10 @@ MHS_API mhs_status mhs_group_set_eager(mhs_group_t g, int eager);
  * solves of its resident B_z to tol in the given mode (CUDA events, the
  * captured-graph path).  Coordinate descent from h's current options over
  * the smoother (red-black point or zebra z-line, MHS_FLAG_ZLINE), the sweep
- * counts (nu1, nu2), the sub-cycle cut-off (cut64 in FP64 mode, cut32 in
- * mixed mode; one candidate per level), the fused-sweep threshold of FP32
+ * counts (nu1, nu2), the level of the separable coarse-grid solve
+ * (sep_coarse: every level that allows it, or none), the sub-cycle cut-off
+ * (cut64 in FP64 mode, cut32 in mixed mode; one candidate per level), the
+ * fused-sweep threshold of FP32
  * levels (fused_min, mixed mode) and the full-multigrid first cycle
  * (MHS_FLAG_NO_FMG); at most two rounds, a change kept when it saves at
  * least 3 %.  Each candidate costs one untimed solve (graph capture) plus
@@ -396,6 +408,10 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
  *   MHS_OP_PROLONG:  u[level] += (bi/tri)linear interpolation of u[level+1] (Sect. 4)
  *   MHS_OP_COARSE:   coarsest-level solve of A u = f (u from 0)
  *   MHS_OP_VCYCLE:   one V(nu1,nu2)-cycle on A u = f from level down
+ *   MHS_OP_EXACT:    u = A^{-1} f on the interior by the separable solver
+ *                    (zero boundary values; the level's r and t are
+ *                    scratch); levels whose sine transforms are fast
+ *                    or short (see sep_coarse), else MHS_ERR_INVALID_ARG
  * For the finest interior level, A includes the Dirichlet data held in u's
  * boundary entries.  Errors: MHS_ERR_INVALID_ARG, MHS_ERR_CUDA. */
 #define MHS_FIELD_U 0
@@ -407,6 +423,7 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
 #define MHS_OP_PROLONG 3
 #define MHS_OP_COARSE 4
 #define MHS_OP_VCYCLE 5
+#define MHS_OP_EXACT 6
 MHS_API mhs_status mhs_level_write(mhs_handle h, int dim, int level, int field, int prec, const double* src);
 MHS_API mhs_status mhs_level_read(mhs_handle h, int dim, int level, int field, int prec, double* dst);
 MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec);

@@ -90,6 +90,8 @@ def _load():
                                       ctypes.c_int, ctypes.c_int]),
                 "orc_vcycle_s": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "orc_vcycle_x": (None, [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_fields": (None, [_PP, _D, _D, _D, _D, _D, _D, ctypes.c_int]),
                 "orc_profiles": (None, [_PP, _D, _D, _D, _D, _D]),
                 "orc_current": (None, [_PP, _D, _D, _D, _D, _D, _D, _D, _D]),
@@ -276,17 +278,21 @@ def solve(pr, bz, tol2d=1e-12, tol3d=1e-12, max_cycles=200, nu1=2, nu2=2, smooth
                    conv_factor_3d=info.conv_factor_3d)
 
 
-def vcycle(pr, u, f=None, nu1=2, nu2=2, smoother="point"):
-    """One V-cycle on the grid of u (2D [ny][nx] or 3D [nz][ny][nx]); returns the new u."""
+def vcycle(pr, u, f=None, nu1=2, nu2=2, smoother="point", exact_level=-1):
+    """One V-cycle on the grid of u (2D [ny][nx] or 3D [nz][ny][nx]); returns the new u.
+
+    exact_level >= 1: the cycle stops at that level and solves its
+    coarse-grid system to rounding (the coarse-grid solve of multigrid
+    theory) instead of descending further."""
     u = _f64(u).copy(); f = _f64(f)
     p = _prob(pr)
     sm = SMOOTHERS[smoother]
     if u.ndim == 2:
         ny, nx = u.shape
-        _load().orc_vcycle_s(ctypes.byref(p), 2, nx, ny, 1, _ptr(u), _ptr(f), nu1, nu2, sm)
+        _load().orc_vcycle_x(ctypes.byref(p), 2, nx, ny, 1, _ptr(u), _ptr(f), nu1, nu2, sm, exact_level)
     else:
         nz, ny, nx = u.shape
-        _load().orc_vcycle_s(ctypes.byref(p), 3, nx, ny, nz, _ptr(u), _ptr(f), nu1, nu2, sm)
+        _load().orc_vcycle_x(ctypes.byref(p), 3, nx, ny, nz, _ptr(u), _ptr(f), nu1, nu2, sm, exact_level)
     return u
 
 

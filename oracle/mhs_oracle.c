@@ -379,6 +379,7 @@ typedef struct {
     double* f[ORC_MAX_LEVELS];
     double* r[ORC_MAX_LEVELS];
     int smoother; /* 0: red-black point Gauss-Seidel; 1: zebra z-line Gauss-Seidel (3D levels) */
+    int exact_level; /* level whose system a V-cycle solves to rounding instead of descending (-1: none) */
 } orc_mg;
 
 static int coarsenable(int n) { return n >= 5 && ((n - 1) % 2) == 0; }
@@ -388,6 +389,7 @@ static void mg_build(orc_mg* mg, const orc_problem* p, int dim) {
     mg->dim = dim;
     mg->nlev = 0;
     mg->smoother = 0;
+    mg->exact_level = -1;
     for (;;) {
         orc_level* L = &mg->L[mg->nlev];
         if (dim == 3) level_init3d(L, p, nx, ny, nz); else level_init2d(L, p, nx, ny);
@@ -439,8 +441,30 @@ static void coarse_solve(orc_mg* mg, int l, double* u, const double* f) {
     }
 }
 
+static void vcycle(orc_mg* mg, int l, double* u, const double* f, int nu1, int nu2);
+
+/* Coarse-grid correction solved exactly: the level's system A u = f (zero
+ * boundary values) iterated to rounding by V-cycles over the coarser levels,
+ * until the residual stops falling or is 1e-15 of ||f||.  Any method that
+ * reaches the exact solution of the coarse system serves here. */
+static void exact_solve(orc_mg* mg, int l, double* u, const double* f, int nu1, int nu2) {
+    const int saved = mg->exact_level;
+    mg->exact_level = -1;
+    const double fn = mg_norm(mg, l, f);
+    double prev = INFINITY;
+    for (int it = 0; it < 200; ++it) {
+        mg_residual(mg, l, u, f, mg->r[l]);
+        const double rn = mg_norm(mg, l, mg->r[l]);
+        if (rn <= 1e-15 * fn || rn > 0.5 * prev) break;
+        prev = rn;
+        vcycle(mg, l, u, f, nu1, nu2);
+    }
+    mg->exact_level = saved;
+}
+
 static void vcycle(orc_mg* mg, int l, double* u, const double* f, int nu1, int nu2) {
     if (l == mg->nlev - 1) { coarse_solve(mg, l, u, f); return; }
+    if (l == mg->exact_level) { exact_solve(mg, l, u, f, nu1, nu2); return; }
     for (int s = 0; s < nu1; ++s) mg_smooth(mg, l, u, f);
     mg_residual(mg, l, u, f, mg->r[l]);
     if (mg->dim == 3) restrict3d(&mg->L[l], mg->r[l], &mg->L[l + 1], mg->f[l + 1]);
@@ -778,20 +802,28 @@ void orc_profiles(const orc_problem* p, double* xi, double* dxi, double* pb, dou
 }
 
 /* One V(nu1,nu2)-cycle for A u = f on the grid of u (dim 3: nx*ny*nz,
- * dim 2: nx*ny), from that grid down to the coarsest level.  u is updated
- * in place; its boundary entries are the Dirichlet data. */
-void orc_vcycle_s(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
-                  int nu2, int smoother) {
+ * dim 2: nx*ny), from that grid down to the coarsest level, or, with
+ * exact_level >= 1, down to that level, whose coarse-grid system is solved
+ * to rounding.  u is updated in place; its boundary entries are the
+ * Dirichlet data. */
+void orc_vcycle_x(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
+                  int nu2, int smoother, int exact_level) {
     orc_problem q = with_size(p, nx, ny, dim == 3 ? nz : 1);
     orc_mg mg;
     mg_build(&mg, &q, dim);
     mg.smoother = smoother;
+    mg.exact_level = exact_level >= 1 ? exact_level : -1;
     const size_t n = level_size(&mg.L[0]);
     double* fz = NULL;
     if (!f) fz = (double*)calloc(n, sizeof(double));
     vcycle(&mg, 0, u, f ? f : fz, nu1, nu2);
     free(fz);
     mg_free(&mg);
+}
+
+void orc_vcycle_s(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,
+                  int nu2, int smoother) {
+    orc_vcycle_x(p, dim, nx, ny, nz, u, f, nu1, nu2, smoother, -1);
 }
 
 void orc_vcycle(const orc_problem* p, int dim, int nx, int ny, int nz, double* u, const double* f, int nu1,

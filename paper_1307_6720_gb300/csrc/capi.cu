@@ -51,7 +51,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 32000000}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 32000000, 300000}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -63,6 +63,7 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->cut64 > 0) o->cut64 = in->cut64;
     if (in->cut32 > 0) o->cut32 = in->cut32;
     if (in->fused_min > 0) o->fused_min = in->fused_min;
+    if (in->sep_coarse != 0) o->sep_coarse = in->sep_coarse < 0 ? -1 : in->sep_coarse;
     o->flags = in->flags;
 }
 
@@ -551,7 +552,9 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
     mhs::Hierarchy& H = dim == 3 ? h->h3 : h->h2;
     if ((op == MHS_OP_RESTRICT || op == MHS_OP_PROLONG) && level >= H.nlev() - 1)
         return fail(MHS_ERR_INVALID_ARG, "no coarser level");
-    if (op < MHS_OP_SMOOTH || op > MHS_OP_VCYCLE) return fail(MHS_ERR_INVALID_ARG, "unknown op");
+    if (op < MHS_OP_SMOOTH || op > MHS_OP_EXACT) return fail(MHS_ERR_INVALID_ARG, "unknown op");
+    if (op == MHS_OP_EXACT && !mhs::sep_level_ok(H.g[level]))
+        return fail(MHS_ERR_INVALID_ARG, "exact solve needs nx - 1 and ny - 1 powers of two, or nx, ny <= 66");
     return guarded([&] {
         const mhs::Geom& g = H.g[level];
         cudaStream_t st = h->stream;
@@ -570,6 +573,10 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
                 mhs::launch_coarse<T>(g, dim, A.coef, A.u, A.f, st);
                 break;
             case MHS_OP_VCYCLE: mhs::vcycle<T>(h, H, level); break;
+            case MHS_OP_EXACT:
+                mhs::sep_tables<T>(h, H, level);
+                mhs::sep_exact<T>(h, H, level);
+                break;
             }
         };
         const int lc = level + 1 < H.nlev() ? level + 1 : level;

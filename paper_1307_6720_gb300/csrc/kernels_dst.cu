@@ -181,20 +181,26 @@ size_t dst_smem_bytes(int L, int P) {
 template <typename T>
 int dst_pairs(int L) {
     // up to 16 pairs per block within 48 KB of shared memory (several blocks per
-    // SM), but at least 4 pairs (up to 96 KB) where that budget would leave fewer
+    // SM), but at least 4 pairs (up to 96 KB) where that budget would leave
+    // fewer, and fewer pairs only for lines that need it
     int p = 16;
     while (p > 4 && dst_smem_bytes<T>(L, p) > 48 * 1024) p >>= 1;
     while (p > 1 && dst_smem_bytes<T>(L, p) > 96 * 1024) p >>= 1;
     return p;
 }
 
+// opt-in shared memory per block of the GPU (227 KB); one pair of the
+// longest lines (L = 4096, FP64) takes 213 KB
+constexpr size_t DST_SMEM_MAX = 227 * 1024;
+
 template <typename T>
 void launch_dst(DstArgs<T> a, cudaStream_t st) {
     a.pairs = dst_pairs<T>(a.L);
     const size_t smem = dst_smem_bytes<T>(a.L, a.pairs);
+    if (smem > DST_SMEM_MAX) throw Error(MHS_ERR_INVALID_ARG, "sine transform lines too long for shared memory");
     static bool configured = false;   // per template instance
     if (!configured) {
-        MHS_CUDA(cudaFuncSetAttribute(dst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        MHS_CUDA(cudaFuncSetAttribute(dst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(DST_SMEM_MAX)));
         configured = true;
     }
     const dim3 grid((a.lines + 2 * a.pairs - 1) / (2 * a.pairs), a.planes);

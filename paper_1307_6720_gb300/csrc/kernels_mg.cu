@@ -67,7 +67,8 @@ __global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, Pla
     if (k >= g.nz) return;
     double cx, cy, cz, d;
     plane_coef(g, dim, alpha, xi, k, cx, cy, cz, d);
-    coef[k] = PlaneCoef<T>{T(cx), T(cy), T(cz), T(d), T(1.0 / d), T(cx / d), T(cy / d), T(cz / d), T(0), T(0)};
+    coef[k] = PlaneCoef<T>{T(cx),     T(cy),     T(cz),     T(d), T(1.0 / d), T(cx / d),
+                           T(cy / d), T(cz / d), T(0),      T(0), T(alpha * alpha - 2.0 * cz)};
 }
 
 // Elimination factors of the z-line smoother's column systems: the plane

@@ -44,6 +44,10 @@ struct PlaneCoef {
     // the z-line smoother (the same for every column of the level):
     // lm = 1 / pivot_k, lsup = cz * lm, pivot_1 = d_1, pivot_k = d_k - cz lsup_{k-1}
     T lm, lsup;
+    // alpha^2 - 2 cz, formed in FP64 before rounding: the part of the diagonal
+    // that the separable solver's mode systems keep after the horizontal terms
+    // are diagonalised (it would cancel against them if taken from d)
+    T base;
 };
 
 // Geometry of one level.  Device arrays are pitched: element (i,j,k) at
@@ -84,12 +88,26 @@ struct DFState {
     PlaneCoefDF* coef = nullptr;
 };
 
+// Tables of the separable solver on one level (device, owned by the
+// context's allocation list): the mode eigenvalues -4 sin^2(pi m / (2 (n - 1)))
+// of the x and y second differences, and either the FFT twiddles (nx - 1 and
+// ny - 1 powers of two) or the dense sine matrices (short rows).  Element
+// type: double for sep64, float for sep32.
+struct SepTables {
+    void *mux = nullptr, *muy = nullptr;
+    void *twx = nullptr, *twy = nullptr;
+    void *sx = nullptr, *sy = nullptr;
+    bool ready = false;
+};
+
 struct Hierarchy {
     int dim = 3;                          // 3: interior, 2: lower boundary plane
     std::vector<Geom> g;                  // level geometries, 0 = finest
     std::vector<LevelArrays<double>> d;   // FP64 arrays
     std::vector<LevelArrays<float>> s;    // FP32 arrays
     int cut64 = 0, cut32 = 0;             // first level handled by the one-CTA sub-cycle (per precision)
+    int exact = -1;                       // level solved exactly by the separable solver in V-cycles (-1: none)
+    std::vector<SepTables> sep64, sep32;  // separable-solver tables per level (built on demand)
     DFState df;                           // finest-level double-float state (mixed mode)
     // TMA plane maps of the FP32 arrays u, t, f per level (3D levels; see kernels_tma.cu)
     std::vector<CUtensorMap> tm_u, tm_t, tm_f;
@@ -194,13 +212,6 @@ struct mhs_ctx {
     double* staging = nullptr;     // FP64 staging buffer of the finest size (level hooks, lazily allocated)
     double* fld[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // pitched Bx, By, Bz, p, rho
     double* post[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}; // pitched jx, jy, jz, |j|, |B| (on first use)
-    struct {
-        float *sx = nullptr, *sy = nullptr;    // sine matrices of the x and y interiors (separable solver)
-        float *mux = nullptr, *muy = nullptr;  // their eigenvalues -4 sin^2(pi m / (2 (n - 1)))
-        void *twx = nullptr, *twy = nullptr;   // FFT twiddles when nx - 1 and ny - 1 are powers of two
-        double *mux64 = nullptr, *muy64 = nullptr;   // FP64 copies for the FP64 direct solve
-        void *twx64 = nullptr, *twy64 = nullptr;
-    } sep;
     bool have_bz = false, have_solution = false;
     bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
     std::vector<void*> allocations;

@@ -60,7 +60,8 @@ static int choose_cut(const Hierarchy& H, size_t elem, size_t max_interior) {
     int cut = H.nlev() - 1;
     for (int l = H.nlev() - 1; l >= 0; --l) {
         size_t bytes = 0;
-        for (int m = l; m < H.nlev(); ++m) bytes += 2 * round_up(H.g[m].n, 4) * elem + H.g[m].nz * 10 * elem;
+        const size_t coef = elem == 8 ? sizeof(PlaneCoef<double>) : sizeof(PlaneCoef<float>);
+        for (int m = l; m < H.nlev(); ++m) bytes += 2 * round_up(H.g[m].n, 4) * elem + H.g[m].nz * coef;
         // the sub-cycle decodes node indices with float reciprocals (exact for rows of <= 1024 nodes)
         if (bytes > subcycle_smem_limit() || H.g[l].interior() > max_interior || H.g[l].nx - 2 > 1024 ||
             H.g[l].ny - 2 > 1024)
@@ -120,10 +121,25 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
     H.df.coef = static_cast<PlaneCoefDF*>(dev_alloc(c, g0.nz * sizeof(PlaneCoefDF)));
 }
 
+// Coarse-grid solve of the V-cycles by the separable solver: the first level
+// below the finest with at most sep_coarse interior nodes whose transforms
+// are available; -1 when none qualifies or the option is off.
+static int choose_exact(const Hierarchy& H, int sep_coarse) {
+    if (sep_coarse <= 0) return -1;
+    for (int l = 1; l < H.nlev(); ++l)
+        if (H.g[l].interior() <= size_t(sep_coarse) && sep_level_ok(H.g[l])) return l;
+    return -1;
+}
+
 void choose_cuts(mhs_ctx* c) {
     for (Hierarchy* H : {&c->h3, &c->h2}) {
         H->cut64 = choose_cut(*H, sizeof(double), size_t(c->opts.cut64));
         H->cut32 = choose_cut(*H, sizeof(float), size_t(c->opts.cut32));
+        H->exact = choose_exact(*H, c->opts.sep_coarse);
+        if (H->exact >= 0) {   // tables now: graph capture must not allocate
+            sep_tables<double>(c, *H, H->exact);
+            sep_tables<float>(c, *H, H->exact);
+        }
     }
 }
 
@@ -275,6 +291,15 @@ static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fi
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
+    if (l == H.exact) {
+        // coarse-grid solve: A u = f exactly (u's interior overwritten; the
+        // correction's boundary values are zero on coarse levels)
+        const Geom& g = H.g[l];
+        TimedScope t(c->timer, sizeof(T) == 8 ? MHS_KT_COARSE64 : MHS_KT_COARSE32, 2.0 * g.interior() * sizeof(T),
+                     0.0, st);
+        sep_exact<T>(c, H, l);
+        return;
+    }
     if (l >= cut_of<T>(H)) {
         subcycle<T>(c, H, l);
         return;
@@ -335,7 +360,8 @@ void fmg(mhs_ctx* c, Hierarchy& H, const T* r0) {
     }
     cudaStream_t st = c->stream;
     launch_restrict<T>(H.g[0], H.g[1], H.dim, r0, arrays<T>(H, 1).f, arrays<T>(H, 1).u, st);
-    const int top = std::min(std::max(cut_of<T>(H), 1), L - 1);
+    int top = std::min(std::max(cut_of<T>(H), 1), L - 1);
+    if (H.exact >= 1) top = std::min(top, H.exact);
     for (int l = 1; l < top; ++l)
         launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, arrays<T>(H, l).f, arrays<T>(H, l + 1).f,
                            arrays<T>(H, l + 1).u, st);
@@ -591,10 +617,7 @@ static bool read_cont(mhs_ctx* c, int which) {
 // in eager mode (kernel timing enabled) the host drives the cycles.
 void solve_begin(mhs_ctx* c, double tol, int mode) {
     cudaStream_t st = c->stream;
-    if (c->opts.flags & MHS_FLAG_SEPARABLE) {   // allocations: not inside a graph capture
-        if (mode == MHS_MIXED) sep_prepare(c);
-        else sep_prepare64(c);
-    }
+    if (c->opts.flags & MHS_FLAG_SEPARABLE) sep_prepare(c, mode);   // allocations: not inside a graph capture
     for (int q = 0; q < 2; ++q) {
         c->ctl_host[q] = SolveCtl{};
         c->ctl_host[q].tol = tol;

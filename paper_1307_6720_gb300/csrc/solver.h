@@ -59,12 +59,16 @@ void smooth_hook(mhs_ctx* c, Hierarchy& H, int l);   // one sweep as the V-cycle
 double read_norm2(mhs_ctx* c, int slot);
 void ensure_field_buffers(mhs_ctx* c);
 void ensure_post_buffers(mhs_ctx* c);
-// separable inner solver (kernels_sep.cu)
-void sep_prepare(mhs_ctx* c);
-void sep_solve(mhs_ctx* c, Hierarchy& H);
-bool sep_fp64_available(const mhs_ctx* c);   // FP64 direct solve: nx - 1 and ny - 1 powers of two
-void sep_prepare64(mhs_ctx* c);
-void sep_correct64(mhs_ctx* c, Hierarchy& H);
+// separable solver (kernels_sep.cu)
+bool sep_level_ok(const Geom& g);   // sine transforms fast (nx - 1, ny - 1 powers of two) or short (nx, ny <= 66)
+template <typename T>
+void sep_tables(mhs_ctx* c, Hierarchy& H, int l);   // build level l's tables once (allocates: not while capturing)
+template <typename T>
+void sep_exact(mhs_ctx* c, Hierarchy& H, int l);    // u = A^{-1} f on level l (interior; r, t scratch)
+void sep_prepare(mhs_ctx* c, int mode);             // finest-level tables of both hierarchies for a solve mode
+void sep_solve(mhs_ctx* c, Hierarchy& H);           // mixed mode: FP32 e = A^{-1} f on the finest level
+bool sep_fp64_available(const mhs_ctx* c);          // FP64 direct solves: sep_level_ok of the finest grid
+void sep_correct64(mhs_ctx* c, Hierarchy& H);       // FP64 mode: P += A^{-1} r on the finest level
 void ensure_staging(mhs_ctx* c);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)

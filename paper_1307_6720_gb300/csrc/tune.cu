@@ -104,6 +104,10 @@ void autotune(mhs_ctx* c, double tol, int mode, int repeats, mhs_tune_result* ou
     // the cut-off that fits shared memory) and 1 (the coarsest level only)
     std::vector<int> cuts{1};
     for (int l = 1; l < c->h3.nlev(); ++l) cuts.push_back(clamp_int(c->h3.g[l].interior()));
+    // coarse-grid solve by the separable solver on any level that allows it, or nowhere
+    std::vector<int> exacts{-1};
+    for (int l = 1; l < c->h3.nlev(); ++l)
+        if (sep_level_ok(c->h3.g[l])) exacts.push_back(clamp_int(c->h3.g[l].interior()));
     const int pairs[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
     for (int round = 0; round < 2; ++round) {
         const mhs_solver_opts before = best;
@@ -116,6 +120,11 @@ void autotune(mhs_ctx* c, double tol, int mode, int repeats, mhs_tune_result* ou
             mhs_solver_opts o = best;
             o.nu1 = p[0];
             o.nu2 = p[1];
+            consider(o);
+        }
+        for (int ex : exacts) {
+            mhs_solver_opts o = best;
+            o.sep_coarse = ex;
             consider(o);
         }
         for (int cut : cuts) {

@@ -26,7 +26,7 @@ MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, M
     1, 2, 4, 8, 16, 32
 MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE = 64, 128, 256
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
-MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE = range(6)
+MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE, MHS_OP_EXACT = range(7)
 
 
 class XiParams(ctypes.Structure):
@@ -42,7 +42,7 @@ class AtmosParams(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int), ("cut64", ctypes.c_int),
-                ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int)]
+                ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int), ("sep_coarse", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -229,8 +229,9 @@ def mhs_set_stream(h, stream) -> None:
     _check(LIB.mhs_set_stream(h, stream))
 
 
-def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0, fused_min=0) -> None:
-    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min)
+def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0, fused_min=0,
+                    sep_coarse=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min, sep_coarse)
     _check(LIB.mhs_set_options(h, ctypes.byref(o)))
 
 

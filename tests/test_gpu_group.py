@@ -36,8 +36,8 @@ def _members(M, seed=0):
     for q, (pr, opts) in enumerate(specs):
         h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"],
                          M.xi_params(pr["xi_kind"], pr["xi_a"], pr["xi_kappa"], pr["xi_b"], pr["xi_omega"]))
-        if opts:
-            M.mhs_set_options(h, **opts)
+        # a group's cycles end in the one-CTA sub-cycle: its solo twin does the same
+        M.mhs_set_options(h, sep_coarse=-1, **opts)
         bz = S.magnetogram_random(pr["nx"], pr["ny"], pr["Lx"], pr["Ly"], seed=100 * seed + q)
         M.mhs_set_lower_bz(h, bz)
         hs.append(h)
@@ -102,7 +102,7 @@ def test_group_repeated_solves_new_bz_and_exact_solution(M):
 
 def test_group_per_instance_status_and_errors(M):
     hs, prs, _ = _members(M)
-    M.mhs_set_options(hs[1], max_cycles=1, flags=M.MHS_FLAG_NO_FMG)
+    M.mhs_set_options(hs[1], max_cycles=1, flags=M.MHS_FLAG_NO_FMG, sep_coarse=-1)
     g = M.mhs_group_create(hs, M.MHS_MIXED)
     infos, sts = M.mhs_group_solve(g, len(hs), 1e-10)
     assert sts[1] == M.MHS_ERR_NO_CONVERGENCE

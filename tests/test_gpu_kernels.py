@@ -30,11 +30,12 @@ SHAPES = [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5)]
 
 def _make(M, nx, ny, nz, Lx=1.0, Ly=0.6, Lz=0.8, alpha=0.7, xi=XI2):
     """A handle on red-black point smoothing (the oracle's default smoother),
-    whatever smoother the anisotropy of the grid would select."""
+    whatever smoother the anisotropy of the grid would select, whose V-cycles
+    descend to the coarsest level (as the oracle's do by default)."""
     pr = S.problem(nx, ny, nz, Lx=Lx, Ly=Ly, Lz=Lz, alpha=alpha, **xi)
     h = M.mhs_create(nx, ny, nz, Lx, Ly, Lz, alpha,
                      M.xi_params(xi["xi_kind"], xi["xi_a"], xi["xi_kappa"], xi.get("xi_b", 0), xi.get("xi_omega", 0)))
-    M.mhs_set_options(h, flags=M.MHS_FLAG_POINT)
+    M.mhs_set_options(h, flags=M.MHS_FLAG_POINT, sep_coarse=-1)
     return pr, h
 
 
@@ -177,6 +178,80 @@ def test_coarse_solve_reaches_coarse_solution(M, dim, prec):
     M.mhs_destroy(h)
 
 
+def _level_problem(M, h, pr, dim, level):
+    nx, ny, nz = M.mhs_level_shape(h, dim, level)
+    return S.problem(nx, ny, nz if dim == 3 else 3, Lx=pr["Lx"], Ly=pr["Ly"], Lz=pr["Lz"], alpha=pr["alpha"],
+                     **{k: pr[k] for k in ("xi_kind", "xi_a", "xi_b", "xi_omega", "xi_kappa")})
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
+@pytest.mark.parametrize("shape", [(33, 17, 9), (65, 33, 33), (25, 13, 13), (49, 65, 17)])
+def test_exact_op_parity(M, shape, dim, prec):
+    """The separable solve of one level (sine transforms in x and y, a
+    tridiagonal system per mode along z) against a sparse direct solve of the
+    level's rediscretised operator, on every level it accepts: fast
+    transforms (nx - 1, ny - 1 powers of two) and dense ones (short rows)."""
+    from oracle import exact
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=0.6, Lz=0.8)
+    rng = np.random.default_rng(nx + ny + nz + dim)
+    for level in range(M.mhs_num_levels(h, dim)):
+        lx, ly, lz = M.mhs_level_shape(h, dim, level)
+        fast = (lx - 1) & (lx - 2) == 0 and (ly - 1) & (ly - 2) == 0
+        if not (fast or (lx <= 66 and ly <= 66)):
+            with pytest.raises(RuntimeError):
+                M.mhs_level_op(h, dim, level, M.MHS_OP_EXACT, prec)
+            continue
+        prl = _level_problem(M, h, pr, dim, level)
+        shape_l = (lz, ly, lx) if dim == 3 else (ly, lx)
+        f = rng.standard_normal(shape_l) * 10
+        if prec == 1:
+            f = f.astype(np.float32).astype(np.float64)
+        M.mhs_level_write(h, dim, level, M.MHS_FIELD_U, prec, np.zeros(shape_l))
+        M.mhs_level_write(h, dim, level, M.MHS_FIELD_F, prec, f)
+        M.mhs_level_op(h, dim, level, M.MHS_OP_EXACT, prec)
+        got = _read(M, h, dim, level, M.MHS_FIELD_U, prec)
+        if dim == 3:
+            want = exact.kron_solve3d(prl, np.zeros((ly, lx)), f)
+        else:
+            want = exact.kron_solve2d(prl, -f)
+        assert _rel(got, want) < (1e-12 if prec == 0 else 2e-5), (level, (lx, ly, lz))
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
+@pytest.mark.parametrize("exact_level", [1, 2])
+def test_vcycle_exact_coarse_parity(M, exact_level, dim, prec):
+    """One V(2,2)-cycle whose coarse-grid system on level 1 or 2 is solved
+    exactly by the separable solver, against the oracle's V-cycle stopping at
+    the same level with that system solved to rounding."""
+    nx, ny, nz = 65, 33, 17
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=0.5, Lz=0.25)
+    lx, ly, lz = M.mhs_level_shape(h, dim, exact_level)
+    interior = (lx - 2) * (ly - 2) * ((lz - 2) if dim == 3 else 1)
+    # sub-cycle only on the coarsest level, so that the cycle reaches exact_level
+    M.mhs_set_options(h, flags=M.MHS_FLAG_POINT, sep_coarse=interior, cut64=1, cut32=1)
+    rng = np.random.default_rng(13 + exact_level)
+    shape = (nz, ny, nx) if dim == 3 else (ny, nx)
+    u = rng.standard_normal(shape)
+    f = rng.standard_normal(shape) * 100
+    if dim == 2:
+        u[0, :] = u[-1, :] = u[:, 0] = u[:, -1] = 0.0
+    M.mhs_level_write(h, dim, 0, M.MHS_FIELD_U, prec, u)
+    M.mhs_level_write(h, dim, 0, M.MHS_FIELD_F, prec, f)
+    if prec == 1:
+        u, f = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+    M.mhs_level_op(h, dim, 0, M.MHS_OP_VCYCLE, prec)
+    got = _read(M, h, dim, 0, M.MHS_FIELD_U, prec)
+    want = oracle.vcycle(pr, u, f, exact_level=exact_level)
+    assert _rel(got, want) < (1e-11 if prec == 0 else 1e-5)
+    # and not the cycle that descends to the coarsest level
+    assert _rel(oracle.vcycle(pr, u, f), want) > 1e-7
+    M.mhs_destroy(h)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_vcycle_parity_3d(M, prec):
     nx, ny, nz = 33, 33, 17
@@ -294,7 +369,7 @@ def test_zline_vcycle_parity(M, prec, cut):
     nodes so that the global-memory line kernel runs on four levels."""
     nx, ny, nz = 65, 33, 33
     pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=0.5, Lz=0.5, xi=XI_STRONG)
-    M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE, cut64=cut, cut32=cut)
+    M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE, cut64=cut, cut32=cut, sep_coarse=-1)
     rng = np.random.default_rng(12)
     u = rng.standard_normal((nz, ny, nx))
     f = rng.standard_normal((nz, ny, nx)) * 100

@@ -42,6 +42,8 @@ MUTANTS = {
                  "const double cz = (d1(By, nx, ny, nz, i, j, k, 0, hx) - d1(Bx, nx, ny, nz, i, j, k, 1, hy));"),
     "trace_interp_weight": ("e[dz][dy] = f0 * (1.0 - f[0]) + f1 * f[0];", "e[dz][dy] = f0 * f[0] + f1 * (1.0 - f[0]);"),
     "rk4_stage_weight": ("(((k1[a] + 2.0 * k2[a]) + 2.0 * k3[a]) + k4[a])", "(((k1[a] + 2.0 * k2[a]) + k3[a]) + 2.0 * k4[a])"),
+    "exact_level_one_cycle": ("if (rn <= 1e-15 * fn || rn > 0.5 * prev) break;", "if (it > 0) break;"),
+    "exact_level_ignored": ("if (l == mg->exact_level) { exact_solve", "if (l == -2) { exact_solve"),
     "gs_divides_wrong_diag": ("u[c] = ((f ? f[c] : 0.0) - off) / L->diag[k];", "u[c] = ((f ? f[c] : 0.0) - off) / L->diag[0];"),
 }
 

@@ -166,6 +166,42 @@ def test_vcycle_convergence_factor():
     assert info["cycles_3d"] <= 14
 
 
+@pytest.mark.parametrize("dim", [3, 2])
+def test_vcycle_with_exact_coarse_level_is_two_grid_cycle(dim):
+    """With its coarse-grid system solved exactly on level 1, the oracle's
+    V-cycle is the textbook two-grid cycle: nu1 sweeps, residual, full
+    weighting, the coarse correction from a sparse direct solve of the
+    rediscretised coarse operator (scipy's SuperLU on the Kronecker-assembled
+    matrix), interpolation added, nu2 sweeps; composed here from the
+    oracle's separately pinned primitives."""
+    xi = dict(xi_kind=2, xi_a=0.7, xi_b=0.3, xi_omega=np.pi, xi_kappa=0.1)
+    nx, ny, nz = 17, 33, 9
+    pr = S.problem(nx, ny, nz, Lx=1.0, Ly=2.0, Lz=0.5, alpha=0.7, **xi)
+    rng = np.random.default_rng(41)
+    shape = (nz, ny, nx) if dim == 3 else (ny, nx)
+    u = rng.standard_normal(shape)
+    f = rng.standard_normal(shape) * 50
+    if dim == 2:
+        u[0, :] = u[-1, :] = u[:, 0] = u[:, -1] = 0.0
+    cx, cy = (nx - 1) // 2 + 1, (ny - 1) // 2 + 1
+    cz = (nz - 1) // 2 + 1
+    prc = S.problem(cx, cy, cz, Lx=1.0, Ly=2.0, Lz=0.5, alpha=0.7, **xi)
+    if dim == 3:
+        v = oracle.rbgs3d(pr, u, f, 2)
+        fc = oracle.restrict(oracle.residual3d(pr, v, f))
+        ec = exact.kron_solve3d(prc, np.zeros((cy, cx)), fc)
+        want = oracle.rbgs3d(pr, oracle.prolong_add(ec, v), f, 2)
+    else:
+        v = oracle.rbgs2d(pr, u, f, 2)
+        fc = oracle.restrict(oracle.residual2d(pr, v, f))
+        ec = exact.kron_solve2d(prc, -fc)
+        want = oracle.rbgs2d(pr, oracle.prolong_add(ec, v), f, 2)
+    got = oracle.vcycle(pr, u, f, exact_level=1)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # descending below level 1 instead gives a different (inexact) correction
+    assert np.abs(oracle.vcycle(pr, u, f) - want).max() > 1e-6 * np.abs(want).max()
+
+
 def test_potential_pair_antisymmetry():
     """B_z of the +/- pair is odd under x -> 1 - x, hence so is P (xi = 0, alpha = 0)."""
     pr, bz = S.potential_field_33()
