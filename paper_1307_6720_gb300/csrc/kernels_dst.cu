@@ -17,6 +17,7 @@
 // (element m of line l at out + l * out_line + m) or transposed (at
 // out + m * out_elem + l), in both cases with consecutive threads on
 // consecutive addresses.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -196,6 +197,13 @@ constexpr size_t DST_SMEM_MAX = 227 * 1024;
 template <typename T>
 void launch_dst(DstArgs<T> a, cudaStream_t st) {
     a.pairs = dst_pairs<T>(a.L);
+    // small transforms (coarse levels): fewer pairs per block, so that the
+    // blocks cover every SM about twice
+    auto blocks = [&](int p) { return size_t((a.lines + 2 * p - 1) / (2 * p)) * size_t(a.planes); };
+    while (a.pairs > 2 && blocks(a.pairs) < 2 * 152) a.pairs >>= 1;
+    // one thread per radix-8 unit of the block's pairs, 64 .. 256
+    const int units = a.pairs * std::max(1, (2 * a.L) / 8);
+    const int threads = std::min(256, std::max(64, (units + 31) / 32 * 32));
     const size_t smem = dst_smem_bytes<T>(a.L, a.pairs);
     if (smem > DST_SMEM_MAX) throw Error(MHS_ERR_INVALID_ARG, "sine transform lines too long for shared memory");
     static bool configured = false;   // per template instance
@@ -204,7 +212,7 @@ void launch_dst(DstArgs<T> a, cudaStream_t st) {
         configured = true;
     }
     const dim3 grid((a.lines + 2 * a.pairs - 1) / (2 * a.pairs), a.planes);
-    dst_kernel<T><<<grid, 256, smem, st>>>(a);
+    dst_kernel<T><<<grid, threads, smem, st>>>(a);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }

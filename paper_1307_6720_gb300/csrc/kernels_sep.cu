@@ -111,47 +111,73 @@ void gemm(const GemmArgs<T>& g, int batch, cudaStream_t st) {
     MHS_CUDA(cudaGetLastError());
 }
 
-// One thread per mode (n, m) of the transformed data t[k][n][m] (k = 0 ..
-// nzi-1 standing for planes 1 .. nzi): Thomas elimination along k with the
-// mode's diagonal D_k = base_k + cx_k mu_x(m) + cy_k mu_y(n), the eliminated
-// super-diagonal kept in w; t is overwritten by the solution.  The plane
-// coefficients (alpha^2 among them) are read from the level's table, so a
-// captured launch follows later parameter changes.
-// (ytrans: the fast index is the y mode, the layout [k][m][n] of the FFT path)
+// Elimination factors of the mode systems of one 3D level, one thread per
+// mode (fast index m, slow index n; the layout of the transformed data),
+// formed in FP64 from the FP64 plane coefficients and rounded to T:
+//   D_k = base_k + c_k^fast mu_fast(m) + c_k^slow mu_slow(n),
+//   pivot_1 = D_1, pivot_k = D_k - cz sup_{k-1}, inv_k = 1 / pivot_k,
+//   sup_k = cz inv_k,
+// with mu(m) = -4 sin^2(pi (m + 1) / (2 (n_nodes - 1))).  ytrans: the fast
+// index is the y mode (fast transforms), else the x mode (dense transforms).
+template <typename T>
+__global__ void sep_pivot_kernel(int nfast, int nslow, int nzi, int nodes_fast, int nodes_slow,
+                                 const PlaneCoef<double>* __restrict__ coef, int ytrans, T* __restrict__ inv,
+                                 T* __restrict__ sup) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (m >= nfast) return;
+    const double sf = sinpi(double(m + 1) / (2.0 * (nodes_fast - 1)));
+    const double ss = sinpi(double(n + 1) / (2.0 * (nodes_slow - 1)));
+    const double af = -4.0 * sf * sf, as = -4.0 * ss * ss;
+    const double cz = coef[1].cz;
+    const size_t stride = size_t(nfast) * nslow, o = size_t(n) * nfast + m;
+    double prev = 0.0;
+    for (int k = 0; k < nzi; ++k) {
+        const PlaneCoef<double> c = coef[k + 1];
+        const double d = ytrans ? c.base + c.cy * af + c.cx * as : c.base + c.cx * af + c.cy * as;
+        const double iv = 1.0 / (k ? d - cz * prev : d);
+        prev = cz * iv;
+        inv[k * stride + o] = T(iv);
+        sup[k * stride + o] = T(prev);
+    }
+}
+
+// One thread per mode (m fast, n slow) of the transformed data t[k][n][m]
+// (k = 0 .. nzi-1 standing for planes 1 .. nzi): the mode's tridiagonal
+// system along k solved with its precomputed elimination factors,
+//   forward  e_k <- (t_k - cz e_{k-1}) inv_k,
+//   backward e_k <- e_k - sup_k e_{k+1},
+// t overwritten by the solution.  U planes of right-hand sides (and, going
+// back, of eliminated values) are loaded before the recursion consumes them,
+// so U memory round trips overlap; the recursion is an FMA and a multiply
+// per plane.
 template <typename T>
 __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef<T>* __restrict__ coef,
-                                  const T* __restrict__ mufast, const T* __restrict__ muslow, T* __restrict__ t,
-                                  T* __restrict__ w, int ytrans) {
-    // U planes of right-hand sides (and, going back, of eliminated values)
-    // are loaded before the recursion consumes them, so U memory round trips
-    // overlap; the recursion itself is a chain of a few FMAs per plane
+                                  const T* __restrict__ inv, const T* __restrict__ sup, T* __restrict__ t) {
     constexpr int U = 8;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m >= nfast) return;
-    const size_t stride = size_t(nfast) * nslow;
-    T* tc = t + size_t(n) * nfast + m;
-    T* wc = w + size_t(n) * nfast + m;
-    const T af = mufast[m], as = muslow[n];
+    const size_t stride = size_t(nfast) * nslow, o = size_t(n) * nfast + m;
+    T* tc = t + o;
+    const T* ic = inv + o;
+    const T* sc = sup + o;
     const T cz = coef[1].cz;
-    T cp = T(0), dp = T(0);
+    T dp = T(0);
     for (int k0 = 0; k0 < nzi; k0 += U) {
-        T rhs[U];
+        T rhs[U], iv[U];
 #pragma unroll
         for (int q = 0; q < U; ++q)
-            if (k0 + q < nzi) rhs[q] = tc[(k0 + q) * stride];
+            if (k0 + q < nzi) {
+                rhs[q] = tc[(k0 + q) * stride];
+                iv[q] = ic[(k0 + q) * stride];
+            }
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int k = k0 + q;
             if (k < nzi) {
-                const PlaneCoef<T> c = coef[k + 1];
-                const T d = ytrans ? c.base + c.cy * af + c.cx * as : c.base + c.cx * af + c.cy * as;
-                const T piv = k ? fma(-cz, cp, d) : d;
-                const T inv = T(1) / piv;
-                dp = (k ? fma(-cz, dp, rhs[q]) : rhs[q]) * inv;
-                cp = cz * inv;
+                dp = (k ? fma(-cz, dp, rhs[q]) : rhs[q]) * iv[q];
                 tc[k * stride] = dp;
-                wc[k * stride] = cp;
             }
         }
     }
@@ -162,7 +188,7 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
         for (int q = 0; q < U; ++q)
             if (k0 - q >= 0) {
                 dd[q] = tc[(k0 - q) * stride];
-                cc[q] = wc[(k0 - q) * stride];
+                cc[q] = sc[(k0 - q) * stride];
             }
 #pragma unroll
         for (int q = 0; q < U; ++q)
@@ -191,17 +217,20 @@ int ilog2(int v) {
 }
 
 // mode solves on the transformed data t (fast index nfast): tridiagonal
-// systems along z (3D, w scratch) or a division per mode (2D)
+// systems along z with the level's elimination factors (3D) or a division per
+// mode (2D)
 template <typename T>
-void mode_solve(const Geom& g, int dim, const PlaneCoef<T>* coef, int nfast, int nslow, const T* mufast,
-                const T* muslow, bool ytrans, T* t, T* w, cudaStream_t st) {
-    const dim3 grid((nfast + 127) / 128, nslow);
+void mode_solve(const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, int nfast, int nslow,
+                const T* mufast, const T* muslow, bool ytrans, T* t, cudaStream_t st) {
+    const int threads = nfast <= 64 ? 64 : 128;
+    const dim3 grid((nfast + threads - 1) / threads, nslow);
     if (dim == 3) {
-        sep_thomas_kernel<T><<<grid, 128, 0, st>>>(nfast, nslow, g.nz - 2, coef, mufast, muslow, t, w, ytrans ? 1 : 0);
+        sep_thomas_kernel<T><<<grid, threads, 0, st>>>(nfast, nslow, g.nz - 2, coef, static_cast<const T*>(tab.inv),
+                                                      static_cast<const T*>(tab.sup), t);
     } else {
         const T cf = T(1.0 / (ytrans ? g.hy * g.hy : g.hx * g.hx));
         const T cs = T(1.0 / (ytrans ? g.hx * g.hx : g.hy * g.hy));
-        sep_divide_kernel<T><<<grid, 128, 0, st>>>(nfast, nslow, cf, cs, mufast, muslow, t);
+        sep_divide_kernel<T><<<grid, threads, 0, st>>>(nfast, nslow, cf, cs, mufast, muslow, t);
     }
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
@@ -211,7 +240,7 @@ void mode_solve(const Geom& g, int dim, const PlaneCoef<T>* coef, int nfast, int
 // pitched level arrays (interior read / written), t1 and t2 dense scratch of
 // the interior size (t2 may be the array of f).
 // Fast transforms: x lines of f -> t1[k][m][j] (transposed), y lines ->
-// t2[k][m][n], mode solves (t1 as scratch), inverse y -> t1[k][j][m]
+// t2[k][m][n], mode solves, inverse y -> t1[k][j][m]
 // (transposed), inverse x -> out, scaled.
 // Dense transforms: t1[k][j][m] = sum_i f[k][j][i] Sx[m][i], t2[k][n][m] =
 // sum_j Sy[n][j] t1[k][j][m], mode solves, and back the same way.
@@ -239,7 +268,7 @@ void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, c
         b.in = t1; b.in_plane = pl; b.in_line = nyi;
         b.out = t2; b.out_plane = pl; b.out_line = nyi; b.out_elem = 1;
         launch_dst<T>(b, st);
-        mode_solve<T>(g, dim, coef, nyi, nxi, muy, mux, true, t2, t1, st);
+        mode_solve<T>(g, dim, coef, tab, nyi, nxi, muy, mux, true, t2, st);
         b.in = t2; b.out = t1; b.out_line = 1; b.out_elem = nxi;
         launch_dst<T>(b, st);
         a.in = t1; a.in_plane = pl; a.in_line = nxi;
@@ -253,7 +282,7 @@ void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, c
     const T* Sy = static_cast<const T*>(tab.sy);
     gemm<T>(GemmArgs<T>{nyi, nxi, nxi, f + off, g.px, sA, Sx, nxi, 0, t1, nxi, pl, T(1), 0}, nzi, st);
     gemm<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t1, nxi, pl, t2, nxi, pl, T(1), 0}, nzi, st);
-    mode_solve<T>(g, dim, coef, nxi, nyi, mux, muy, false, t2, t1, st);
+    mode_solve<T>(g, dim, coef, tab, nxi, nyi, mux, muy, false, t2, st);
     gemm<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t2, nxi, pl, t1, nxi, pl, T(1), 0}, nzi, st);
     gemm<T>(GemmArgs<T>{nyi, nxi, nxi, t1, nxi, pl, Sx, nxi, 0, out + off, g.px, sA, scale, accumulate ? 1 : 0}, nzi,
             st);
@@ -267,6 +296,22 @@ template <>
 LevelArrays<float>& arrays_of<float>(Hierarchy& H, int l) { return H.s[l]; }
 template <typename T>
 std::vector<SepTables>& tables_of(Hierarchy& H) { return sizeof(T) == 8 ? H.sep64 : H.sep32; }
+
+// elimination factors of level l's mode systems from the current coefficients
+template <typename T>
+void compute_pivots(mhs_ctx* c, Hierarchy& H, int l, SepTables& t) {
+    const Geom& g = H.g[l];
+    if (H.dim != 3 || !t.inv) return;
+    const bool ytrans = t.twx != nullptr;
+    const int nxi = g.nx - 2, nyi = g.ny - 2;
+    const int nfast = ytrans ? nyi : nxi, nslow = ytrans ? nxi : nyi;
+    const int threads = nfast <= 64 ? 64 : 128;
+    sep_pivot_kernel<T><<<dim3((nfast + threads - 1) / threads, nslow), threads, 0, c->stream>>>(
+        nfast, nslow, g.nz - 2, ytrans ? g.ny : g.nx, ytrans ? g.nx : g.ny, H.d[l].coef, ytrans ? 1 : 0,
+        static_cast<T*>(t.inv), static_cast<T*>(t.sup));
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
 
 template <typename T>
 const SepTables& tables(Hierarchy& H, int l) {
@@ -330,7 +375,22 @@ void sep_tables(mhs_ctx* c, Hierarchy& H, int l) {
         t.sx = upload(sine(g.nx));
         t.sy = upload(sine(g.ny));
     }
+    if (H.dim == 3 && g.nz > 2) {
+        const size_t n = size_t(g.nx - 2) * size_t(g.ny - 2) * size_t(g.nz - 2);
+        for (void** p : {&t.inv, &t.sup}) {
+            MHS_CUDA(cudaMalloc(p, n * sizeof(T)));
+            c->allocations.push_back(*p);
+        }
+        compute_pivots<T>(c, H, l, t);
+    }
     t.ready = true;
+}
+
+void sep_refresh(mhs_ctx* c, Hierarchy& H) {
+    for (size_t l = 0; l < H.sep64.size(); ++l)
+        if (H.sep64[l].ready) compute_pivots<double>(c, H, int(l), H.sep64[l]);
+    for (size_t l = 0; l < H.sep32.size(); ++l)
+        if (H.sep32[l].ready) compute_pivots<float>(c, H, int(l), H.sep32[l]);
 }
 
 template <typename T>

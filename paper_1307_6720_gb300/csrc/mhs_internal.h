@@ -90,13 +90,17 @@ struct DFState {
 
 // Tables of the separable solver on one level (device, owned by the
 // context's allocation list): the mode eigenvalues -4 sin^2(pi m / (2 (n - 1)))
-// of the x and y second differences, and either the FFT twiddles (nx - 1 and
-// ny - 1 powers of two) or the dense sine matrices (short rows).  Element
-// type: double for sep64, float for sep32.
+// of the x and y second differences, either the FFT twiddles (nx - 1 and
+// ny - 1 powers of two) or the dense sine matrices (short rows), and for 3D
+// levels the elimination factors of every mode's tridiagonal system along z
+// (inverse pivots and eliminated super-diagonals, in the layout of the
+// transformed data), which depend on alpha and xi but not on the right-hand
+// side.  Element type: double for sep64, float for sep32.
 struct SepTables {
     void *mux = nullptr, *muy = nullptr;
     void *twx = nullptr, *twy = nullptr;
     void *sx = nullptr, *sy = nullptr;
+    void *inv = nullptr, *sup = nullptr;
     bool ready = false;
 };
 

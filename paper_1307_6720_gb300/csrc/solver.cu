@@ -152,6 +152,9 @@ void compute_coefficients(mhs_ctx* c) {
         launch_df_coef(H->g[0], H->d[0].coef, H->df.coef, c->stream);
     }
     launch_profiles(c->h3.g[0], c->xi, c->atm, c->prof, c->stream);
+    // separable-solver pivots follow alpha and xi (tables live in device memory, so
+    // captured graphs stay valid)
+    for (Hierarchy* H : {&c->h3, &c->h2}) sep_refresh(c, *H);
     // the smoother may follow the anisotropy class; the graph key holds the choice,
     // so a captured solve is rebuilt only when the choice changes
     c->aniso = aniso_class(c);
@@ -165,7 +168,6 @@ void create(mhs_ctx* c) {
     subcycle_prepare();
     build_hierarchy(c, c->h3, 3);
     build_hierarchy(c, c->h2, 2);
-    choose_cuts(c);
     c->ns.max_blocks = 65536;
     c->ns.partial = static_cast<double*>(dev_alloc(c, c->ns.max_blocks * sizeof(double)));
     c->ns.result = static_cast<double*>(dev_alloc(c, 16 * sizeof(double)));
@@ -177,6 +179,7 @@ void create(mhs_ctx* c) {
     c->bz = static_cast<double*>(dev_alloc(c, c->h2.g[0].n * sizeof(double)));
     c->prof = static_cast<double*>(dev_alloc(c, 8 * size_t(c->nz) * sizeof(double)));
     compute_coefficients(c);
+    choose_cuts(c);   // after the coefficients: separable tables derive their pivots from them
     MHS_CUDA(cudaStreamSynchronize(c->stream));
 }
 
@@ -312,11 +315,16 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     const bool f_zero = dbl && l == 0 && H.dim == 3 && c->f_zero_finest;
     const double fs = f_zero ? 0.0 : s;
     const T* f = f_zero ? nullptr : A.f;
-    const double upd_flops = H.dim == 3 ? 10.0 : 7.0;
+    // algorithmic flops per node: the update u = f/d - ax(E+W) - ay(N+S) [- az(U+D)]
+    // takes 2 (3) additions, 2 (3) multiplications, 2 (3) subtractions and, with f,
+    // one more multiplication and subtraction; the residual f - A u adds the
+    // centre term (a multiplication and an addition) to the stencil sum
+    const double upd_flops = H.dim == 3 ? (f_zero ? 8.0 : 10.0) : 7.0;
+    const double res_flops = H.dim == 3 ? (f_zero ? 10.0 : 11.0) : 8.0;
     const bool fine = H.dim == 3 && l == 0;
     smooth_n<T>(c, H, l, f, c->opts.nu1, fine, N * (2 * s + fs), N * upd_flops);
     {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * (upd_flops + 1), st, fine);
+        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * res_flops, st, fine);
         launch_residual<T>(g, H.dim, A.coef, A.u, f, A.r, nullptr, 0, st);
     }
     LevelArrays<T>& C = arrays<T>(H, l + 1);
@@ -402,18 +410,21 @@ static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
     const Geom& g = H.g[0];
     LevelArrays<double>& A = H.d[0];
     const double N = double(g.interior());
-    const double fb = (H.dim == 3 && c->f_zero_finest) ? 0.0 : 8.0;
-    const double fl = H.dim == 3 ? 11.0 : 8.0;
+    const bool fz = H.dim == 3 && c->f_zero_finest;   // f = 0: not read
+    // bytes: u read, r written, f read unless zero; flops: the residual (10 in 3D
+    // without f, 11 with f, 8 in 2D) and the square-accumulate of the norm (2)
+    const double fb = fz ? 0.0 : 8.0;
+    const double fl = (H.dim == 3 ? (fz ? 10.0 : 11.0) : 8.0) + 2.0;
     if (mode == MHS_MIXED) {
         // double-float residual of P = hi + lo, rounded into the FP32 right-hand side
-        const bool fz = H.dim == 3 && c->f_zero_finest;
         TimedScope t(c->timer, MHS_KT_RESID_MIXED, N * (8.0 + (fz ? 0.0 : 8.0) + 4.0), N * 70.0, c->stream,
                      H.dim == 3);
         return launch_df_residual(g, H.dim, H.df.coef, H.df.hi, H.df.lo, fz ? nullptr : H.df.fh,
                                   fz ? nullptr : H.df.fl, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
     }
     TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream, H.dim == 3);
-    return launch_residual<double>(g, H.dim, A.coef, A.u, A.f, A.r, c->ns.partial, c->ns.max_blocks, c->stream);
+    return launch_residual<double>(g, H.dim, A.coef, A.u, fz ? nullptr : A.f, A.r, c->ns.partial, c->ns.max_blocks,
+                                   c->stream);
 }
 
 static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {

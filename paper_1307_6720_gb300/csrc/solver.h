@@ -65,6 +65,7 @@ template <typename T>
 void sep_tables(mhs_ctx* c, Hierarchy& H, int l);   // build level l's tables once (allocates: not while capturing)
 template <typename T>
 void sep_exact(mhs_ctx* c, Hierarchy& H, int l);    // u = A^{-1} f on level l (interior; r, t scratch)
+void sep_refresh(mhs_ctx* c, Hierarchy& H);         // recompute the pivots of every built table (new coefficients)
 void sep_prepare(mhs_ctx* c, int mode);             // finest-level tables of both hierarchies for a solve mode
 void sep_solve(mhs_ctx* c, Hierarchy& H);           // mixed mode: FP32 e = A^{-1} f on the finest level
 bool sep_fp64_available(const mhs_ctx* c);          // FP64 direct solves: sep_level_ok of the finest grid
