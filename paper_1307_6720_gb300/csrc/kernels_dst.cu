@@ -58,7 +58,10 @@ __device__ __forceinline__ void bfly(C& a, C& b, const C w) {
 // those stages combine; sub-stage t pairs j with j + 2^t under the twiddle
 // e^{-2 pi i rr / (2H)}, H = h 2^t, rr = r + (j mod 2^t) h, taken from the
 // table e^{-2 pi i q / (2L)} at q = rr L / H.
-template <int Q, typename C>
+// LAST: these are the final stages; the last one only needs its lower
+// outputs (positions below L hold the modes the transform returns), so the
+// upper half is neither formed nor stored.
+template <int Q, bool LAST, typename C>
 __device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int PS, int bits, int L, int s) {
     constexpr int R = 1 << Q;
     const int h = 1 << s, ub = bits - Q;
@@ -79,11 +82,56 @@ __device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int PS, int b
             for (int j = 0; j < R; ++j) {
                 if (j & d) continue;
                 const int rr = r + (j & (d - 1)) * h;
-                bfly(v[j], v[j + d], tw[rr * tstride]);
+                if (LAST && t == Q - 1) {
+                    const C w = tw[rr * tstride];
+                    const C b = v[j + d];
+                    v[j] = C{v[j].x + (b.x * w.x - b.y * w.y), v[j].y + (b.x * w.y + b.y * w.x)};
+                } else {
+                    bfly(v[j], v[j + d], tw[rr * tstride]);
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < R; ++j) zp[phys(base + j * h)] = v[j];
+        for (int j = 0; j < (LAST ? R / 2 : R); ++j) zp[phys(base + j * h)] = v[j];
+    }
+}
+
+// The first three stages (half-sizes 1, 2, 4) as one radix-8 pass whose
+// twiddles are the eighth roots of unity e^{-i pi q / 4}: multiplications by
+// 1 and -i become additions and swaps, those by (+-1 - i)/sqrt(2) two
+// additions and two multiplications.
+template <typename C>
+__device__ __forceinline__ void fft_first(C* z, int P, int PS, int bits) {
+    using T = decltype(C{}.x);
+    const T c = T(0.70710678118654752440);
+    const int ub = bits - 3;
+    const int units = P << ub;
+    for (int e = threadIdx.x; e < units; e += blockDim.x) {
+        const int pair = e >> ub, u = e & ((1 << ub) - 1);
+        const int base = u << 3;
+        C* zp = z + pair * PS;
+        C v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = zp[phys(base + j)];
+        auto add = [](C& a, C& b, const C t) {   // a, b <- a + t, a - t
+            b = C{a.x - t.x, a.y - t.y};
+            a = C{a.x + t.x, a.y + t.y};
+        };
+        // half-size 1: twiddle 1
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) add(v[j], v[j + 1], v[j + 1]);
+        // half-size 2: twiddles 1, -i
+        add(v[0], v[2], v[2]);
+        add(v[4], v[6], v[6]);
+        add(v[1], v[3], C{v[3].y, -v[3].x});
+        add(v[5], v[7], C{v[7].y, -v[7].x});
+        // half-size 4: twiddles 1, (1 - i)/sqrt2, -i, (-1 - i)/sqrt2
+        add(v[0], v[4], v[4]);
+        add(v[1], v[5], C{(v[5].x + v[5].y) * c, (v[5].y - v[5].x) * c});
+        add(v[2], v[6], C{v[6].y, -v[6].x});
+        add(v[3], v[7], C{(v[7].y - v[7].x) * c, -(v[7].x + v[7].y) * c});
+#pragma unroll
+        for (int j = 0; j < 8; ++j) zp[phys(base + j)] = v[j];
     }
 }
 
@@ -131,17 +179,24 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
         }
     }
     __syncthreads();
-    // radix-8 passes (three stages each), the remaining one or two stages last
+    // radix-8 passes (three stages each; the first with constant twiddles), the
+    // remaining one or two stages last
     int s = 0;
+    if (bits >= 3) {
+        fft_first(z, P, PS, bits);
+        __syncthreads();
+        s = 3;
+    }
     for (; s + 3 <= bits; s += 3) {
-        fft_pass<3>(z, tw, P, PS, bits, a.L, s);
+        if (s + 3 == bits) fft_pass<3, true>(z, tw, P, PS, bits, a.L, s);
+        else fft_pass<3, false>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     }
     if (bits - s == 2) {
-        fft_pass<2>(z, tw, P, PS, bits, a.L, s);
+        fft_pass<2, true>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     } else if (bits - s == 1) {
-        fft_pass<1>(z, tw, P, PS, bits, a.L, s);
+        fft_pass<1, true>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     }
     // X_a = -Im(Z)/2, X_b = Re(Z)/2, m = 1 .. N, scaled

@@ -149,12 +149,12 @@ __global__ void sep_pivot_kernel(int nfast, int nslow, int nzi, int nodes_fast, 
 //   backward e_k <- e_k - sup_k e_{k+1},
 // t overwritten by the solution.  U planes of right-hand sides (and, going
 // back, of eliminated values) are loaded before the recursion consumes them,
-// so U memory round trips overlap; the recursion is an FMA and a multiply
-// per plane.
+// so U memory round trips overlap (the factor tables through the read-only
+// path); the recursion is an FMA and a multiply per plane.
 template <typename T>
 __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef<T>* __restrict__ coef,
                                   const T* __restrict__ inv, const T* __restrict__ sup, T* __restrict__ t) {
-    constexpr int U = 8;
+    constexpr int U = 16;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m >= nfast) return;
@@ -170,7 +170,7 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
         for (int q = 0; q < U; ++q)
             if (k0 + q < nzi) {
                 rhs[q] = tc[(k0 + q) * stride];
-                iv[q] = ic[(k0 + q) * stride];
+                iv[q] = __ldg(ic + (k0 + q) * stride);
             }
 #pragma unroll
         for (int q = 0; q < U; ++q) {
@@ -188,7 +188,7 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
         for (int q = 0; q < U; ++q)
             if (k0 - q >= 0) {
                 dd[q] = tc[(k0 - q) * stride];
-                cc[q] = sc[(k0 - q) * stride];
+                cc[q] = __ldg(sc + (k0 - q) * stride);
             }
 #pragma unroll
         for (int q = 0; q < U; ++q)

@@ -56,9 +56,13 @@ __device__ __forceinline__ void residual_body(const Geom& g, const PlaneCoef<T>*
         for (int k = D3 ? 1 + b.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gd.z) {
             const PlaneCoef<T> c = coef[k];
             const size_t o = at(g, i, j, k);
-            T au = c.cx * (u[o + 1] + u[o - 1]) + c.cy * (u[o + g.px] + u[o - g.px]) + c.d * u[o];
-            if (D3) au += c.cz * (u[o + g.plane] + u[o - g.plane]);
-            const T rv = (f ? f[o] : T(0)) - au;
+            // r = f - cz (U + D) - cy (N + S) - cx (E + W) - d u: one FMA per
+            // term, f (or 0) as the first addend
+            T v = f ? f[o] : T(0);
+            if (D3) v = fma(-c.cz, u[o + g.plane] + u[o - g.plane], v);
+            v = fma(-c.cy, u[o + g.px] + u[o - g.px], v);
+            v = fma(-c.cx, u[o + 1] + u[o - 1], v);
+            const T rv = fma(-c.d, u[o], v);
             r[o] = rv;
             if (NORM) acc += double(rv) * double(rv);
         }
@@ -141,16 +145,21 @@ __device__ __forceinline__ void residual_body_v4(const Geom& g, const PlaneCoef<
             if (i < 1 || i > g.nx - 2) continue;
             const float e = q < 3 ? lane(cc, q + 1) : east;
             const float w = q > 0 ? lane(cc, q - 1) : west;
-            float au = c.cx * (e + w) + c.cy * (lane(nn, q) + lane(ss, q)) + c.d * lane(cc, q);
-            au += c.cz * (lane(uu, q) + lane(dd, q));
-            res[q] = (f ? lane(ff, q) : 0.f) - au;
+            float v = f ? lane(ff, q) : 0.f;
+            v = fmaf(-c.cz, lane(uu, q) + lane(dd, q), v);
+            v = fmaf(-c.cy, lane(nn, q) + lane(ss, q), v);
+            v = fmaf(-c.cx, e + w, v);
+            res[q] = fmaf(-c.d, lane(cc, q), v);
         }
         *reinterpret_cast<float4*>(r + o) = make_float4(res[0], res[1], res[2], res[3]);
     }
 }
 
 // Full weighting: tensor product of (1/4, 1/2, 1/4) around the fine node
-// (2I, 2J, 2K) coincident with coarse interior node (I, J, K).  With
+// (2I, 2J, 2K) coincident with coarse interior node (I, J, K), formed as the
+// tensor product of (1, 2, 1) sums (two operations per triple: a + c, then
+// an FMA with 2b) scaled once by 1/64 (2D: 1/16); the power-of-two weights
+// make this the same weighted sum up to the order of the additions.  With
 // uc != nullptr the coarse iterate is zeroed at the same nodes (the initial
 // guess of the coarse-grid correction).
 template <typename T, bool D3>
@@ -161,19 +170,14 @@ __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, co
     if (I > gc.nx - 2 || J > gc.ny - 2) return;
     for (int K = D3 ? 1 + b.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gd.z) {
         const size_t o = at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
-        T acc = T(0);
-#pragma unroll
-        for (int c = (D3 ? -1 : 0); c <= (D3 ? 1 : 0); ++c) {
-            const T wc = D3 ? (c == 0 ? T(0.5) : T(0.25)) : T(1);
-            const size_t oc = o + (ptrdiff_t)c * (ptrdiff_t)gf.plane;
-            T s = T(0);
-#pragma unroll
-            for (int bb = -1; bb <= 1; ++bb) {
-                const T wb = (bb == 0) ? T(0.5) : T(0.25);
-                const size_t ob = oc + (ptrdiff_t)bb * gf.px;
-                s += wb * (T(0.25) * rf[ob - 1] + T(0.5) * rf[ob] + T(0.25) * rf[ob + 1]);
-            }
-            acc += wc * s;
+        auto row = [&](size_t ob) { return fma(T(2), rf[ob], rf[ob - 1] + rf[ob + 1]); };
+        auto plane = [&](size_t oc) { return fma(T(2), row(oc), row(oc - gf.px) + row(oc + gf.px)); };
+        T acc;
+        if (D3) {
+            const T lo = plane(o - gf.plane), mid = plane(o), hi = plane(o + gf.plane);
+            acc = fma(T(2), mid, lo + hi) * T(1.0 / 64.0);
+        } else {
+            acc = plane(o) * T(1.0 / 16.0);
         }
         fc[at(gc, I, J, K)] = acc;
         if (uc) uc[at(gc, I, J, K)] = T(0);
