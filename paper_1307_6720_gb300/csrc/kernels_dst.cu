@@ -157,7 +157,6 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
     const int nl = min(2 * P, a.lines - line0);       // lines of the block
     const T* in = a.in + plane * a.in_plane + (long long)line0 * a.in_line;
     const C* twg = static_cast<const C*>(a.tw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < a.L; e += blockDim.x) tw[e] = twg[e];
     // positions 0 and L (bit-reversed: 0 and 1) of every pair are zero; a pair
     // with one line has a zero imaginary part everywhere
@@ -168,14 +167,33 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
     if (nl & 1)
         for (int e = threadIdx.x; e < L2; e += blockDim.x) reinterpret_cast<T*>(&z[(nl >> 1) * PS + phys(e)])[1] = T(0);
     __syncthreads();
-    // scatter the odd extensions into bit-reversed positions (a warp per line)
-    for (int l = warp; l < nl; l += nwarps) {
-        C* zp = z + (l >> 1) * PS;
-        const T* src = in + (long long)l * a.in_line;
-        for (int i = 1 + lane; i <= N; i += 32) {
-            const T v = src[i - 1];
-            reinterpret_cast<T*>(&zp[phys(bitrev(i, bits))])[l & 1] = v;
-            reinterpret_cast<T*>(&zp[phys(bitrev(L2 - i, bits))])[l & 1] = -v;
+    // scatter the odd extensions into bit-reversed positions: element e of the
+    // block's nl * N inputs is x_i of line l (e = l N + i - 1), consecutive
+    // threads on consecutive inputs; U loads per thread are in flight before
+    // their values are placed
+    {
+        constexpr int U = 8;
+        const int total = nl * N;
+        for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+            T v[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int e = e0 + q * blockDim.x;
+                if (e < total) {
+                    const int l = e / N, i = e - l * N;
+                    v[q] = in[(long long)l * a.in_line + i];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int e = e0 + q * blockDim.x;
+                if (e < total) {
+                    const int l = e / N, i = e - l * N + 1;
+                    C* zp = z + (l >> 1) * PS;
+                    reinterpret_cast<T*>(&zp[phys(bitrev(i, bits))])[l & 1] = v[q];
+                    reinterpret_cast<T*>(&zp[phys(bitrev(L2 - i, bits))])[l & 1] = -v[q];
+                }
+            }
         }
     }
     __syncthreads();
@@ -199,28 +217,40 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
         fft_pass<1, true>(z, tw, P, PS, bits, a.L, s);
         __syncthreads();
     }
-    // X_a = -Im(Z)/2, X_b = Re(Z)/2, m = 1 .. N, scaled
+    // X_a = -Im(Z)/2, X_b = Re(Z)/2, m = 1 .. N, scaled; the block's nl * N
+    // outputs flattened so that consecutive threads write consecutive
+    // addresses: line layout (m fastest) or transposed (line fastest)
     const T hs = T(0.5) * a.scale;
     T* out = a.out + plane * a.out_plane;
-    if (a.out_elem == 1) {
-        for (int l = warp; l < nl; l += nwarps) {
-            const C* zp = z + (l >> 1) * PS;
-            T* dst = out + (long long)(line0 + l) * a.out_line;
-            for (int m = 1 + lane; m <= N; m += 32) {
-                const C zm = zp[phys(m)];
-                const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
-                dst[m - 1] = a.accumulate ? dst[m - 1] + v : v;
+    const int total = nl * N;
+    const bool lines_out = a.out_elem == 1;
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+        T v[U], old[U];
+        long long at[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < total) {
+                int l, m;
+                if (lines_out) {
+                    l = e / N;
+                    m = e - l * N + 1;
+                } else {
+                    m = e / nl + 1;
+                    l = e - (m - 1) * nl;
+                }
+                const C zm = z[(l >> 1) * PS + phys(m)];
+                v[q] = (l & 1) ? hs * zm.x : -hs * zm.y;
+                at[q] = lines_out ? (long long)(line0 + l) * a.out_line + (m - 1)
+                                  : (long long)(m - 1) * a.out_elem + line0 + l;
+                if (a.accumulate) old[q] = out[at[q]];
             }
         }
-    } else {
-        // transposed: a warp per mode, consecutive lanes on consecutive lines
-        for (int m = 1 + warp; m <= N; m += nwarps) {
-            T* dst = out + (long long)(m - 1) * a.out_elem + line0;
-            for (int l = lane; l < nl; l += 32) {
-                const C zm = z[(l >> 1) * PS + phys(m)];
-                const T v = (l & 1) ? hs * zm.x : -hs * zm.y;
-                dst[l] = a.accumulate ? dst[l] + v : v;
-            }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < total) out[at[q]] = a.accumulate ? old[q] + v[q] : v[q];
         }
     }
 }

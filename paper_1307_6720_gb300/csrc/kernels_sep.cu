@@ -19,6 +19,7 @@
 // the planes; the inverse is the same transform scaled by
 // (2/(nx-1)) (2/(ny-1)).  In FP32 the solve is accurate to about 1e-6
 // relative, which the double-float outer loop of mixed mode then corrects.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -199,6 +200,120 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
     }
 }
 
+// The same mode systems with more parallelism, for levels whose planes fit
+// shared memory: a block takes 32 consecutive fast modes of one slow index,
+// stages their right-hand sides and factors for every plane through shared
+// memory (coalesced rows; the tile is padded to 33 columns), and a warp solves
+// one mode at a time with its lanes over the planes.  Each recurrence of the
+// elimination is affine in its carried value,
+//   forward  e_k = a_k e_{k-1} + b_k,  a_k = -cz inv_k (a_0 = 0), b_k = t_k inv_k,
+//   backward e_k = alpha_k e_{k+1} + e_k,  alpha_k = -sup_k (0 on the top plane),
+// so every lane composes the maps of its run of consecutive planes, a warp
+// scan of the composed maps (shuffles) gives each lane the value entering its
+// run, and the lane then repeats the sequential steps of its run from it.
+template <typename T>
+__global__ void __launch_bounds__(1024) sep_scan_kernel(int nfast, int nslow, int nzi,
+                                                       const PlaneCoef<T>* __restrict__ coef,
+                                                       const T* __restrict__ inv, const T* __restrict__ sup,
+                                                       T* __restrict__ t) {
+    extern __shared__ __align__(16) unsigned char scan_smem[];
+    constexpr int W = 33;
+    T* st = reinterpret_cast<T*>(scan_smem);   // [nzi][W]: right-hand sides, then solution
+    T* si = st + size_t(nzi) * W;              // inverse pivots
+    T* ss = si + size_t(nzi) * W;              // eliminated super-diagonals
+    const int m0 = blockIdx.x * 32, n = blockIdx.y;
+    const int nc = min(32, nfast - m0);
+    const size_t stride = size_t(nfast) * nslow, base = size_t(n) * nfast + m0;
+    const T cz = coef[1].cz;
+    // rows in batches of R per thread, every load of a batch issued before its
+    // values are stored (one memory round trip per batch instead of per row)
+    constexpr int R = 8;
+    const int c_ld = threadIdx.x & 31, r_ld = threadIdx.x >> 5, rstep = blockDim.x >> 5;
+    for (int k0 = r_ld; k0 < nzi; k0 += R * rstep) {
+        T vt[R], vi[R], vs[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int k = k0 + q * rstep;
+            if (k < nzi && c_ld < nc) {
+                const size_t gi = k * stride + base + c_ld;
+                vt[q] = t[gi];
+                vi[q] = __ldg(inv + gi);
+                vs[q] = __ldg(sup + gi);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int k = k0 + q * rstep;
+            if (k < nzi && c_ld < nc) {
+                st[k * W + c_ld] = vt[q];
+                si[k * W + c_ld] = vi[q];
+                ss[k * W + c_ld] = vs[q];
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int run = (nzi + 31) / 32;
+    const int k0 = min(nzi, lane * run), k1 = min(nzi, k0 + run);
+    for (int c = warp; c < nc; c += nw) {
+        // forward: compose this lane's maps, scan, then the sequential steps
+        T A = T(1), B = T(0);
+        for (int k = k0; k < k1; ++k) {
+            const T iv = si[k * W + c];
+            const T a = k ? -cz * iv : T(0);
+            B = fma(a, B, st[k * W + c] * iv);
+            A = a * A;
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+            const T Ap = __shfl_up_sync(full, A, off), Bp = __shfl_up_sync(full, B, off);
+            if (lane >= off) {
+                B = fma(A, Bp, B);
+                A = A * Ap;
+            }
+        }
+        T d = __shfl_up_sync(full, B, 1);
+        if (lane == 0) d = T(0);
+        for (int k = k0; k < k1; ++k) {
+            const T iv = si[k * W + c];
+            d = (k ? fma(-cz, d, st[k * W + c]) : st[k * W + c]) * iv;
+            st[k * W + c] = d;
+        }
+        __syncwarp();
+        // backward: the same from the top plane down
+        A = T(1);
+        B = T(0);
+        for (int k = k1 - 1; k >= k0; --k) {
+            const T al = k == nzi - 1 ? T(0) : -ss[k * W + c];
+            B = fma(al, B, st[k * W + c]);
+            A = al * A;
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+            const T An = __shfl_down_sync(full, A, off), Bn = __shfl_down_sync(full, B, off);
+            if (lane + off < 32) {
+                B = fma(A, Bn, B);
+                A = A * An;
+            }
+        }
+        T x = __shfl_down_sync(full, B, 1);
+        if (lane == 31) x = T(0);
+        for (int k = k1 - 1; k >= k0; --k) {
+            x = k == nzi - 1 ? st[k * W + c] : fma(-ss[k * W + c], x, st[k * W + c]);
+            st[k * W + c] = x;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nzi * 32; e += blockDim.x) {
+        const int k = e >> 5, c = e & 31;
+        if (c < nc) t[k * stride + base + c] = st[k * W + c];
+    }
+}
+
+constexpr size_t SCAN_SMEM_MAX = 200 * 1024;
+template <typename T>
+size_t scan_smem_bytes(int nzi) { return size_t(3) * size_t(nzi) * 33 * sizeof(T); }
+
 // lower-boundary plane: that = rhat / (cx mu_x(m) + cy mu_y(n))
 template <typename T>
 __global__ void sep_divide_kernel(int nxi, int nyi, T cx, T cy, const T* __restrict__ mux, const T* __restrict__ muy,
@@ -224,7 +339,20 @@ void mode_solve(const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTable
                 const T* mufast, const T* muslow, bool ytrans, T* t, cudaStream_t st) {
     const int threads = nfast <= 64 ? 64 : 128;
     const dim3 grid((nfast + threads - 1) / threads, nslow);
-    if (dim == 3) {
+    // the scan costs about four times the arithmetic of the plain recurrence:
+    // FP32 levels only (in FP64 the plain recurrence is faster on this GPU)
+    if (dim == 3 && sizeof(T) == 4 && scan_smem_bytes<T>(g.nz - 2) <= SCAN_SMEM_MAX) {
+        static bool configured = false;   // per template instance
+        if (!configured) {
+            MHS_CUDA(cudaFuncSetAttribute(sep_scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(SCAN_SMEM_MAX)));
+            configured = true;
+        }
+        // a warp per mode of the block's 32
+        sep_scan_kernel<T><<<dim3((nfast + 31) / 32, nslow), 32 * std::min(32, nfast), scan_smem_bytes<T>(g.nz - 2),
+                             st>>>(
+            nfast, nslow, g.nz - 2, coef, static_cast<const T*>(tab.inv), static_cast<const T*>(tab.sup), t);
+    } else if (dim == 3) {
         sep_thomas_kernel<T><<<grid, threads, 0, st>>>(nfast, nslow, g.nz - 2, coef, static_cast<const T*>(tab.inv),
                                                       static_cast<const T*>(tab.sup), t);
     } else {
