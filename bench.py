@@ -368,7 +368,8 @@ def run_gpu(args):
 
 def run_op(args):
     """One finest-level operation of an interior hierarchy (the 129^3 workload's parameters on the grid
-    --grid, isotropic spacing), repeated; prints its mean device time."""
+    --grid, isotropic spacing), repeated; prints its mean device time.  `exact` is the separable solve of
+    the level (zero boundary values), the coarse-grid solve the V-cycles use on such a level."""
     import numpy as np
     import torch
     from paper_1307_6720_gb300 import mhs as M
@@ -386,7 +387,7 @@ def run_op(args):
     for field in (M.MHS_FIELD_U, M.MHS_FIELD_F, M.MHS_FIELD_R):
         M.mhs_level_write(h, 3, 0, field, prec, rng.standard_normal(shape))
     op = {"smooth": M.MHS_OP_SMOOTH, "residual": M.MHS_OP_RESIDUAL, "restrict": M.MHS_OP_RESTRICT,
-          "prolong": M.MHS_OP_PROLONG, "vcycle": M.MHS_OP_VCYCLE}[args.op]
+          "prolong": M.MHS_OP_PROLONG, "vcycle": M.MHS_OP_VCYCLE, "exact": M.MHS_OP_EXACT}[args.op]
     for _ in range(args.warmup):
         M.mhs_level_op(h, 3, 0, op, prec)
     torch.cuda.synchronize()
@@ -668,7 +669,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--light", action="store_true",
                     help="timed steps only (no CPU baseline, e2e, kernel timing or second mode): for launch lists")
-    ap.add_argument("--op", choices=["smooth", "residual", "restrict", "prolong", "vcycle"], default=None,
+    ap.add_argument("--op", choices=["smooth", "residual", "restrict", "prolong", "vcycle", "exact"], default=None,
                     help="repeat one finest-level operation of the interior hierarchy (--steps times) for kernel capture")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="precision of --op")
     ap.add_argument("--grid", type=int, nargs=3, default=[129, 129, 129], metavar=("NX", "NY", "NZ"),

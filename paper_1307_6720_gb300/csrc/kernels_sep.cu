@@ -387,12 +387,12 @@ void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, c
     if (tab.twx) {
         const int Lx = g.nx - 1, Ly = g.ny - 1;
         DstArgs<T> a{};
-        a.L = Lx; a.log2n = ilog2(2 * Lx); a.lines = nyi; a.planes = nzi; a.tw = tab.twx; a.scale = T(1);
+        a.L = Lx; a.log2n = ilog2(Lx); a.lines = nyi; a.planes = nzi; a.tw = tab.twx; a.scale = T(1);
         a.in = f + off; a.in_plane = sA; a.in_line = g.px;
         a.out = t1; a.out_plane = pl; a.out_line = 1; a.out_elem = nyi;
         launch_dst<T>(a, st);
         DstArgs<T> b{};
-        b.L = Ly; b.log2n = ilog2(2 * Ly); b.lines = nxi; b.planes = nzi; b.tw = tab.twy; b.scale = T(1);
+        b.L = Ly; b.log2n = ilog2(Ly); b.lines = nxi; b.planes = nzi; b.tw = tab.twy; b.scale = T(1);
         b.in = t1; b.in_plane = pl; b.in_line = nyi;
         b.out = t2; b.out_plane = pl; b.out_line = nyi; b.out_elem = 1;
         launch_dst<T>(b, st);

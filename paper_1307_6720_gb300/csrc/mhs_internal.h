@@ -277,7 +277,7 @@ void launch_sweep(const Geom& g, const PlaneCoef<T>* coef, const T* uin, const T
 // out + p out_plane + l out_line + m out_elem (out_elem = 1: lines; else transposed, out_line = 1)
 template <typename T>
 struct DstArgs {
-    int L = 0, log2n = 0, lines = 0, planes = 0, pairs = 0;
+    int L = 0, log2n = 0, lines = 0, planes = 0, pairs = 0;   // L = N (power of two), log2n = log2 L
     const T* in = nullptr;
     long long in_plane = 0, in_line = 0;
     T* out = nullptr;
