@@ -592,10 +592,15 @@ def serving_leg(M, requests=1000, load=0.8, inflight=16, budget_gb=64):
                                    mags[n][r % 4], TOL, M.MHS_MIXED, phi=bufs[0], Bx=bufs[1], By=bufs[2],
                                    Bz=bufs[3], p=bufs[4], rho=bufs[5])
 
+    def warm(srv):
+        # create the resident hierarchies (up to max_inflight per grid) and capture their graphs:
+        # three rounds of max_inflight requests in flight, untimed
+        for _ in range(3):
+            for t in [submit(srv, r) for r in range(min(requests, 3 * inflight))]:
+                M.mhs_server_wait(srv, t, 600.0)
+
     srv = M.mhs_server_create(budget_gb << 30, inflight)
-    # warm the resident hierarchies and capture the graphs
-    for r in range(min(requests, 24)):
-        M.mhs_server_wait(srv, submit(srv, r), 600.0)
+    warm(srv)
     t0 = time.perf_counter()
     tickets = [submit(srv, r) for r in range(requests)]
     for t in tickets:
@@ -604,8 +609,7 @@ def serving_leg(M, requests=1000, load=0.8, inflight=16, budget_gb=64):
     M.mhs_server_destroy(srv)
 
     srv = M.mhs_server_create(budget_gb << 30, inflight)
-    for r in range(min(requests, 24)):
-        M.mhs_server_wait(srv, submit(srv, r), 600.0)
+    warm(srv)
     rate = load * capacity
     arr = S.SplitMix64(42)
     t_next = time.perf_counter()

@@ -205,8 +205,7 @@ mhs_status mhs_set_options(mhs_handle h, const mhs_solver_opts* opts) {
         return fail(MHS_ERR_INVALID_ARG, "options out of range");
     fill_opts(&h->opts, opts);
     return guarded([&] {
-        mhs::invalidate_graphs(h);
-        mhs::choose_cuts(h);
+        mhs::choose_cuts(h);   // captured solves are cached per option set
         return MHS_OK;
     });
 }

@@ -199,6 +199,25 @@ struct TimedScope {
 
 }  // namespace mhs
 
+namespace mhs {
+// Everything a captured solve depends on besides device memory: the options
+// and the choices derived from them and from the problem.
+struct GraphKey {
+    int v[10];
+    bool operator==(const GraphKey& o) const {
+        for (int q = 0; q < 10; ++q)
+            if (v[q] != o.v[q]) return false;
+        return true;
+    }
+};
+struct CachedGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    long long count[4] = {};    // kernels per graph section (see build_graph)
+    unsigned long long used = 0;
+};
+}  // namespace mhs
+
 struct mhs_ctx {
     int nx, ny, nz;
     double Lx, Ly, Lz, alpha;
@@ -224,9 +243,12 @@ struct mhs_ctx {
     mhs::SolveCtl* ctl = nullptr;       // device control blocks [0] lower boundary, [1] interior
     mhs::SolveCtl* ctl_host = nullptr;  // pinned mirror
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;  // private streams for graph capture
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};             // captured solve per precision mode
-    long long gkey[2] = {-1, -1};                              // options the graph was captured with
-    long long gcount[2][4] = {};                               // kernels per graph section (see build_graph)
+    // captured solves per precision mode, one per option set (see graph_key in solver.cu), so that
+    // switching between option sets (e.g. the autotuner's per-class choices in a server) replays
+    // instead of recapturing; least recently used evicted beyond a few
+    std::vector<mhs::CachedGraph> graphs[2];
+    unsigned long long graph_clock = 0;
+    long long launched_count[4] = {};                          // kernels per section of the launched graph
     bool use_graphs = true;
     bool pending_graph = false;                                 // the enqueued solve is a graph launch
     cudaStream_t bstream = nullptr;                             // stream of this handle inside batched solves

@@ -162,8 +162,7 @@ void Server::start(const std::shared_ptr<Request>& q) {
     mhs_solver_opts tuned;
     if (tune_lookup(c, r.mode, &tuned) && std::memcmp(&tuned, &c->opts, sizeof tuned) != 0) {
         c->opts = tuned;
-        invalidate_graphs(c);
-        choose_cuts(c);
+        choose_cuts(c);   // the handle keeps a captured solve per option set
     }
     const Geom& g2 = c->h2.g[0];
     MHS_CUDA(cudaMemcpy2DAsync(c->bz, g2.px * sizeof(double), q->bz.data(), g2.nx * sizeof(double),

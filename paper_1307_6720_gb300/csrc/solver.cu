@@ -185,9 +185,9 @@ void create(mhs_ctx* c) {
 
 void invalidate_graphs(mhs_ctx* c) {
     for (int m = 0; m < 2; ++m) {
-        if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
-        c->gexec[m] = nullptr;
-        c->gkey[m] = -1;
+        for (CachedGraph& e : c->graphs[m])
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+        c->graphs[m].clear();
     }
 }
 
@@ -565,11 +565,17 @@ static void add_while(mhs_ctx* c, cudaGraphConditionalHandle hnd, F&& fn) {
     c->stream = outer;
 }
 
-static long long graph_key(mhs_ctx* c) {
-    return (long long)c->opts.nu1 | (long long)c->opts.nu2 << 8 | (long long)c->opts.inner_cycles << 16 |
-           (long long)(c->opts.flags & MHS_FLAG_WARM) << 24 | (long long)c->f_zero_finest << 25 |
-           (long long)use_zline(c) << 26 | (long long)(c->opts.flags & MHS_FLAG_SEPARABLE) << 27;
+// The options a captured solve is built from (sweeps, cut-offs, coarse solve,
+// thresholds, graph-relevant flags) and the derived choices (smoother, zero
+// finest right-hand side).  The tolerance and the cycle limit live in device
+// memory, not in the graph.
+static GraphKey graph_key(mhs_ctx* c) {
+    const int flags = c->opts.flags & ~(MHS_FLAG_NO_GRAPH | MHS_FLAG_ZLINE | MHS_FLAG_POINT | MHS_FLAG_BZ_MIMETIC);
+    return GraphKey{{c->opts.nu1, c->opts.nu2, c->opts.inner_cycles, flags, c->opts.cut64, c->opts.cut32,
+                     c->opts.fused_min, c->opts.sep_coarse, c->f_zero_finest ? 1 : 0, use_zline(c) ? 1 : 0}};
 }
+
+constexpr size_t GRAPH_CACHE = 8;   // captured solves kept per precision mode
 
 static void build_graph(mhs_ctx* c, int mode) {
     cudaStream_t user = c->stream;
@@ -599,13 +605,25 @@ static void build_graph(mhs_ctx* c, int mode) {
         epilogue(e3, c->h3);
         const long long l5 = launches();
         count_launches(-(l5 - l0));   // capture records kernels without running them
-        c->gcount[mode][0] = (l1 - l0) + (l3 - l2) + (l5 - l4);   // run once per solve
-        c->gcount[mode][1] = l2 - l1;                             // per lower-boundary cycle
-        c->gcount[mode][2] = 0;
-        c->gcount[mode][3] = l4 - l3;                             // per interior cycle
+        CachedGraph e;
+        e.count[0] = (l1 - l0) + (l3 - l2) + (l5 - l4);   // run once per solve
+        e.count[1] = l2 - l1;                             // per lower-boundary cycle
+        e.count[2] = 0;
+        e.count[3] = l4 - l3;                             // per interior cycle
         MHS_CUDA(cudaStreamEndCapture(c->stream, &graph));
-        MHS_CUDA(cudaGraphInstantiate(&c->gexec[mode], graph, 0));
+        MHS_CUDA(cudaGraphInstantiate(&e.exec, graph, 0));
         cudaGraphDestroy(graph);
+        graph = nullptr;
+        e.key = graph_key(c);
+        std::vector<CachedGraph>& v = c->graphs[mode];
+        if (v.size() >= GRAPH_CACHE) {   // evict the least recently used
+            size_t lru = 0;
+            for (size_t q = 1; q < v.size(); ++q)
+                if (v[q].used < v[lru].used) lru = q;
+            cudaGraphExecDestroy(v[lru].exec);
+            v.erase(v.begin() + lru);
+        }
+        v.push_back(e);
     } catch (...) {
         cudaGraph_t junk;
         if (cudaStreamEndCapture(c->stream, &junk) == cudaSuccess && junk) cudaGraphDestroy(junk);
@@ -615,7 +633,15 @@ static void build_graph(mhs_ctx* c, int mode) {
         throw;
     }
     c->stream = user;
-    c->gkey[mode] = graph_key(c);
+}
+
+// the cached graph of the current options, captured on first use
+static CachedGraph& current_graph(mhs_ctx* c, int mode) {
+    const GraphKey k = graph_key(c);
+    for (CachedGraph& e : c->graphs[mode])
+        if (e.key == k) return e;
+    build_graph(c, mode);   // capture records work only; nothing runs until the launch
+    return c->graphs[mode].back();
 }
 
 static bool read_cont(mhs_ctx* c, int which) {
@@ -639,12 +665,10 @@ void solve_begin(mhs_ctx* c, double tol, int mode) {
     MHS_CUDA(cudaEventRecord(c->ev0, st));
     c->pending_graph = c->use_graphs && !c->timer.enabled && !(c->opts.flags & MHS_FLAG_NO_GRAPH);
     if (c->pending_graph) {
-        if (!c->gexec[mode] || c->gkey[mode] != graph_key(c)) {
-            if (c->gexec[mode]) cudaGraphExecDestroy(c->gexec[mode]);
-            c->gexec[mode] = nullptr;
-            build_graph(c, mode);   // capture records work only; nothing runs until the launch
-        }
-        MHS_CUDA(cudaGraphLaunch(c->gexec[mode], st));
+        CachedGraph& e = current_graph(c, mode);
+        e.used = ++c->graph_clock;
+        for (int q = 0; q < 4; ++q) c->launched_count[q] = e.count[q];
+        MHS_CUDA(cudaGraphLaunch(e.exec, st));
     } else {
         Enq e{c, mode, false, 0};
         prologue_2d(e);
@@ -668,7 +692,7 @@ mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     const SolveCtl& a = c->ctl_host[0];
     const SolveCtl& b = c->ctl_host[1];
     if (c->pending_graph) {
-        const long long* n = c->gcount[mode];
+        const long long* n = c->launched_count;
         count_launches(n[0] + a.cycles * n[1] + n[2] + b.cycles * n[3]);
     }
     if (info) {

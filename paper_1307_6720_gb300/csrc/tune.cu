@@ -50,7 +50,6 @@ bool same_opts(const mhs_solver_opts& a, const mhs_solver_opts& b) { return std:
 
 void apply_opts(mhs_ctx* c, const mhs_solver_opts& o) {
     c->opts = o;
-    invalidate_graphs(c);
     choose_cuts(c);
 }
 
