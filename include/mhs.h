@@ -215,11 +215,11 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * and the whole solve (lower-boundary and interior problems, both with the
  * full-multigrid first cycle and V-cycles until each instance reaches the
  * tolerance) is one captured CUDA graph whose loops run while any instance
- * still iterates; converged instances drop out of the launches.  A group's
- * V-cycles end in the one-CTA sub-cycle (the separable coarse-grid solve,
- * sep_coarse, is not used); otherwise each instance runs the operations of
- * its solo mhs_solve with the same block decomposition, so its P is bitwise
- * identical to solving it alone with sep_coarse = -1.
+ * still iterates; converged instances drop out of the launches.  Each
+ * instance runs the operations of its solo mhs_solve (its coarse-grid solve
+ * included: the separable solve's stages are grouped launches too) with
+ * arithmetic that does not depend on the decomposition, so its P is bitwise
+ * identical to solving it alone.
  *
  * The instances, ordered by decreasing cycle working set (every level's
  * arrays in the cycle precision, plus the double-float state in mixed

@@ -78,6 +78,57 @@ LevelArrays<float>& arr<float>(Hierarchy& H, int l) { return H.s[l]; }
 
 int top_level(int L, int cut) { return std::min(std::max(cut, 1), L - 1); }
 
+// level whose system the instance's cycles solve exactly (as in the solo
+// V-cycle), or -1
+template <typename T>
+int exact_level(const Hierarchy& H) { return sizeof(T) == 8 ? H.exact64 : H.exact32; }
+
+template <typename T>
+std::vector<GSepTable<T>>& exact_tables(GDim& D);
+template <>
+std::vector<GSepTable<float>>& exact_tables<float>(GDim& D) { return D.exact32; }
+template <>
+std::vector<GSepTable<double>>& exact_tables<double>(GDim& D) { return D.exact64; }
+
+// stage tables of the exact coarse-grid solves: items of stage s and kind k
+// share a launch; block shapes of the plain mode solves follow the launch's
+// thread count
+template <typename T>
+void upload_exact(GPart* G, GDim& D, std::vector<std::vector<GSepItem<T>>>& by_stage) {
+    std::vector<GSepTable<T>>& out = exact_tables<T>(D);
+    out.clear();
+    for (auto& items : by_stage) {
+        for (int kind = SEP_DST; kind <= SEP_DIVIDE; ++kind) {
+            std::vector<GSepItem<T>> v;
+            for (const GSepItem<T>& it : items)
+                if (it.st.kind == kind) v.push_back(it);
+            if (v.empty()) continue;
+            GSepTable<T> t;
+            t.kind = kind;
+            for (const GSepItem<T>& it : v) {
+                t.threads = std::max(t.threads, it.st.threads);
+                t.smem = std::max(t.smem, it.st.smem);
+            }
+            long long off = 0;
+            for (GSepItem<T>& it : v) {
+                if (kind == SEP_THOMAS || kind == SEP_DIVIDE)
+                    it.st.grid.x = unsigned((it.st.mode.nfast + t.threads - 1) / t.threads);
+                it.gx = int(it.st.grid.x);
+                it.gy = int(it.st.grid.y);
+                it.gz = int(it.st.grid.z);
+                it.first = int(off);
+                off += (long long)it.gx * it.gy * it.gz;
+            }
+            if (off > 0x7fffffffLL) throw Error(MHS_ERR_INVALID_ARG, "group: a grouped launch needs more than 2^31 blocks");
+            t.n = int(v.size());
+            t.blocks = int(off);
+            t.items = static_cast<GSepItem<T>*>(galloc(G, v.size() * sizeof(GSepItem<T>)));
+            MHS_CUDA(cudaMemcpy(t.items, v.data(), v.size() * sizeof(GSepItem<T>), cudaMemcpyHostToDevice));
+            out.push_back(t);
+        }
+    }
+}
+
 // Operations whose result does not depend on the block decomposition (every
 // node written by one thread from values the launch does not write: colour
 // passes, residuals without norms, transfers, elementwise updates) run in
@@ -107,6 +158,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     std::vector<GItem> sub, sub8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
         res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
     std::vector<SubParams<T>> params;
+    std::vector<std::vector<GSepItem<T>>> exact_items;   // per stage of the separable solves
     D.max_nu1 = D.max_nu2 = 0;
     D.max_top = -1;
     D.sub_smem = 0;
@@ -116,16 +168,18 @@ void build_dim(GPart* G, GDim& D, int dim) {
         SolveCtl* ctl = c->ctl + (dim == 3 ? 1 : 0);
         const int Lq = H.nlev();
         const int cut = dbl ? H.cut64 : H.cut32;
+        const int ex = exact_level<T>(H);
+        const int stop = ex >= 0 ? ex : cut;   // first level not cycled by per-level launches
         const bool fmg = !(c->opts.flags & MHS_FLAG_NO_FMG);
-        const int top = fmg ? top_level(Lq, cut) : -1;
+        const int top = fmg ? (ex >= 1 ? std::min(top_level(Lq, cut), ex) : top_level(Lq, cut)) : -1;
         const bool line = dim == 3 && use_zline(c);
         const int nu1 = c->opts.nu1, nu2 = c->opts.nu2;
         D.max_nu1 = std::max(D.max_nu1, nu1);
         D.max_nu2 = std::max(D.max_nu2, nu2);
         D.max_top = std::max(D.max_top, top);
         const bool fz = dbl && dim == 3 && c->f_zero_finest;   // f = 0 on the finest FP64 interior level
-        // ---- V-cycle levels above the sub-cycle ----
-        for (int l = 0; l < cut; ++l) {
+        // ---- V-cycle levels above the sub-cycle or the exact coarse-grid solve ----
+        for (int l = 0; l < stop; ++l) {
             LevelArrays<T>& A = arr<T>(H, l);
             LevelArrays<T>& C = arr<T>(H, l + 1);
             const Geom& g = H.g[l];
@@ -185,6 +239,20 @@ void build_dim(GPart* G, GDim& D, int dim) {
             pr.ia[1] = top;
             fmg_prol[l].push_back(pr);
         }
+        // ---- exact coarse-grid solve: the solo solve's stages ----
+        if (ex >= 0) {
+            std::vector<SepStage<T>> stages;
+            sep_exact_plan<T>(c, H, ex, stages);
+            if (exact_items.size() < stages.size()) exact_items.resize(stages.size());
+            for (size_t k = 0; k < stages.size(); ++k) {
+                GSepItem<T> it;
+                std::memset(&it, 0, sizeof it);
+                it.ctl = ctl;
+                it.top = top;
+                it.st = stages[k];
+                exact_items[k].push_back(it);
+            }
+        }
         // ---- sub-cycle parameters for every start level from the cut-off down ----
         GItem sb = item(q, dim3(1, 1, 1), H.g[std::min(cut, Lq - 1)], ctl);
         sb.ia[1] = top;
@@ -218,7 +286,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             D.sub_smem = std::max(D.sub_smem, p.smem_bytes);
             params.push_back(p);
         }
-        (rows == 8 ? sub8 : sub).push_back(sb);
+        if (ex < 0) (rows == 8 ? sub8 : sub).push_back(sb);
         // ---- prologue, cycle end, epilogue ----
         const Geom& g0 = H.g[0];
         auto words = [](size_t elems, size_t bytes) { return int(elems * bytes / 4); };
@@ -355,6 +423,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     up(fmg_prol, D.fmg_prol);
     D.sub = upload(G, sub);
     D.sub8 = upload(G, sub8);
+    upload_exact<T>(G, D, exact_items);
     D.params = galloc(G, params.size() * sizeof(SubParams<T>));
     MHS_CUDA(cudaMemcpy(D.params, params.data(), params.size() * sizeof(SubParams<T>), cudaMemcpyHostToDevice));
     D.zero_u = upload(G, zero_u);
@@ -408,6 +477,7 @@ void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
     }
     glaunch_subcycle<T>(D.sub, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 32, st);
     glaunch_subcycle<T>(D.sub8, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 8, st);
+    for (const GSepTable<T>& t : exact_tables<T>(D)) glaunch_sep<T>(t, fmg_step, gate, st);
     for (int l = D.L - 2; l >= s; --l) {
         glaunch_prolong<T>(D.prol[l], d3, fmg_step, gate, st);
         smooth(D.post_pt, D.post_ln, l, D.max_nu2);

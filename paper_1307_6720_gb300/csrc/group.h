@@ -68,6 +68,48 @@ void glaunch_any(SolveCtl* const* ctls, int n, cudaGraphConditionalHandle handle
 void glaunch_gather_ctl(SolveCtl* const* ctls, int n, SolveCtl* out, cudaStream_t st);
 void gsubcycle_prepare();
 
+// One instance's stage of a separable coarse-grid solve in a grouped launch
+// (the stage's arguments and its solo grid; `top` gates full-multigrid steps
+// like GItem::ia[1]).
+template <typename T>
+struct GSepItem {
+    int first;          // first block of the item in the grouped grid
+    int gx, gy, gz;     // the stage's own grid
+    SolveCtl* ctl;      // the instance's control block
+    int top;            // the instance's full-multigrid top level
+    SepStage<T> st;
+};
+template <typename T>
+struct GSepTable {
+    GSepItem<T>* items = nullptr;   // device
+    int n = 0, blocks = 0, threads = 0, kind = SEP_DST;
+    size_t smem = 0;                // largest dynamic shared memory of the items
+};
+template <typename T>
+void glaunch_sep(const GSepTable<T>& t, int fmg_step, int gate, cudaStream_t st);   // kernels_sep.cu
+template <typename T>
+void glaunch_dst(const GSepTable<T>& t, int fmg_step, int gate, cudaStream_t st);   // kernels_dst.cu
+
+#ifdef __CUDACC__
+// item of this block of a grouped launch (binary search over first-block
+// offsets), its local block index in lb; nullptr when the item is gated off
+template <typename I>
+__device__ __forceinline__ const I* glocate(const I* __restrict__ items, int n, int gate, int fmg_step, int& lb) {
+    int lo = 0, hi = n - 1;
+    const int blk = int(blockIdx.x);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const I& it = items[lo];
+    if (gate == G_ACTIVE && !it.ctl->cont) return nullptr;
+    if (fmg_step >= 0 && it.top < fmg_step) return nullptr;
+    lb = blk - it.first;
+    return &it;
+}
+#endif
+
 // tables of one problem (lower boundary or interior) of a group
 struct GDim {
     int dim = 3;
@@ -79,6 +121,10 @@ struct GDim {
     // coarse solution, per level, for the instances using it
     std::vector<GTable> fmg_restr, fmg_prol;
     GTable sub, sub8;                            // sub-cycle: one item per instance (32 or 8 rows of threads)
+    // separable coarse-grid solves of the instances that end their cycles in one:
+    // one table per (stage, kind), in launch order, in the cycle precision
+    std::vector<GSepTable<float>> exact32;
+    std::vector<GSepTable<double>> exact64;
     void* params = nullptr;                      // SubParams<T>[], device
     size_t sub_smem = 0;
     // once per solve

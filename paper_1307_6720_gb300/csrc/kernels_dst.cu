@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "group.h"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -148,8 +149,10 @@ __host__ __device__ inline int pair_stride(int F) {
     return padded | 1;
 }
 
+// block (bx, by) = (line block, plane) of the transform a; every thread of
+// the block calls it
 template <typename T>
-__global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
+__device__ __forceinline__ void dst_body(const DstArgs<T>& a, int bx, int by) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char dst_smem[];
     constexpr bool HALF = sizeof(T) == 8;              // half-length form (FP64) or odd extensions (FP32)
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
     C* z = reinterpret_cast<C*>(dst_smem);            // P pairs, PS points apart
     C* tw = z + P * PS;                                // twiddle table, L entries
     T* ob = reinterpret_cast<T*>(tw + a.L);            // results: 2P lines of N - 1
-    const int plane = blockIdx.y;
-    const int line0 = blockIdx.x * 2 * P;             // first line of the block in its plane
+    const int plane = by;
+    const int line0 = bx * 2 * P;                     // first line of the block in its plane
     const int nl = min(2 * P, a.lines - line0);       // lines of the block
     const T* in = a.in + plane * a.in_plane + (long long)line0 * a.in_line;
     const C* twg = static_cast<const C*>(a.tw);
@@ -342,6 +345,20 @@ __global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) dst_kernel(DstArgs<T> a) {
+    dst_body(a, int(blockIdx.x), int(blockIdx.y));
+}
+
+// one stage of every item's separable solve (grouped launch)
+template <typename T>
+__global__ void __launch_bounds__(256) g_dst_kernel(const GSepItem<T>* items, int n, int fmg_step, int gate) {
+    int lb;
+    const GSepItem<T>* it = glocate(items, n, gate, fmg_step, lb);
+    if (!it) return;
+    dst_body(it->st.dst, lb % it->gx, lb / it->gx);
+}
+
 }  // namespace
 
 // shared memory of a block: P pairs of FFT points (N in FP64, 2N in FP32)
@@ -372,7 +389,7 @@ int dst_pairs(int L) {
 constexpr size_t DST_SMEM_MAX = 227 * 1024;
 
 template <typename T>
-void launch_dst(DstArgs<T> a, cudaStream_t st) {
+void dst_shape(DstArgs<T>& a, dim3& grid, int& threads, size_t& smem) {
     a.pairs = dst_pairs<T>(a.L);
     // small transforms (coarse levels): fewer pairs per block, so that the
     // blocks cover every SM about twice
@@ -380,16 +397,34 @@ void launch_dst(DstArgs<T> a, cudaStream_t st) {
     while (a.pairs > 2 && blocks(a.pairs) < 2 * 152) a.pairs >>= 1;
     // one thread per radix-8 unit of the block's pairs, 64 .. 256
     const int units = a.pairs * std::max(1, fft_length<T>(a.L) / 8);
-    const int threads = std::min(256, std::max(64, (units + 31) / 32 * 32));
-    const size_t smem = dst_smem_bytes<T>(a.L, a.pairs);
+    threads = std::min(256, std::max(64, (units + 31) / 32 * 32));
+    smem = dst_smem_bytes<T>(a.L, a.pairs);
     if (smem > DST_SMEM_MAX) throw Error(MHS_ERR_INVALID_ARG, "sine transform lines too long for shared memory");
+    grid = dim3((a.lines + 2 * a.pairs - 1) / (2 * a.pairs), a.planes);
+}
+
+template <typename T>
+void launch_dst_stage(const SepStage<T>& s, cudaStream_t st) {
     static bool configured = false;   // per template instance
     if (!configured) {
         MHS_CUDA(cudaFuncSetAttribute(dst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(DST_SMEM_MAX)));
         configured = true;
     }
-    const dim3 grid((a.lines + 2 * a.pairs - 1) / (2 * a.pairs), a.planes);
-    dst_kernel<T><<<grid, threads, smem, st>>>(a);
+    dst_kernel<T><<<s.grid, s.threads, s.smem, st>>>(s.dst);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void glaunch_dst(const GSepTable<T>& t, int fmg_step, int gate, cudaStream_t st) {
+    if (t.n == 0) return;
+    static bool configured = false;
+    if (!configured) {
+        MHS_CUDA(
+            cudaFuncSetAttribute(g_dst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(DST_SMEM_MAX)));
+        configured = true;
+    }
+    g_dst_kernel<T><<<t.blocks, t.threads, t.smem, st>>>(t.items, t.n, fmg_step, gate);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
@@ -409,8 +444,12 @@ void* make_twiddles(int L) {
     return p;
 }
 
-template void launch_dst<float>(DstArgs<float>, cudaStream_t);
-template void launch_dst<double>(DstArgs<double>, cudaStream_t);
+template void dst_shape<float>(DstArgs<float>&, dim3&, int&, size_t&);
+template void dst_shape<double>(DstArgs<double>&, dim3&, int&, size_t&);
+template void launch_dst_stage<float>(const SepStage<float>&, cudaStream_t);
+template void launch_dst_stage<double>(const SepStage<double>&, cudaStream_t);
+template void glaunch_dst<float>(const GSepTable<float>&, int, int, cudaStream_t);
+template void glaunch_dst<double>(const GSepTable<double>&, int, int, cudaStream_t);
 template void* make_twiddles<float>(int);
 template void* make_twiddles<double>(int);
 

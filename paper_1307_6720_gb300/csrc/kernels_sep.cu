@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "group.h"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -31,32 +32,19 @@ namespace mhs {
 
 namespace {
 
-// C_b = scale * A_b * B_b (+ C_b with accumulate) for b < batch, row-major with leading dimensions
-// and batch strides (0: shared by the batch).  64 x 64 output tile per block
-// of 256 threads, 4 x 4 outputs per thread (rows ty + 16 r, columns tx + 16 c),
-// K staged through shared memory 16 at a time.
-template <typename T>
-struct GemmArgs {
-    int M, N, K;
-    const T* A;
-    long long lda, sA;
-    const T* B;
-    long long ldb, sB;
-    T* C;
-    long long ldc, sC;
-    T scale;
-    int accumulate;
-};
-
+// C_b = scale A_b B_b (+ C_b): 64 x 64 output tile per block of 256 threads,
+// 4 x 4 outputs per thread (rows ty + 16 r, columns tx + 16 c), K staged
+// through shared memory 16 at a time; block (bx, by, bz) = (column tile, row
+// tile, batch).
 constexpr int TM = 64, TN = 64, TK = 16;
 
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs<T> g) {
+__device__ __forceinline__ void gemm_body(const GemmArgs<T>& g, int bx, int by, int bz) {
     __shared__ T As[TK][TM + 4];
     __shared__ T Bs[TK][TN + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
-    const long long b = blockIdx.z;
+    const int row0 = by * TM, col0 = bx * TN;
+    const long long b = bz;
     const T* A = g.A + b * g.sA;
     const T* B = g.B + b * g.sB;
     T* C = g.C + b * g.sC;
@@ -105,11 +93,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs<T> g) {
 }
 
 template <typename T>
-void gemm(const GemmArgs<T>& g, int batch, cudaStream_t st) {
-    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, batch);
-    gemm_kernel<T><<<grid, 256, 0, st>>>(g);
-    count_launches(1);
-    MHS_CUDA(cudaGetLastError());
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs<T> g) {
+    gemm_body(g, int(blockIdx.x), int(blockIdx.y), int(blockIdx.z));
 }
 
 // Elimination factors of the mode systems of one 3D level, one thread per
@@ -153,17 +138,17 @@ __global__ void sep_pivot_kernel(int nfast, int nslow, int nzi, int nodes_fast, 
 // so U memory round trips overlap (the factor tables through the read-only
 // path); the recursion is an FMA and a multiply per plane.
 template <typename T>
-__global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef<T>* __restrict__ coef,
-                                  const T* __restrict__ inv, const T* __restrict__ sup, T* __restrict__ t) {
+__device__ __forceinline__ void thomas_body(const ModeArgs<T>& a, int bx, int by) {
     constexpr int U = 16;
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
-    if (m >= nfast) return;
-    const size_t stride = size_t(nfast) * nslow, o = size_t(n) * nfast + m;
-    T* tc = t + o;
-    const T* ic = inv + o;
-    const T* sc = sup + o;
-    const T cz = coef[1].cz;
+    const int m = bx * blockDim.x + threadIdx.x;
+    const int n = by;
+    if (m >= a.nfast) return;
+    const int nzi = a.nzi;
+    const size_t stride = size_t(a.nfast) * a.nslow, o = size_t(n) * a.nfast + m;
+    T* tc = a.t + o;
+    const T* ic = a.inv + o;
+    const T* sc = a.sup + o;
+    const T cz = a.coef[1].cz;
     T dp = T(0);
     for (int k0 = 0; k0 < nzi; k0 += U) {
         T rhs[U], iv[U];
@@ -200,6 +185,11 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
     }
 }
 
+template <typename T>
+__global__ void sep_thomas_kernel(ModeArgs<T> a) {
+    thomas_body(a, int(blockIdx.x), int(blockIdx.y));
+}
+
 // The same mode systems with more parallelism, for levels whose planes fit
 // shared memory: a block takes 32 consecutive fast modes of one slow index,
 // stages their right-hand sides and factors for every plane through shared
@@ -212,19 +202,20 @@ __global__ void sep_thomas_kernel(int nfast, int nslow, int nzi, const PlaneCoef
 // scan of the composed maps (shuffles) gives each lane the value entering its
 // run, and the lane then repeats the sequential steps of its run from it.
 template <typename T>
-__global__ void __launch_bounds__(1024) sep_scan_kernel(int nfast, int nslow, int nzi,
-                                                       const PlaneCoef<T>* __restrict__ coef,
-                                                       const T* __restrict__ inv, const T* __restrict__ sup,
-                                                       T* __restrict__ t) {
+__device__ __forceinline__ void scan_body(const ModeArgs<T>& ma, int bx, int by) {
     extern __shared__ __align__(16) unsigned char scan_smem[];
+    const int nfast = ma.nfast, nslow = ma.nslow, nzi = ma.nzi;
+    const T* __restrict__ inv = ma.inv;
+    const T* __restrict__ sup = ma.sup;
+    T* __restrict__ t = ma.t;
     constexpr int W = 33;
     T* st = reinterpret_cast<T*>(scan_smem);   // [nzi][W]: right-hand sides, then solution
     T* si = st + size_t(nzi) * W;              // inverse pivots
     T* ss = si + size_t(nzi) * W;              // eliminated super-diagonals
-    const int m0 = blockIdx.x * 32, n = blockIdx.y;
+    const int m0 = bx * 32, n = by;
     const int nc = min(32, nfast - m0);
     const size_t stride = size_t(nfast) * nslow, base = size_t(n) * nfast + m0;
-    const T cz = coef[1].cz;
+    const T cz = ma.coef[1].cz;
     // rows in batches of R per thread, every load of a batch issued before its
     // values are stored (one memory round trip per batch instead of per row)
     constexpr int R = 8;
@@ -310,18 +301,40 @@ __global__ void __launch_bounds__(1024) sep_scan_kernel(int nfast, int nslow, in
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) sep_scan_kernel(ModeArgs<T> a) {
+    scan_body(a, int(blockIdx.x), int(blockIdx.y));
+}
+
 constexpr size_t SCAN_SMEM_MAX = 200 * 1024;
 template <typename T>
 size_t scan_smem_bytes(int nzi) { return size_t(3) * size_t(nzi) * 33 * sizeof(T); }
 
-// lower-boundary plane: that = rhat / (cx mu_x(m) + cy mu_y(n))
+// lower-boundary plane: that = rhat / (cf mu_fast(m) + cs mu_slow(n))
 template <typename T>
-__global__ void sep_divide_kernel(int nxi, int nyi, T cx, T cy, const T* __restrict__ mux, const T* __restrict__ muy,
-                                  T* __restrict__ t) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
-    if (m >= nxi) return;
-    t[size_t(n) * nxi + m] /= cx * mux[m] + cy * muy[n];
+__device__ __forceinline__ void divide_body(const ModeArgs<T>& a, int bx, int by) {
+    const int m = bx * blockDim.x + threadIdx.x;
+    const int n = by;
+    if (m >= a.nfast) return;
+    a.t[size_t(n) * a.nfast + m] /= a.cf * a.mufast[m] + a.cs * a.muslow[n];
+}
+
+template <typename T>
+__global__ void sep_divide_kernel(ModeArgs<T> a) {
+    divide_body(a, int(blockIdx.x), int(blockIdx.y));
+}
+
+// one stage of every item's separable solve (grouped launches)
+template <typename T, int KIND>
+__global__ void __launch_bounds__(1024) g_sep_kernel(const GSepItem<T>* items, int n, int fmg_step, int gate) {
+    int lb;
+    const GSepItem<T>* it = glocate(items, n, gate, fmg_step, lb);
+    if (!it) return;
+    const int bx = lb % it->gx, by = (lb / it->gx) % it->gy, bz = lb / (it->gx * it->gy);
+    if constexpr (KIND == SEP_GEMM) gemm_body(it->st.gemm, bx, by, bz);
+    else if constexpr (KIND == SEP_SCAN) scan_body(it->st.mode, bx, by);
+    else if constexpr (KIND == SEP_THOMAS) thomas_body(it->st.mode, bx, by);
+    else divide_body(it->st.mode, bx, by);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -331,51 +344,66 @@ int ilog2(int v) {
     return b;
 }
 
-// mode solves on the transformed data t (fast index nfast): tridiagonal
-// systems along z with the level's elimination factors (3D) or a division per
-// mode (2D)
+// the mode-solve stage on transformed data t (fast index nfast): tridiagonal
+// systems along z with the level's elimination factors (3D; a warp scan per
+// mode on FP32 levels whose planes fit shared memory, the plain recurrence
+// otherwise) or a division per mode (2D)
 template <typename T>
-void mode_solve(const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, int nfast, int nslow,
-                const T* mufast, const T* muslow, bool ytrans, T* t, cudaStream_t st) {
-    const int threads = nfast <= 64 ? 64 : 128;
-    const dim3 grid((nfast + threads - 1) / threads, nslow);
-    // the scan costs about four times the arithmetic of the plain recurrence:
-    // FP32 levels only (in FP64 the plain recurrence is faster on this GPU)
-    if (dim == 3 && sizeof(T) == 4 && scan_smem_bytes<T>(g.nz - 2) <= SCAN_SMEM_MAX) {
-        static bool configured = false;   // per template instance
-        if (!configured) {
-            MHS_CUDA(cudaFuncSetAttribute(sep_scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(SCAN_SMEM_MAX)));
-            configured = true;
+SepStage<T> mode_stage(const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, int nfast, int nslow,
+                       const T* mufast, const T* muslow, bool ytrans, T* t) {
+    SepStage<T> s;
+    ModeArgs<T>& m = s.mode;
+    m.nfast = nfast;
+    m.nslow = nslow;
+    m.nzi = dim == 3 ? g.nz - 2 : 1;
+    m.coef = coef;
+    m.t = t;
+    if (dim == 3) {
+        m.inv = static_cast<const T*>(tab.inv);
+        m.sup = static_cast<const T*>(tab.sup);
+        // the scan costs about four times the arithmetic of the plain
+        // recurrence: FP32 levels only (in FP64 the plain recurrence is faster)
+        if (sizeof(T) == 4 && scan_smem_bytes<T>(m.nzi) <= SCAN_SMEM_MAX) {
+            s.kind = SEP_SCAN;
+            s.threads = 32 * std::min(32, nfast);   // a warp per mode of the block's 32
+            s.grid = dim3((nfast + 31) / 32, nslow);
+            s.smem = scan_smem_bytes<T>(m.nzi);
+            return s;
         }
-        // a warp per mode of the block's 32
-        sep_scan_kernel<T><<<dim3((nfast + 31) / 32, nslow), 32 * std::min(32, nfast), scan_smem_bytes<T>(g.nz - 2),
-                             st>>>(
-            nfast, nslow, g.nz - 2, coef, static_cast<const T*>(tab.inv), static_cast<const T*>(tab.sup), t);
-    } else if (dim == 3) {
-        sep_thomas_kernel<T><<<grid, threads, 0, st>>>(nfast, nslow, g.nz - 2, coef, static_cast<const T*>(tab.inv),
-                                                      static_cast<const T*>(tab.sup), t);
+        s.kind = SEP_THOMAS;
     } else {
-        const T cf = T(1.0 / (ytrans ? g.hy * g.hy : g.hx * g.hx));
-        const T cs = T(1.0 / (ytrans ? g.hx * g.hx : g.hy * g.hy));
-        sep_divide_kernel<T><<<grid, threads, 0, st>>>(nfast, nslow, cf, cs, mufast, muslow, t);
+        s.kind = SEP_DIVIDE;
+        m.mufast = mufast;
+        m.muslow = muslow;
+        m.cf = T(1.0 / (ytrans ? g.hy * g.hy : g.hx * g.hx));
+        m.cs = T(1.0 / (ytrans ? g.hx * g.hx : g.hy * g.hy));
     }
-    count_launches(1);
-    MHS_CUDA(cudaGetLastError());
+    s.threads = nfast <= 64 ? 64 : 128;
+    s.grid = dim3((nfast + s.threads - 1) / s.threads, nslow);
+    return s;
 }
 
-// A e = f on one level, e = out (stored, or added with accumulate), f and out
-// pitched level arrays (interior read / written), t1 and t2 dense scratch of
-// the interior size (t2 may be the array of f).
+template <typename T>
+SepStage<T> gemm_stage(const GemmArgs<T>& g, int batch) {
+    SepStage<T> s;
+    s.kind = SEP_GEMM;
+    s.gemm = g;
+    s.threads = 256;
+    s.grid = dim3((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, batch);
+    return s;
+}
+
+// The stages of A e = f on one level, e = out (stored, or added with
+// accumulate), f and out pitched level arrays (interior read / written), t1
+// and t2 dense scratch of the interior size (t2 may be the array of f).
 // Fast transforms: x lines of f -> t1[k][m][j] (transposed), y lines ->
-// t2[k][m][n], mode solves, inverse y -> t1[k][j][m]
-// (transposed), inverse x -> out, scaled.
+// t2[k][m][n], mode solves, inverse y -> t1[k][j][m] (transposed), inverse
+// x -> out, scaled.
 // Dense transforms: t1[k][j][m] = sum_i f[k][j][i] Sx[m][i], t2[k][n][m] =
 // sum_j Sy[n][j] t1[k][j][m], mode solves, and back the same way.
 template <typename T>
-void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, const T* f,
-                 T* t1, T* t2, T* out, bool accumulate) {
-    cudaStream_t st = c->stream;
+void plan_level(const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, const T* f, T* t1, T* t2,
+                T* out, bool accumulate, std::vector<SepStage<T>>& stages) {
     const int nxi = g.nx - 2, nyi = g.ny - 2, nzi = dim == 3 ? g.nz - 2 : 1;
     if (nxi < 1 || nyi < 1 || nzi < 1) return;
     const long long pl = (long long)nxi * nyi;
@@ -385,35 +413,72 @@ void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, c
     const T* muy = static_cast<const T*>(tab.muy);
     const T scale = T((2.0 / (g.nx - 1)) * (2.0 / (g.ny - 1)));
     if (tab.twx) {
+        auto dst = [&](const DstArgs<T>& a) {
+            SepStage<T> s;
+            s.kind = SEP_DST;
+            s.dst = a;
+            dst_shape<T>(s.dst, s.grid, s.threads, s.smem);
+            stages.push_back(s);
+        };
         const int Lx = g.nx - 1, Ly = g.ny - 1;
         DstArgs<T> a{};
         a.L = Lx; a.log2n = ilog2(Lx); a.lines = nyi; a.planes = nzi; a.tw = tab.twx; a.scale = T(1);
         a.in = f + off; a.in_plane = sA; a.in_line = g.px;
         a.out = t1; a.out_plane = pl; a.out_line = 1; a.out_elem = nyi;
-        launch_dst<T>(a, st);
+        dst(a);
         DstArgs<T> b{};
         b.L = Ly; b.log2n = ilog2(Ly); b.lines = nxi; b.planes = nzi; b.tw = tab.twy; b.scale = T(1);
         b.in = t1; b.in_plane = pl; b.in_line = nyi;
         b.out = t2; b.out_plane = pl; b.out_line = nyi; b.out_elem = 1;
-        launch_dst<T>(b, st);
-        mode_solve<T>(g, dim, coef, tab, nyi, nxi, muy, mux, true, t2, st);
+        dst(b);
+        stages.push_back(mode_stage<T>(g, dim, coef, tab, nyi, nxi, muy, mux, true, t2));
         b.in = t2; b.out = t1; b.out_line = 1; b.out_elem = nxi;
-        launch_dst<T>(b, st);
+        dst(b);
         a.in = t1; a.in_plane = pl; a.in_line = nxi;
         a.out = out + off; a.out_plane = sA; a.out_line = g.px; a.out_elem = 1;
         a.scale = scale;
         a.accumulate = accumulate ? 1 : 0;
-        launch_dst<T>(a, st);
+        dst(a);
         return;
     }
     const T* Sx = static_cast<const T*>(tab.sx);
     const T* Sy = static_cast<const T*>(tab.sy);
-    gemm<T>(GemmArgs<T>{nyi, nxi, nxi, f + off, g.px, sA, Sx, nxi, 0, t1, nxi, pl, T(1), 0}, nzi, st);
-    gemm<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t1, nxi, pl, t2, nxi, pl, T(1), 0}, nzi, st);
-    mode_solve<T>(g, dim, coef, tab, nxi, nyi, mux, muy, false, t2, st);
-    gemm<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t2, nxi, pl, t1, nxi, pl, T(1), 0}, nzi, st);
-    gemm<T>(GemmArgs<T>{nyi, nxi, nxi, t1, nxi, pl, Sx, nxi, 0, out + off, g.px, sA, scale, accumulate ? 1 : 0}, nzi,
-            st);
+    stages.push_back(gemm_stage<T>(GemmArgs<T>{nyi, nxi, nxi, f + off, g.px, sA, Sx, nxi, 0, t1, nxi, pl, T(1), 0}, nzi));
+    stages.push_back(gemm_stage<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t1, nxi, pl, t2, nxi, pl, T(1), 0}, nzi));
+    stages.push_back(mode_stage<T>(g, dim, coef, tab, nxi, nyi, mux, muy, false, t2));
+    stages.push_back(gemm_stage<T>(GemmArgs<T>{nyi, nxi, nyi, Sy, nyi, 0, t2, nxi, pl, t1, nxi, pl, T(1), 0}, nzi));
+    stages.push_back(gemm_stage<T>(
+        GemmArgs<T>{nyi, nxi, nxi, t1, nxi, pl, Sx, nxi, 0, out + off, g.px, sA, scale, accumulate ? 1 : 0}, nzi));
+}
+
+template <typename T>
+void launch_stage(const SepStage<T>& s, cudaStream_t st) {
+    switch (s.kind) {
+    case SEP_DST: launch_dst_stage<T>(s, st); return;
+    case SEP_GEMM: gemm_kernel<T><<<s.grid, s.threads, 0, st>>>(s.gemm); break;
+    case SEP_SCAN: {
+        static bool configured = false;   // per template instance
+        if (!configured) {
+            MHS_CUDA(cudaFuncSetAttribute(sep_scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(SCAN_SMEM_MAX)));
+            configured = true;
+        }
+        sep_scan_kernel<T><<<s.grid, s.threads, s.smem, st>>>(s.mode);
+        break;
+    }
+    case SEP_THOMAS: sep_thomas_kernel<T><<<s.grid, s.threads, 0, st>>>(s.mode); break;
+    default: sep_divide_kernel<T><<<s.grid, s.threads, 0, st>>>(s.mode); break;
+    }
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, const T* f,
+                 T* t1, T* t2, T* out, bool accumulate) {
+    std::vector<SepStage<T>> stages;
+    plan_level<T>(g, dim, coef, tab, f, t1, t2, out, accumulate, stages);
+    for (const SepStage<T>& s : stages) launch_stage<T>(s, c->stream);
 }
 
 template <typename T>
@@ -527,6 +592,36 @@ void sep_exact(mhs_ctx* c, Hierarchy& H, int l) {
     level_solve<T>(c, H.g[l], H.dim, A.coef, tables<T>(H, l), A.f, A.r, A.t, A.u, false);
 }
 
+template <typename T>
+void sep_exact_plan(mhs_ctx* c, Hierarchy& H, int l, std::vector<SepStage<T>>& stages) {
+    (void)c;
+    LevelArrays<T>& A = arrays_of<T>(H, l);
+    plan_level<T>(H.g[l], H.dim, A.coef, tables<T>(H, l), A.f, A.r, A.t, A.u, false, stages);
+}
+
+template <typename T>
+void glaunch_sep(const GSepTable<T>& t, int fmg_step, int gate, cudaStream_t st) {
+    if (t.n == 0) return;
+    switch (t.kind) {
+    case SEP_DST: glaunch_dst<T>(t, fmg_step, gate, st); return;
+    case SEP_GEMM: g_sep_kernel<T, SEP_GEMM><<<t.blocks, t.threads, 0, st>>>(t.items, t.n, fmg_step, gate); break;
+    case SEP_SCAN: {
+        static bool configured = false;
+        if (!configured) {
+            MHS_CUDA(cudaFuncSetAttribute(g_sep_kernel<T, SEP_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(SCAN_SMEM_MAX)));
+            configured = true;
+        }
+        g_sep_kernel<T, SEP_SCAN><<<t.blocks, t.threads, t.smem, st>>>(t.items, t.n, fmg_step, gate);
+        break;
+    }
+    case SEP_THOMAS: g_sep_kernel<T, SEP_THOMAS><<<t.blocks, t.threads, 0, st>>>(t.items, t.n, fmg_step, gate); break;
+    default: g_sep_kernel<T, SEP_DIVIDE><<<t.blocks, t.threads, 0, st>>>(t.items, t.n, fmg_step, gate); break;
+    }
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
 void sep_prepare(mhs_ctx* c, int mode) {
     for (Hierarchy* H : {&c->h3, &c->h2}) {
         if (mode == MHS_MIXED) sep_tables<float>(c, *H, 0);
@@ -551,5 +646,9 @@ template void sep_tables<double>(mhs_ctx*, Hierarchy&, int);
 template void sep_tables<float>(mhs_ctx*, Hierarchy&, int);
 template void sep_exact<double>(mhs_ctx*, Hierarchy&, int);
 template void sep_exact<float>(mhs_ctx*, Hierarchy&, int);
+template void sep_exact_plan<double>(mhs_ctx*, Hierarchy&, int, std::vector<SepStage<double>>&);
+template void sep_exact_plan<float>(mhs_ctx*, Hierarchy&, int, std::vector<SepStage<float>>&);
+template void glaunch_sep<double>(const GSepTable<double>&, int, int, cudaStream_t);
+template void glaunch_sep<float>(const GSepTable<float>&, int, int, cudaStream_t);
 
 }  // namespace mhs

@@ -110,7 +110,9 @@ struct Hierarchy {
     std::vector<LevelArrays<double>> d;   // FP64 arrays
     std::vector<LevelArrays<float>> s;    // FP32 arrays
     int cut64 = 0, cut32 = 0;             // first level handled by the one-CTA sub-cycle (per precision)
-    int exact = -1;                       // level solved exactly by the separable solver in V-cycles (-1: none)
+    // level whose system the V-cycles of each precision solve exactly by the separable
+    // solver: the chosen level when the cycle reaches it before the sub-cycle cut-off, else -1
+    int exact64 = -1, exact32 = -1;
     std::vector<SepTables> sep64, sep32;  // separable-solver tables per level (built on demand)
     DFState df;                           // finest-level double-float state (mixed mode)
     // TMA plane maps of the FP32 arrays u, t, f per level (3D levels; see kernels_tma.cu)
@@ -309,9 +311,53 @@ struct DstArgs {
     const void* tw = nullptr;   // complex twiddles e^{-2 pi i q / (2L)}, q < L
 };
 template <typename T>
-void launch_dst(DstArgs<T> a, cudaStream_t st);
-template <typename T>
 void* make_twiddles(int L);
+
+// ---- stages of one separable solve (kernels_sep.cu, kernels_dst.cu) ----
+// C_b = scale A_b B_b (+ C_b with accumulate), b < batch, row-major with
+// leading dimensions and batch strides (0: shared by the batch)
+template <typename T>
+struct GemmArgs {
+    int M = 0, N = 0, K = 0;
+    const T* A = nullptr;
+    long long lda = 0, sA = 0;
+    const T* B = nullptr;
+    long long ldb = 0, sB = 0;
+    T* C = nullptr;
+    long long ldc = 0, sC = 0;
+    T scale = T(1);
+    int accumulate = 0;
+};
+// mode systems on transformed data t[k][slow][fast] (k < nzi; nzi = 1: the
+// lower-boundary division by cf mu_fast + cs mu_slow)
+template <typename T>
+struct ModeArgs {
+    int nfast = 0, nslow = 0, nzi = 0;
+    const PlaneCoef<T>* coef = nullptr;
+    const T* inv = nullptr;     // elimination factors (3D)
+    const T* sup = nullptr;
+    T* t = nullptr;
+    const T* mufast = nullptr;  // mode eigenvalues (2D)
+    const T* muslow = nullptr;
+    T cf = T(0), cs = T(0);
+};
+enum SepKind { SEP_DST = 0, SEP_GEMM = 1, SEP_SCAN = 2, SEP_THOMAS = 3, SEP_DIVIDE = 4 };
+// one kernel launch of a separable solve with its launch shape
+template <typename T>
+struct SepStage {
+    int kind = SEP_DST;
+    dim3 grid;
+    int threads = 0;
+    size_t smem = 0;
+    DstArgs<T> dst;
+    GemmArgs<T> gemm;
+    ModeArgs<T> mode;
+};
+// launch shape of a sine-transform stage (sets a.pairs)
+template <typename T>
+void dst_shape(DstArgs<T>& a, dim3& grid, int& threads, size_t& smem);
+template <typename T>
+void launch_dst_stage(const SepStage<T>& s, cudaStream_t st);
 
 // ---- zebra z-line Gauss-Seidel sweep, both colours (kernels_line.cu); scratch holds g.n elements ----
 template <typename T>

@@ -135,11 +135,12 @@ void choose_cuts(mhs_ctx* c) {
     for (Hierarchy* H : {&c->h3, &c->h2}) {
         H->cut64 = choose_cut(*H, sizeof(double), size_t(c->opts.cut64));
         H->cut32 = choose_cut(*H, sizeof(float), size_t(c->opts.cut32));
-        H->exact = choose_exact(*H, c->opts.sep_coarse);
-        if (H->exact >= 0) {   // tables now: graph capture must not allocate
-            sep_tables<double>(c, *H, H->exact);
-            sep_tables<float>(c, *H, H->exact);
-        }
+        const int e = choose_exact(*H, c->opts.sep_coarse);
+        H->exact64 = e >= 1 && e <= H->cut64 ? e : -1;
+        H->exact32 = e >= 1 && e <= H->cut32 ? e : -1;
+        // tables now: graph capture must not allocate
+        if (H->exact64 >= 0) sep_tables<double>(c, *H, H->exact64);
+        if (H->exact32 >= 0) sep_tables<float>(c, *H, H->exact32);
     }
 }
 
@@ -219,6 +220,8 @@ LevelArrays<float>& arrays<float>(Hierarchy& H, int l) { return H.s[l]; }
 
 template <typename T>
 static int cut_of(const Hierarchy& H) { return sizeof(T) == 8 ? H.cut64 : H.cut32; }
+template <typename T>
+static int exact_of(const Hierarchy& H) { return sizeof(T) == 8 ? H.exact64 : H.exact32; }
 
 // V-cycle from level l down; levels at or below the cut-off run in one CTA.
 template <typename T>
@@ -294,7 +297,7 @@ static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fi
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
-    if (l == H.exact) {
+    if (l == exact_of<T>(H)) {
         // coarse-grid solve: A u = f exactly (u's interior overwritten; the
         // correction's boundary values are zero on coarse levels)
         const Geom& g = H.g[l];
@@ -369,7 +372,7 @@ void fmg(mhs_ctx* c, Hierarchy& H, const T* r0) {
     cudaStream_t st = c->stream;
     launch_restrict<T>(H.g[0], H.g[1], H.dim, r0, arrays<T>(H, 1).f, arrays<T>(H, 1).u, st);
     int top = std::min(std::max(cut_of<T>(H), 1), L - 1);
-    if (H.exact >= 1) top = std::min(top, H.exact);
+    if (exact_of<T>(H) >= 1) top = std::min(top, exact_of<T>(H));
     for (int l = 1; l < top; ++l)
         launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, arrays<T>(H, l).f, arrays<T>(H, l + 1).f,
                            arrays<T>(H, l + 1).u, st);

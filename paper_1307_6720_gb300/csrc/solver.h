@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cmath>
+#include <vector>
 
 #include "mhs_internal.h"
 
@@ -66,6 +67,8 @@ void sep_tables(mhs_ctx* c, Hierarchy& H, int l);   // build level l's tables on
 template <typename T>
 void sep_exact(mhs_ctx* c, Hierarchy& H, int l);    // u = A^{-1} f on level l (interior; r, t scratch)
 void sep_refresh(mhs_ctx* c, Hierarchy& H);         // recompute the pivots of every built table (new coefficients)
+template <typename T>
+void sep_exact_plan(mhs_ctx* c, Hierarchy& H, int l, std::vector<SepStage<T>>& stages);   // sep_exact's launches
 void sep_prepare(mhs_ctx* c, int mode);             // finest-level tables of both hierarchies for a solve mode
 void sep_solve(mhs_ctx* c, Hierarchy& H);           // mixed mode: FP32 e = A^{-1} f on the finest level
 bool sep_fp64_available(const mhs_ctx* c);          // FP64 direct solves: sep_level_ok of the finest grid

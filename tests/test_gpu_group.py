@@ -20,7 +20,9 @@ def M():
 
 
 def _members(M, seed=0):
-    """Uneven grids, xi families and options, one anisotropic (z-line) member."""
+    """Uneven grids, xi families and options: one anisotropic (z-line) member, cycles
+    ending in the separable coarse-grid solve (fast and dense transforms) or in
+    the one-CTA sub-cycle."""
     specs = [
         (S.problem(33, 33, 33, alpha=0.3, xi_kind=1, xi_a=0.5, xi_kappa=1.0), {}),
         (S.problem(65, 65, 65, alpha=0.5, xi_kind=1, xi_a=0.5, xi_kappa=1.0), {}),
@@ -31,13 +33,15 @@ def _members(M, seed=0):
         (S.problem(65, 33, 33, Ly=0.5, Lz=0.5, alpha=0.6, xi_kind=1, xi_a=0.5, xi_kappa=1.0), dict(nu1=1, nu2=1)),
         (S.problem(65, 65, 33, Lz=0.5, alpha=0.5, xi_kind=1, xi_a=0.4, xi_kappa=1.0), dict(cut64=40, cut32=40)),
         (S.problem(5, 5, 5, alpha=0.2), {}),
+        (S.problem(65, 65, 65, alpha=0.4, xi_kind=1, xi_a=0.5, xi_kappa=1.0), dict(sep_coarse=-1)),   # sub-cycle
+        (S.problem(25, 25, 13, Lz=0.5, alpha=0.3, xi_kind=1, xi_a=0.4, xi_kappa=1.0), {}),   # dense transforms
     ]
     hs, prs, bzs = [], [], []
     for q, (pr, opts) in enumerate(specs):
         h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"],
                          M.xi_params(pr["xi_kind"], pr["xi_a"], pr["xi_kappa"], pr["xi_b"], pr["xi_omega"]))
-        # a group's cycles end in the one-CTA sub-cycle: its solo twin does the same
-        M.mhs_set_options(h, sep_coarse=-1, **opts)
+        if opts:
+            M.mhs_set_options(h, **opts)
         bz = S.magnetogram_random(pr["nx"], pr["ny"], pr["Lx"], pr["Ly"], seed=100 * seed + q)
         M.mhs_set_lower_bz(h, bz)
         hs.append(h)
@@ -102,7 +106,7 @@ def test_group_repeated_solves_new_bz_and_exact_solution(M):
 
 def test_group_per_instance_status_and_errors(M):
     hs, prs, _ = _members(M)
-    M.mhs_set_options(hs[1], max_cycles=1, flags=M.MHS_FLAG_NO_FMG, sep_coarse=-1)
+    M.mhs_set_options(hs[1], max_cycles=1, flags=M.MHS_FLAG_NO_FMG)
     g = M.mhs_group_create(hs, M.MHS_MIXED)
     infos, sts = M.mhs_group_solve(g, len(hs), 1e-10)
     assert sts[1] == M.MHS_ERR_NO_CONVERGENCE

@@ -472,3 +472,30 @@ def test_exact_coarse_grid_solve(M, case, mode):
         _compare(got, want, 1e-10 if mode == 0 else 1e-8)
     assert info_e["cycles_3d"] <= info_s["cycles_3d"], (info_e, info_s)
     assert info_e["cycles_2d"] <= info_s["cycles_2d"] + 1, (info_e, info_s)
+
+
+def test_captured_solves_cached_per_option_set(M):
+    """Switching options replays the solve captured for each option set:
+    results for an option set are bitwise the same before and after other
+    option sets ran, also once more sets ran than the cache keeps (8)."""
+    pr, bz = S.linear_mhs(33, seed=81)
+    h = M.mhs_create(33, 33, 33, 1.0, 1.0, 1.0, pr["alpha"], _xi(M, pr))
+    M.mhs_set_lower_bz(h, bz)
+    sets = [dict(), dict(nu1=1, nu2=1), dict(sep_coarse=-1), dict(cut64=40, cut32=40), dict(nu1=3, nu2=1),
+            dict(flags=M.MHS_FLAG_NO_FMG), dict(sep_coarse=1000), dict(nu1=1, nu2=2), dict(nu1=2, nu2=1),
+            dict(flags=M.MHS_FLAG_ZLINE)]
+
+    def run(opts, mode):
+        M.mhs_set_options(h, **opts)
+        info = M.mhs_solve(h, 1e-10, mode)
+        phi = np.zeros((33, 33, 33))
+        M.mhs_get_phi(h, phi)
+        return info, phi
+
+    for mode in (0, 1):
+        first = [run(o, mode) for o in sets]
+        again = [run(o, mode) for o in reversed(sets)][::-1]
+        for (ia, pa), (ib, pb), o in zip(first, again, sets):
+            assert np.array_equal(pa, pb), o
+            assert ia["cycles_3d"] == ib["cycles_3d"] and ia["rel_res_3d"] == ib["rel_res_3d"], o
+    M.mhs_destroy(h)
