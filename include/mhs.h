@@ -108,7 +108,7 @@ typedef struct {
     int cut32;           /* same for FP32 levels [4000] */
     int fused_min;       /* FP32 3D levels with at least this many interior nodes use the fused, TMA-staged
                             red-black sweep (one pass per sweep, HBM-bound); smaller, cache-resident levels use the
-                            two colour passes, which have less latency [32000000] */
+                            two colour passes, which have less latency [12000000] */
     int sep_coarse;      /* coarse-grid solve of the V-cycles: the first level below the finest with at most this
                             many interior nodes, whose sine transforms are fast (nx - 1 and ny - 1 powers of two)
                             or short (nx, ny <= 66), is solved exactly by the separable solver (sine transforms

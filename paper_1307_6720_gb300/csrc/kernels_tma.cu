@@ -2,15 +2,21 @@
 //
 // Same sweep as kernels_sweep.cu (out of place, both colours, z-marching
 // over a chunk of planes per CTA), but the planes of the old iterate and of f
-// arrive by TMA: one thread issues cp.async.bulk.tensor loads of a
-// (TX+8) x (TY+4) box per plane three z-steps ahead, into a four-slot
-// shared-memory ring, and each stage completes on an mbarrier (transaction
-// bytes).  The loads of later planes are therefore in flight while the
-// current plane is computed, which hides L2/HBM latency.
+// arrive by TMA: one thread issues cp.async.bulk.tensor loads of a 72 x 12
+// box per plane three z-steps ahead, into a four-slot shared-memory ring, and
+// each stage completes on an mbarrier (transaction bytes).  The loads of later
+// planes are therefore in flight while the current plane is computed, which
+// hides L2/HBM latency.
+//
+// A CTA of 32 x 8 threads owns a 64 x 8 tile; every thread takes an x-pair
+// of nodes, of which exactly one is red and one black, so all lanes do the
+// same work: per z-step it forms the red value of plane k+1 (tile plus a
+// 1-node halo: 33 pairs x 10 rows over the 256 threads), then the black value
+// of plane k and writes both nodes of its pair.
 //
 // TMA rules honoured: the box's innermost start coordinate is a multiple of 4
-// floats (16 bytes; the box starts 4 nodes left of the tile's halo-2 origin
-// and is 40 floats wide); loads may start at negative coordinates (zero
+// floats (16 bytes: the box starts at x = 64 bx - 4, 5 nodes left of the
+// tile) and 72 floats wide; loads may start at negative coordinates (zero
 // fill); every shared-memory destination is 128-byte aligned.  Every mbarrier
 // wait has an iteration limit: on expiry the CTA records an error flag,
 // waits (again bounded) for its own copies in flight, and exits.
@@ -23,14 +29,15 @@ namespace mhs {
 
 namespace {
 
-constexpr int TX = 32, TY = 8;
-constexpr int BW = TX + 8, BH = TY + 4;   // TMA box: 40 x 12 floats (row of 160 bytes)
-constexpr int RX = TX + 2, RY = TY + 2;   // new red values: 1-node halo
+constexpr int TX = 64, TY = 8;            // tile of outputs; threads 32 x 8, an x-pair each
+constexpr int BW = 72, BH = 12;           // TMA box (floats): x from 64 bx - 4, y from y0 - 2
+constexpr int RX = TX + 2, RY = TY + 2;   // red values: tile + 1-node halo
+constexpr int RPAIRS = RX / 2;            // x-pairs per red row
 constexpr unsigned BOX_BYTES = BW * BH * 4;
 constexpr int WAIT_LIMIT = 1 << 22;
 
 struct __align__(128) TmaSmem {
-    float old[4][BH][BW];   // 1920 bytes per slot (a multiple of 128)
+    float old[4][BH][BW];   // 3456 bytes per slot (27 x 128)
     float f[4][BH][BW];
     float red[3][RY][RX];
     unsigned long long bar[4];
@@ -72,17 +79,18 @@ __device__ __forceinline__ void tma_load_plane(void* dst, const CUtensorMap* map
         : "memory");
 }
 
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(256)
     rb_sweep_tma_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_f, Geom g,
                         const PlaneCoef<float>* __restrict__ coef, float* __restrict__ uout, int kchunk,
                         int* __restrict__ err) {
     __shared__ TmaSmem s;
-    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
     const int x0 = 1 + blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
     const int k0 = 1 + blockIdx.z * kchunk;
     if (k0 > g.nz - 2) return;
     const int k1 = min(k0 + kchunk, g.nz - 1);
-    const int bx = x0 - 5, by = y0 - 2;   // box origin: bx = 32 * blockIdx.x - 4, a multiple of 4
+    const int bx = x0 - 5, by = y0 - 2;   // box origin: bx = 64 * blockIdx.x - 4, a multiple of 4
+    // shared-memory box coordinates of node (x, y): (x - bx, y - by)
 
     if (tid == 0) {
         for (int q = 0; q < 4; ++q) mbar_init(&s.bar[q], 1);
@@ -126,21 +134,27 @@ __global__ void __launch_bounds__(TX* TY)
         return true;
     };
 
+    // red values of plane kk on the tile and its halo: pair e = (row hy, pair j)
+    // holds nodes x0 - 1 + 2j and x0 + 2j of row y0 - 1 + hy, the red one at
+    // offset (x0 - 1 + y + kk) & 1 in the pair
     auto red = [&](int kk) {
         float(*dst)[RX] = s.red[kk % 3];
         const float(*o0)[BW] = s.old[kk & 3];
+        const float(*om)[BW] = s.old[(kk + 3) & 3];   // plane kk-1
+        const float(*op)[BW] = s.old[(kk + 1) & 3];   // plane kk+1
+        const float(*fk)[BW] = s.f[kk & 3];
         const bool inner_plane = kk >= 1 && kk <= g.nz - 2;
         PlaneCoef<float> c{};
         if (inner_plane) c = coef[kk];
-        for (int q = tid; q < RX * RY; q += TX * TY) {
-            const int hx = q % RX, hy = q / RX;
-            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-            const int ox = hx + 4, oy = hy + 1;
+        for (int e = tid; e < RPAIRS * RY; e += 256) {
+            const int hy = e / RPAIRS, j = e - hy * RPAIRS;
+            const int gy = y0 - 1 + hy;
+            const int hx = 2 * j + ((x0 - 1 + gy + kk) & 1);
+            const int gx = x0 - 1 + hx;
+            const int ox = gx - bx, oy = gy - by;
             float v = o0[oy][ox];
-            if (inner_plane && gx >= 1 && gx <= g.nx - 2 && gy >= 1 && gy <= g.ny - 2 && ((gx + gy + kk) & 1) == 0) {
-                const float(*om)[BW] = s.old[(kk + 3) & 3];   // plane kk-1
-                const float(*op)[BW] = s.old[(kk + 1) & 3];   // plane kk+1
-                float w = s.f[kk & 3][oy][ox] * c.inv_d;
+            if (inner_plane && gx >= 1 && gx <= g.nx - 2 && gy >= 1 && gy <= g.ny - 2) {
+                float w = fk[oy][ox] * c.inv_d;
                 w = fmaf(-c.az, om[oy][ox] + op[oy][ox], w);
                 w = fmaf(-c.ay, o0[oy + 1][ox] + o0[oy - 1][ox], w);
                 v = fmaf(-c.ax, o0[oy][ox + 1] + o0[oy][ox - 1], w);
@@ -148,22 +162,30 @@ __global__ void __launch_bounds__(TX* TY)
             dst[hy][hx] = v;
         }
     };
+    // plane k of the tile: the thread's pair (x0 + 2 tx, x0 + 2 tx + 1) in row
+    // y0 + ty: the black node updated from the red values of planes k-1, k,
+    // k+1, the red node copied from its red entry
     auto black_store = [&](int k) {
-        const PlaneCoef<float> c = coef[k];
+        const int gy = y0 + threadIdx.y;
+        if (gy > g.ny - 2) return;
+        const int xa = x0 + 2 * threadIdx.x;
+        if (xa > g.nx - 2) return;
+        const int ob = (xa + gy + k) & 1 ? 0 : 1;   // black node's offset in the pair
+        const int gb = xa + ob, gr = xa + 1 - ob;
         const float(*r0)[RX] = s.red[k % 3];
+        const int ry = threadIdx.y + 1;
+        const PlaneCoef<float> c = coef[k];
         const float(*rm)[RX] = s.red[(k + 2) % 3];
         const float(*rp)[RX] = s.red[(k + 1) % 3];
-        const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-        if (gx > g.nx - 2 || gy > g.ny - 2) return;
-        const int rx = threadIdx.x + 1, ry = threadIdx.y + 1;
-        float v = r0[ry][rx];
-        if ((gx + gy + k) & 1) {
-            float w = s.f[k & 3][ry + 1][rx + 4] * c.inv_d;
-            w = fmaf(-c.az, rm[ry][rx] + rp[ry][rx], w);
-            w = fmaf(-c.ay, r0[ry + 1][rx] + r0[ry - 1][rx], w);
-            v = fmaf(-c.ax, r0[ry][rx + 1] + r0[ry][rx - 1], w);
-        }
-        uout[at(g, gx, gy, k)] = v;
+        const int rb = gb - x0 + 1;
+        float w = s.f[k & 3][gy - by][gb - bx] * c.inv_d;
+        w = fmaf(-c.az, rm[ry][rb] + rp[ry][rb], w);
+        w = fmaf(-c.ay, r0[ry + 1][rb] + r0[ry - 1][rb], w);
+        const float vb = fmaf(-c.ax, r0[ry][rb + 1] + r0[ry][rb - 1], w);
+        const float vr = r0[ry][gr - x0 + 1];
+        float* row = uout + at(g, 0, gy, k);
+        if (gb <= g.nx - 2) row[gb] = vb;
+        if (gr <= g.nx - 2) row[gr] = vr;
     };
 
     issue(0);
@@ -210,7 +232,7 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 // 3D tensor map over a pitched FP32 level array (x fastest) with a
-// (TX+8) x (TY+4) x 1 box: one plane of a tile with its halo.
+// 72 x 12 x 1 box: one plane of a 64 x 8 tile with its halo.
 void make_plane_map(CUtensorMap* map, const Geom& g, const float* base) {
     const cuuint64_t dims[3] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz)};
     const cuuint64_t strides[2] = {cuuint64_t(g.px) * 4, cuuint64_t(g.plane) * 4};   // multiples of 16 bytes
@@ -232,7 +254,7 @@ void launch_sweep_tma(const Geom& g, const CUtensorMap& tm_in, const CUtensorMap
     if (chunks < 1) chunks = 1;
     const int kchunk = (nzi + chunks - 1) / chunks;
     const dim3 grid(gx, gy, (nzi + kchunk - 1) / kchunk);
-    rb_sweep_tma_kernel<<<grid, dim3(TX, TY), 0, st>>>(tm_in, tm_f, g, coef, uout, kchunk, err);
+    rb_sweep_tma_kernel<<<grid, dim3(32, TY), 0, st>>>(tm_in, tm_f, g, coef, uout, kchunk, err);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
