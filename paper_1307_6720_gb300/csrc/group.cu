@@ -140,8 +140,7 @@ void upload_exact(GPart* G, GDim& D, std::vector<std::vector<GSepItem<T>>>& by_s
 // 2,610 solves/s on a 256-instance mix).  Norm partials keep the solo
 // decomposition (it fixes the summation order).
 constexpr int kZCap = 8;
-dim3 fat(dim3 grid, int items) {
-    (void)items;
+dim3 fat(dim3 grid) {
     grid.z = std::min<unsigned>(grid.z, kZCap);
     return grid;
 }
@@ -188,7 +187,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             const Geom& g = H.g[l];
             const Geom& gc = H.g[l + 1];
             T* f = (fz && l == 0) ? nullptr : A.f;
-            GItem s = item(q, line ? zline_grid(g) : fat(smooth_grid_t<T>(g, d3), n), g, ctl);
+            GItem s = item(q, line ? zline_grid(g) : fat(smooth_grid_t<T>(g, d3)), g, ctl);
             s.coef = A.coef;
             s.p[0] = A.u;
             s.p[1] = f;
@@ -198,21 +197,21 @@ void build_dim(GPart* G, GDim& D, int dim) {
             (line ? pre_ln : pre_pt)[l].push_back(s);
             s.ia[0] = nu2;
             (line ? post_ln : post_pt)[l].push_back(s);
-            GItem r = item(q, fat(residual_grid_plain_t<T>(g, d3), n), g, ctl);
+            GItem r = item(q, fat(residual_grid_plain_t<T>(g, d3)), g, ctl);
             r.coef = A.coef;
             r.p[0] = A.u;
             r.p[1] = f;
             r.p[2] = A.r;
             r.ia[1] = top;
             res[l].push_back(r);
-            GItem rs = item(q, fat(restrict_grid(gc, d3), n), g, ctl);
+            GItem rs = item(q, fat(restrict_grid(gc, d3)), g, ctl);
             rs.g2 = gc;
             rs.p[0] = A.r;
             rs.p[1] = C.f;
             rs.p[2] = C.u;
             rs.ia[1] = top;
             restr[l].push_back(rs);
-            GItem pr = item(q, fat(prolong_grid(gc, d3), n), gc, ctl);
+            GItem pr = item(q, fat(prolong_grid(gc, d3)), gc, ctl);
             pr.g2 = g;
             pr.p[0] = C.u;
             pr.p[1] = A.u;
@@ -225,7 +224,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             LevelArrays<T>& C = arr<T>(H, l + 1);
             const Geom& g = H.g[l];
             const Geom& gc = H.g[l + 1];
-            GItem rs = item(q, fat(restrict_grid(gc, d3), n), g, ctl);
+            GItem rs = item(q, fat(restrict_grid(gc, d3)), g, ctl);
             rs.g2 = gc;
             // the residual of the first test: FP64 mode in A.r of level 0, mixed mode the
             // double-float residual rounded into S.f of level 0
@@ -235,7 +234,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             rs.p[2] = C.u;
             rs.ia[1] = top;
             fmg_restr[l].push_back(rs);
-            GItem pr = item(q, fat(prolong_grid(gc, d3), n), gc, ctl);
+            GItem pr = item(q, fat(prolong_grid(gc, d3)), gc, ctl);
             pr.g2 = g;
             pr.p[0] = C.u;
             pr.p[1] = A.u;
@@ -370,7 +369,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
                 dc.p[3] = H.df.lo;
                 df_copy.push_back(dc);
                 if (!c->f_zero_finest) {
-                    GItem sp = item(q, fat(df_grid(g0, 1, 0), n), g0, ctl);
+                    GItem sp = item(q, fat(df_grid(g0, 1, 0)), g0, ctl);
                     sp.p[0] = H.d[0].f;
                     sp.p[1] = H.df.fh;
                     sp.p[2] = H.df.fl;
@@ -392,7 +391,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
             zero_lo.push_back(zero_item(H.df.lo, g0.n, sizeof(float)));
             GItem ze = zero_item(H.s[0].u, g0.n, sizeof(float));
             zero_e.push_back(ze);
-            GItem cr = item(q, fat(df_grid(g0, d3, 0), n), g0, ctl);
+            GItem cr = item(q, fat(df_grid(g0, d3, 0)), g0, ctl);
             cr.p[0] = H.s[0].u;
             cr.p[1] = H.df.hi;
             cr.p[2] = H.df.lo;
