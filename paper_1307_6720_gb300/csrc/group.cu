@@ -157,7 +157,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     const int L = D.L;
     std::vector<std::vector<GItem>> pre_pt(L), post_pt(L), pre_ln(L), post_ln(L), res(L), restr(L), prol(L),
         fmg_restr(L), fmg_prol(L);
-    std::vector<GItem> sub, sub8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
+    std::vector<GItem> sub, sub8, subz, subz8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
         res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
     std::vector<SubParams<T>> params;
     std::vector<std::vector<GSepItem<T>>> exact_items;   // per stage of the separable solves
@@ -288,7 +288,10 @@ void build_dim(GPart* G, GDim& D, int dim) {
             D.sub_smem = std::max(D.sub_smem, p.smem_bytes);
             params.push_back(p);
         }
-        if (ex < 0) (rows == 8 ? sub8 : sub).push_back(sb);
+        if (ex < 0) {
+            if (cut == 0) (rows == 8 ? subz8 : subz).push_back(sb);
+            else (rows == 8 ? sub8 : sub).push_back(sb);
+        }
         // ---- prologue, cycle end, epilogue ----
         const Geom& g0 = H.g[0];
         auto words = [](size_t elems, size_t bytes) { return int(elems * bytes / 4); };
@@ -425,6 +428,8 @@ void build_dim(GPart* G, GDim& D, int dim) {
     up(fmg_prol, D.fmg_prol);
     D.sub = upload(G, sub);
     D.sub8 = upload(G, sub8);
+    D.subz = upload(G, subz);
+    D.subz8 = upload(G, subz8);
     upload_exact<T>(G, D, exact_items);
     D.params = galloc(G, params.size() * sizeof(SubParams<T>));
     MHS_CUDA(cudaMemcpy(D.params, params.data(), params.size() * sizeof(SubParams<T>), cudaMemcpyHostToDevice));
@@ -463,27 +468,61 @@ namespace {
 // fmg_step >= 0 restricts the launch to instances whose full-multigrid top
 // level is at least fmg_step (the up-sweep of the first cycle).
 template <typename T>
-void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
+void gsmooth(GPart* G, GDim& D, std::vector<GTable>& pt, std::vector<GTable>& ln, int l, int nsweep, int fmg_step,
+             int gate) {
+    const int d3 = D.dim == 3;
+    for (int w = 0; w < nsweep; ++w) {
+        for (int colour = 0; colour < 2; ++colour) glaunch_colour<T>(pt[l], d3, colour, w, fmg_step, gate, G->stream);
+        for (int colour = 0; colour < 2; ++colour) glaunch_zline<T>(ln[l], colour, w, fmg_step, gate, G->stream);
+    }
+}
+
+// levels s.. of the instances above their cut-off, their sub-cycles or exact
+// solves, and back up to level s (with_z: also the instances whose sub-cycle
+// starts at level 0)
+template <typename T>
+void gvcycle_from(GPart* G, GDim& D, int s, int fmg_step, int gate, bool with_z) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
-    auto smooth = [&](std::vector<GTable>& pt, std::vector<GTable>& ln, int l, int nsweep) {
-        for (int w = 0; w < nsweep; ++w) {
-            for (int colour = 0; colour < 2; ++colour) glaunch_colour<T>(pt[l], d3, colour, w, fmg_step, gate, st);
-            for (int colour = 0; colour < 2; ++colour) glaunch_zline<T>(ln[l], colour, w, fmg_step, gate, st);
-        }
-    };
     for (int l = s; l < D.L - 1; ++l) {
-        smooth(D.pre_pt, D.pre_ln, l, D.max_nu1);
+        gsmooth<T>(G, D, D.pre_pt, D.pre_ln, l, D.max_nu1, fmg_step, gate);
         glaunch_residual<T>(D.res[l], d3, fmg_step, gate, st);
         glaunch_restrict<T>(D.restr[l], d3, fmg_step, gate, st);
     }
-    glaunch_subcycle<T>(D.sub, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 32, st);
-    glaunch_subcycle<T>(D.sub8, static_cast<const SubParams<T>*>(D.params), d3, s, fmg_step, gate, D.sub_smem, 8, st);
+    const SubParams<T>* params = static_cast<const SubParams<T>*>(D.params);
+    glaunch_subcycle<T>(D.sub, params, d3, s, fmg_step, gate, D.sub_smem, 32, st);
+    glaunch_subcycle<T>(D.sub8, params, d3, s, fmg_step, gate, D.sub_smem, 8, st);
+    if (with_z) {
+        glaunch_subcycle<T>(D.subz, params, d3, s, fmg_step, gate, D.sub_smem, 32, st);
+        glaunch_subcycle<T>(D.subz8, params, d3, s, fmg_step, gate, D.sub_smem, 8, st);
+    }
     for (const GSepTable<T>& t : exact_tables<T>(D)) glaunch_sep<T>(t, fmg_step, gate, st);
     for (int l = D.L - 2; l >= s; --l) {
         glaunch_prolong<T>(D.prol[l], d3, fmg_step, gate, st);
-        smooth(D.post_pt, D.post_ln, l, D.max_nu2);
+        gsmooth<T>(G, D, D.post_pt, D.post_ln, l, D.max_nu2, fmg_step, gate);
     }
+}
+
+template <typename T>
+void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
+    gvcycle_from<T>(G, D, s, fmg_step, gate, true);
+}
+
+// FP64 cycles with the convergence test after the pre-smoothing (as the solo
+// solve): instances above their cut-off at level 0 take the coarse-grid
+// correction of the latest residual, post- and then pre-smoothing; instances
+// whose sub-cycle starts at level 0 take a whole sub-cycle
+void gvcycle_rotated(GPart* G, GDim& D, int gate) {
+    cudaStream_t st = G->stream;
+    const int d3 = D.dim == 3;
+    glaunch_restrict<double>(D.restr[0], d3, -1, gate, st);
+    gvcycle_from<double>(G, D, 1, -1, gate, false);
+    const SubParams<double>* params = static_cast<const SubParams<double>*>(D.params);
+    glaunch_subcycle<double>(D.subz, params, d3, 0, -1, gate, D.sub_smem, 32, st);
+    glaunch_subcycle<double>(D.subz8, params, d3, 0, -1, gate, D.sub_smem, 8, st);
+    glaunch_prolong<double>(D.prol[0], d3, -1, gate, st);
+    gsmooth<double>(G, D, D.post_pt, D.post_ln, 0, D.max_nu2, -1, gate);
+    gsmooth<double>(G, D, D.pre_pt, D.pre_ln, 0, D.max_nu1, -1, gate);
 }
 
 // first cycle by full multigrid on the correction equation (instances
@@ -547,7 +586,8 @@ void gcycle(GPart* G, GDim& D, SolveCtl* const* ctls, cudaGraphConditionalHandle
     const int d3 = D.dim == 3;
     const bool mixed = G->mode == MHS_MIXED;
     if (mixed) glaunch_zero(D.zero_e, G_ACTIVE, st);
-    gvcycle<T>(G, D, 0, -1, G_ACTIVE);
+    if (mixed || D.L < 2) gvcycle<T>(G, D, 0, -1, G_ACTIVE);
+    else gvcycle_rotated(G, D, G_ACTIVE);
     if (mixed) {
         glaunch_df_correct(D.correct, d3, G_ACTIVE, st);
         glaunch_df_residual(D.res_norm, d3, G_ACTIVE, st);

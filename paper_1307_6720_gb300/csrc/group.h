@@ -121,6 +121,7 @@ struct GDim {
     // coarse solution, per level, for the instances using it
     std::vector<GTable> fmg_restr, fmg_prol;
     GTable sub, sub8;                            // sub-cycle: one item per instance (32 or 8 rows of threads)
+    GTable subz, subz8;                          // the same for instances whose sub-cycle starts at level 0
     // separable coarse-grid solves of the instances that end their cycles in one:
     // one table per (stage, kind), in launch order, in the cycle precision
     std::vector<GSepTable<float>> exact32;

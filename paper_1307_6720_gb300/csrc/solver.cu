@@ -294,6 +294,52 @@ static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fi
     if (fused && (n & 1)) MHS_CUDA(cudaMemcpyAsync(A.u, A.t, g.n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
 }
 
+// Per-level accounting and right-hand side of the V-cycle's operations on
+// level l: f vanishes on the finest FP64 interior level (the Dirichlet data
+// sits in u); algorithmic flops per node: the update u = f/d - ax(E+W) -
+// ay(N+S) [- az(U+D)] takes 2 (3) additions, 2 (3) multiplications, 2 (3)
+// subtractions and, with f, one more multiplication and subtraction; the
+// residual f - A u adds the centre term (a multiplication and an addition).
+template <typename T>
+struct LevelOps {
+    const T* f;
+    double s, N, fs, upd_flops, res_flops;
+    bool fine;
+    LevelOps(mhs_ctx* c, Hierarchy& H, int l) {
+        const bool dbl = sizeof(T) == 8;
+        const Geom& g = H.g[l];
+        s = sizeof(T);
+        N = double(g.interior());
+        const bool f_zero = dbl && l == 0 && H.dim == 3 && c->f_zero_finest;
+        fs = f_zero ? 0.0 : s;
+        f = f_zero ? nullptr : arrays<T>(H, l).f;
+        upd_flops = H.dim == 3 ? (f_zero ? 8.0 : 10.0) : 7.0;
+        res_flops = H.dim == 3 ? (f_zero ? 10.0 : 11.0) : 8.0;
+        fine = H.dim == 3 && l == 0;
+    }
+};
+
+// the coarse-grid correction of level l from its residual in A.r: restriction,
+// the coarser cycle, interpolation added to u
+template <typename T>
+static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>& o) {
+    cudaStream_t st = c->stream;
+    const bool dbl = sizeof(T) == 8;
+    LevelArrays<T>& A = arrays<T>(H, l);
+    LevelArrays<T>& C = arrays<T>(H, l + 1);
+    const double N = o.N, s = o.s, Nc = double(H.g[l + 1].interior());
+    {
+        TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
+                     Nc * (H.dim == 3 ? 54.0 : 18.0), st, o.fine);
+        launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, A.r, C.f, C.u, st);
+    }
+    vcycle<T>(c, H, l + 1);
+    {
+        TimedScope t(c->timer, dbl ? MHS_KT_PROLONG64 : MHS_KT_PROLONG32, (2 * N + Nc) * s, 4.0 * N, st, o.fine);
+        launch_prolong<T>(H.g[l + 1], H.g[l], H.dim, C.u, A.u, st);
+    }
+}
+
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
@@ -313,36 +359,33 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     LevelArrays<T>& A = arrays<T>(H, l);
     const Geom& g = H.g[l];
     const bool dbl = sizeof(T) == 8;
-    const double s = sizeof(T), N = double(g.interior());
-    // f vanishes on the finest FP64 interior level (the Dirichlet data sits in u)
-    const bool f_zero = dbl && l == 0 && H.dim == 3 && c->f_zero_finest;
-    const double fs = f_zero ? 0.0 : s;
-    const T* f = f_zero ? nullptr : A.f;
-    // algorithmic flops per node: the update u = f/d - ax(E+W) - ay(N+S) [- az(U+D)]
-    // takes 2 (3) additions, 2 (3) multiplications, 2 (3) subtractions and, with f,
-    // one more multiplication and subtraction; the residual f - A u adds the
-    // centre term (a multiplication and an addition) to the stencil sum
-    const double upd_flops = H.dim == 3 ? (f_zero ? 8.0 : 10.0) : 7.0;
-    const double res_flops = H.dim == 3 ? (f_zero ? 10.0 : 11.0) : 8.0;
-    const bool fine = H.dim == 3 && l == 0;
-    smooth_n<T>(c, H, l, f, c->opts.nu1, fine, N * (2 * s + fs), N * upd_flops);
+    const LevelOps<T> o(c, H, l);
+    const double sweep_bytes = o.N * (2 * o.s + o.fs);
+    smooth_n<T>(c, H, l, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
     {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, N * (2 * s + fs), N * res_flops, st, fine);
-        launch_residual<T>(g, H.dim, A.coef, A.u, f, A.r, nullptr, 0, st);
+        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, sweep_bytes, o.N * o.res_flops, st, o.fine);
+        launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st);
     }
-    LevelArrays<T>& C = arrays<T>(H, l + 1);
-    const double Nc = double(H.g[l + 1].interior());
-    {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
-                     Nc * (H.dim == 3 ? 54.0 : 18.0), st, fine);
-        launch_restrict<T>(g, H.g[l + 1], H.dim, A.r, C.f, C.u, st);
-    }
-    vcycle<T>(c, H, l + 1);
-    {
-        TimedScope t(c->timer, dbl ? MHS_KT_PROLONG64 : MHS_KT_PROLONG32, (2 * N + Nc) * s, 4.0 * N, st, fine);
-        launch_prolong<T>(H.g[l + 1], g, H.dim, C.u, A.u, st);
-    }
-    smooth_n<T>(c, H, l, f, c->opts.nu2, fine, N * (2 * s + fs), N * upd_flops);
+    coarse_correction<T>(c, H, l, o);
+    smooth_n<T>(c, H, l, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
+}
+
+// FP64 cycles of the finest level with the convergence test after the
+// pre-smoothing: the coarse-grid correction of the residual of the latest
+// test (in A.r), post-smoothing, then the next cycle's pre-smoothing; the
+// residual of that iterate (with norm partials) serves both the test and the
+// next restriction, so a cycle computes one finest-level residual instead of
+// two.  Levels of nu1 + nu2 sweeps per cycle as in vcycle; the solve returns
+// the iterate whose residual passed the test.  Needs level 0 above the
+// sub-cycle cut-off.
+static bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H) { return H.cut64 >= 1 && H.nlev() > 1; }
+
+static void vcycle_rotated(mhs_ctx* c, Hierarchy& H) {
+    const LevelOps<double> o(c, H, 0);
+    const double sweep_bytes = o.N * (2 * o.s + o.fs);
+    coarse_correction<double>(c, H, 0, o);
+    smooth_n<double>(c, H, 0, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
+    smooth_n<double>(c, H, 0, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
 }
 
 template <typename T>
@@ -450,6 +493,8 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
         const double N = double(g.interior());
         TimedScope t(c->timer, MHS_KT_SEPARABLE, N * 8.0 * 3.0, 0.0, c->stream, H.dim == 3);
         sep_correct64(c, H);
+    } else if (rotated_cycles(c, H)) {
+        vcycle_rotated(c, H);
     } else {
         vcycle<double>(c, H, 0);
     }
