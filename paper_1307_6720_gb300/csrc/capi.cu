@@ -125,6 +125,18 @@ void from_pitched(const mhs::Geom& g, double* dst, const double* src, size_t row
     MHS_CUDA(cudaMemcpy2DAsync(dst, g.nx * sizeof(double), src, g.px * sizeof(double), g.nx * sizeof(double), rows,
                                cudaMemcpyDefault, st));
 }
+// the same for a result array of the handle: to host memory the rows are
+// first packed densely on the device (the staging buffer), so the transfer
+// is one contiguous copy instead of one short row per DMA step
+void copy_out(mhs_handle h, const mhs::Geom& g, double* dst, const double* src, size_t rows) {
+    if (is_device_ptr(dst)) {
+        from_pitched(g, dst, src, rows, h->stream);
+        return;
+    }
+    mhs::ensure_staging(h);
+    mhs::launch_pack(src, h->staging, g.nx, g.px, rows, h->stream);
+    MHS_CUDA(cudaMemcpyAsync(dst, h->staging, size_t(g.nx) * rows * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+}
 }  // namespace
 
 extern "C" {
@@ -334,7 +346,7 @@ mhs_status mhs_get_phi(mhs_handle h, double* phi) {
     if (!h->have_solution) return fail(MHS_ERR_BAD_STATE, "no solution yet (call mhs_solve)");
     return guarded([&] {
         const mhs::Geom& g = h->h3.g[0];
-        from_pitched(g, phi, h->h3.d[0].u, size_t(g.ny) * g.nz, h->stream);
+        copy_out(h, g, phi, h->h3.d[0].u, size_t(g.ny) * g.nz);
         if (!is_device_ptr(phi)) MHS_CUDA(cudaStreamSynchronize(h->stream));
         return MHS_OK;
     });
@@ -356,7 +368,7 @@ mhs_status mhs_fields(mhs_handle h, double* Bx, double* By, double* Bz, double* 
         bool host = false;
         for (int q = 0; q < 5; ++q) {
             if (!outs[q]) continue;
-            from_pitched(g, outs[q], h->fld[q], size_t(g.ny) * g.nz, h->stream);
+            copy_out(h, g, outs[q], h->fld[q], size_t(g.ny) * g.nz);
             host = host || !is_device_ptr(outs[q]);
         }
         if (host) MHS_CUDA(cudaStreamSynchronize(h->stream));
@@ -387,7 +399,7 @@ mhs_status mhs_current(mhs_handle h, double* jx, double* jy, double* jz, double*
         bool host = false;
         for (int q = 0; q < 5; ++q) {
             if (!outs[q]) continue;
-            from_pitched(g, outs[q], h->post[q], size_t(g.ny) * g.nz, h->stream);
+            copy_out(h, g, outs[q], h->post[q], size_t(g.ny) * g.nz);
             host = host || !is_device_ptr(outs[q]);
         }
         if (host) MHS_CUDA(cudaStreamSynchronize(h->stream));

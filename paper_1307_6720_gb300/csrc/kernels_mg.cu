@@ -481,7 +481,20 @@ __global__ void f2d_kernel(const float* __restrict__ s, double* __restrict__ d, 
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
         d[i] = double(s[i]);
 }
+// rows of nx doubles at pitch px -> dense rows (a row per block-stride step)
+__global__ void pack_kernel(const double* __restrict__ s, double* __restrict__ d, int nx, int px, size_t rows) {
+    for (size_t r = blockIdx.x; r < rows; r += gridDim.x)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) d[r * nx + i] = s[r * px + i];
+}
 }  // namespace
+void launch_pack(const double* src, double* dst, int nx, int px, size_t rows, cudaStream_t st) {
+    if (rows == 0) return;
+    const unsigned blocks = unsigned(rows < 152 * 16 ? rows : 152 * 16);
+    pack_kernel<<<blocks, 128, 0, st>>>(src, dst, nx, px, rows);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
 void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st) {
     d2f_kernel<<<152 * 8, 256, 0, st>>>(src, dst, n);
     count_launches(1);

@@ -77,6 +77,7 @@ void ensure_staging(mhs_ctx* c);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)
 void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
+void launch_pack(const double* src, double* dst, int nx, int px, size_t rows, cudaStream_t st);   // pitched -> dense
 void launch_f2d(const float* src, double* dst, size_t n, cudaStream_t st);
 
 }  // namespace mhs
