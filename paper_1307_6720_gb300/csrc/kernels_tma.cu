@@ -32,14 +32,14 @@ namespace {
 constexpr int TX = 64, TY = 8;            // tile of outputs; threads 32 x 8, an x-pair each
 constexpr int BW = 72, BH = 12;           // TMA box (floats): x from 64 bx - 4, y from y0 - 2
 constexpr int RX = TX + 2, RY = TY + 2;   // red values: tile + 1-node halo
-constexpr int RPAIRS = RX / 2;            // x-pairs per red row
+constexpr int RPAIRS = RX / 2;            // x-pairs per red row = red values per row (stored densely)
 constexpr unsigned BOX_BYTES = BW * BH * 4;
 constexpr int WAIT_LIMIT = 1 << 22;
 
 struct __align__(128) TmaSmem {
     float old[4][BH][BW];   // 3456 bytes per slot (27 x 128)
     float f[4][BH][BW];
-    float red[3][RY][RX];
+    float red[3][RY][RPAIRS];   // row hy: the red value of pair j at [hy][j]
     unsigned long long bar[4];
 };
 
@@ -136,9 +136,10 @@ __global__ void __launch_bounds__(256)
 
     // red values of plane kk on the tile and its halo: pair e = (row hy, pair j)
     // holds nodes x0 - 1 + 2j and x0 + 2j of row y0 - 1 + hy, the red one at
-    // offset (x0 - 1 + y + kk) & 1 in the pair
+    // offset (x0 - 1 + y + kk) & 1 in the pair; stored densely at [hy][j]
+    PlaneCoef<float> c_red{};   // coefficients of the latest red plane (the next black plane's)
     auto red = [&](int kk) {
-        float(*dst)[RX] = s.red[kk % 3];
+        float(*dst)[RPAIRS] = s.red[kk % 3];
         const float(*o0)[BW] = s.old[kk & 3];
         const float(*om)[BW] = s.old[(kk + 3) & 3];   // plane kk-1
         const float(*op)[BW] = s.old[(kk + 1) & 3];   // plane kk+1
@@ -146,11 +147,11 @@ __global__ void __launch_bounds__(256)
         const bool inner_plane = kk >= 1 && kk <= g.nz - 2;
         PlaneCoef<float> c{};
         if (inner_plane) c = coef[kk];
+        c_red = c;
         for (int e = tid; e < RPAIRS * RY; e += 256) {
             const int hy = e / RPAIRS, j = e - hy * RPAIRS;
             const int gy = y0 - 1 + hy;
-            const int hx = 2 * j + ((x0 - 1 + gy + kk) & 1);
-            const int gx = x0 - 1 + hx;
+            const int gx = x0 - 1 + 2 * j + ((x0 - 1 + gy + kk) & 1);
             const int ox = gx - bx, oy = gy - by;
             float v = o0[oy][ox];
             if (inner_plane && gx >= 1 && gx <= g.nx - 2 && gy >= 1 && gy <= g.ny - 2) {
@@ -159,30 +160,33 @@ __global__ void __launch_bounds__(256)
                 w = fmaf(-c.ay, o0[oy + 1][ox] + o0[oy - 1][ox], w);
                 v = fmaf(-c.ax, o0[oy][ox + 1] + o0[oy][ox - 1], w);
             }
-            dst[hy][hx] = v;
+            dst[hy][j] = v;
         }
     };
     // plane k of the tile: the thread's pair (x0 + 2 tx, x0 + 2 tx + 1) in row
     // y0 + ty: the black node updated from the red values of planes k-1, k,
-    // k+1, the red node copied from its red entry
-    auto black_store = [&](int k) {
+    // k+1, the red node copied from its red entry.  With p the red offset of
+    // the row, the black node is at offset p, its west and east red neighbours
+    // are entries tx and tx + 1 of the row, the red node of the pair entry
+    // tx + 1 - p, and the red values above, below and in planes k -+ 1 (rows of
+    // the other parity) entry tx + p.
+    auto black_store = [&](int k, const PlaneCoef<float>& c) {
         const int gy = y0 + threadIdx.y;
         if (gy > g.ny - 2) return;
         const int xa = x0 + 2 * threadIdx.x;
         if (xa > g.nx - 2) return;
-        const int ob = (xa + gy + k) & 1 ? 0 : 1;   // black node's offset in the pair
-        const int gb = xa + ob, gr = xa + 1 - ob;
-        const float(*r0)[RX] = s.red[k % 3];
-        const int ry = threadIdx.y + 1;
-        const PlaneCoef<float> c = coef[k];
-        const float(*rm)[RX] = s.red[(k + 2) % 3];
-        const float(*rp)[RX] = s.red[(k + 1) % 3];
-        const int rb = gb - x0 + 1;
+        const int p = (x0 - 1 + gy + k) & 1;
+        const int gb = xa + p, gr = xa + 1 - p;
+        const int tx = threadIdx.x, ry = threadIdx.y + 1;
+        const float(*r0)[RPAIRS] = s.red[k % 3];
+        const float(*rm)[RPAIRS] = s.red[(k + 2) % 3];
+        const float(*rp)[RPAIRS] = s.red[(k + 1) % 3];
+        const int jv = tx + p;
         float w = s.f[k & 3][gy - by][gb - bx] * c.inv_d;
-        w = fmaf(-c.az, rm[ry][rb] + rp[ry][rb], w);
-        w = fmaf(-c.ay, r0[ry + 1][rb] + r0[ry - 1][rb], w);
-        const float vb = fmaf(-c.ax, r0[ry][rb + 1] + r0[ry][rb - 1], w);
-        const float vr = r0[ry][gr - x0 + 1];
+        w = fmaf(-c.az, rm[ry][jv] + rp[ry][jv], w);
+        w = fmaf(-c.ay, r0[ry + 1][jv] + r0[ry - 1][jv], w);
+        const float vb = fmaf(-c.ax, r0[ry][tx + 1] + r0[ry][tx], w);
+        const float vr = r0[ry][tx + 1 - p];
         float* row = uout + at(g, 0, gy, k);
         if (gb <= g.nx - 2) row[gb] = vb;
         if (gr <= g.nx - 2) row[gr] = vr;
@@ -200,12 +204,13 @@ __global__ void __launch_bounds__(256)
     red(k0);
     __syncthreads();
     for (int k = k0, j = 0; k < k1; ++k, ++j) {
+        const PlaneCoef<float> ck = c_red;   // plane k's coefficients, loaded by red(k)
         issue(j + 3);
         issued = j + 4;
         if (!wait_stage(j + 2)) return;
         red(k + 1);
         __syncthreads();
-        black_store(k);
+        black_store(k, ck);
         __syncthreads();
     }
     // the stage issued during the last step is still in flight: complete it
