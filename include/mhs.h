@@ -444,8 +444,8 @@ MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int pr
 #define MHS_KT_RESTRICT32 5
 #define MHS_KT_PROLONG64 6
 #define MHS_KT_PROLONG32 7
-#define MHS_KT_COARSE64 8
-#define MHS_KT_COARSE32 9
+#define MHS_KT_COARSE64 8      /* coarse-grid solve, FP64: the one-CTA sub-cycle or the separable solve of a level */
+#define MHS_KT_COARSE32 9      /* the same in FP32 */
 #define MHS_KT_RESID_MIXED 10  /* double-float outer residual rounded to the FP32 right-hand side */
 #define MHS_KT_CORRECT 11      /* (hi, lo) += e32, the double-float iterate */
 #define MHS_KT_FIELDS 12       /* B, p, rho */
