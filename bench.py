@@ -71,9 +71,14 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", self.gpu], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "50", "-i", self.gpu], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the first sample must exist before the timed region starts (nvidia-smi takes a while to come up)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -472,18 +477,8 @@ def large_grid_leg(M, steps, with_error=True):
 
 
 def batched_instances(count=256):
-    """Seeded instances: grids 33^3, 65^3, 129^3 and 129x129x65 (on [0,1]^2 x [0,0.5]) in turn,
-    alpha ~ U[0,0.8], xi = a exp(-kappa z) with a ~ U[0,1), kappa ~ U[0.5,2], 8-spot magnetograms;
-    instance i draws from splitmix64(1000 + i)."""
-    shapes = [(33, 33, 1.0), (65, 65, 1.0), (129, 129, 1.0), (129, 65, 0.5)]
-    inst = []
-    for i in range(count):
-        n, nz, Lz = shapes[i % 4]
-        rng = S.SplitMix64(1000 + i)
-        alpha, a, kappa = rng.uniform(0.0, 0.8), rng.uniform(0.0, 1.0), rng.uniform(0.5, 2.0)
-        inst.append(dict(n=n, nz=nz, Lz=Lz, alpha=alpha, a=a, kappa=kappa,
-                         bz=S.magnetogram_random(n, n, seed=1000 + i)))
-    return inst
+    """The seeded 256-instance batch (grids 33^3 .. 129^3 and 129x129x65, random alpha, a, kappa)."""
+    return S.batched_instances(count)
 
 
 def batched_leg(M, reps=3, count=256, tune=True):
@@ -560,7 +555,7 @@ def batched_leg(M, reps=3, count=256, tune=True):
     return res
 
 
-def serving_leg(M, requests=1000, load=0.8, inflight=16, budget_gb=64):
+def serving_leg(M, requests=10000, load=0.8, inflight=16, budget_gb=64):
     """Poisson arrivals of solve requests, grid sizes 65^3 / 129^3 / 257^3 at 60/30/10 %, random
     magnetograms and alpha / xi parameters (request r: splitmix64(r); arrivals: splitmix64(42)),
     served with HBM-budget admission and resident hierarchies (mixed precision, Phi + fields into
@@ -666,7 +661,7 @@ def serving_leg(M, requests=1000, load=0.8, inflight=16, budget_gb=64):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--impl", choices=["mhs", "reference"], default="mhs")
@@ -682,7 +677,7 @@ def main():
     ap.add_argument("--tma", action="store_true", help="--op smooth in FP32: the fused TMA-staged sweep")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the large-grid, batched and serving legs")
-    ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the serving leg")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven kernel-by-kernel solve instead of the captured graph (for launch lists)")
     ap.add_argument("--zline", action="store_true",

@@ -138,6 +138,14 @@ typedef struct {
                                    double-float loop, 2-3 steps.  FP64 mode: FP64 direct solves, 1-2 steps,
                                    when nx - 1 and ny - 1 are powers of two or nx, ny <= 66 (else V-cycles).
                                    Not in groups */
+#define MHS_FLAG_LOWER_FP64 512 /* mixed mode: solve the lower-boundary problem (eq. lower_bound) by FP64 V-cycles,
+                                   as in FP64 mode, instead of FP32 cycles in a double-float defect correction
+                                   loop; the interior problem keeps the mixed-precision loop.  The double-float
+                                   iterate (48-bit significand) bounds the relative residual of the
+                                   lower-boundary problem near 5e-12 on 257^2 and 2e-11 on 513^2 nodes (the
+                                   interior problem's, whose right-hand side is smoother, near 1e-13 and 1e-12);
+                                   with this flag both reach tolerances of 1e-12 on those grids.  The lower
+                                   boundary is a small part of the work (1 / nz of the unknowns).  Not in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of

@@ -685,6 +685,8 @@ GPart* part_create(mhs_ctx** hs, int n, int mode) {
         if (c->opts.inner_cycles != 1) throw Error(MHS_ERR_INVALID_ARG, "group: inner_cycles must be 1");
         if (c->opts.flags & MHS_FLAG_SEPARABLE)
             throw Error(MHS_ERR_INVALID_ARG, "group: the separable inner solver is not available in groups");
+        if (mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_LOWER_FP64))
+            throw Error(MHS_ERR_INVALID_ARG, "group: MHS_FLAG_LOWER_FP64 is not available in groups");
     }
     gsubcycle_prepare();
     MHS_CUDA(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));

@@ -450,6 +450,14 @@ struct Enq {
     cudaGraphConditionalHandle hnd = 0;
 };
 
+// Precision of the lower-boundary solve: that of the solve, except that
+// MHS_FLAG_LOWER_FP64 turns a mixed-mode lower-boundary solve into FP64
+// cycles (its double-float iterate bounds the residual near 5e-12 on 257^2
+// nodes and 2e-11 on 513^2); the interior solve keeps the mode it was given.
+static int lower_mode(const mhs_ctx* c, int mode) {
+    return (mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_LOWER_FP64)) ? int(MHS_FP64) : mode;
+}
+
 // residual of the current iterate (FP64, or FP64 rounded into the FP32
 // right-hand side in mixed mode) with norm partials; returns their count
 static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
@@ -567,6 +575,10 @@ static void prologue_3d(const Enq& e) {
                 MHS_CUDA(cudaMemsetAsync(H.df.hi, 0, g.n * sizeof(float), c->stream));
                 MHS_CUDA(cudaMemsetAsync(H.df.lo, 0, g.n * sizeof(float), c->stream));
             }
+            // the Dirichlet plane in double-float form: the lower-boundary iterate itself, or the
+            // split of its FP64 solution when that problem ran in FP64 cycles
+            if (lower_mode(c, e.mode) != e.mode)
+                launch_df_split(c->h2.g[0], 2, c->h2.d[0].u, c->h2.df.hi, c->h2.df.lo, c->stream);
             launch_df_copy_plane(c->h2.g[0], c->h2.df.hi, c->h2.df.lo, g, H.df.hi, H.df.lo, c->stream);
             if (!c->f_zero_finest) launch_df_split(g, 3, H.d[0].f, H.df.fh, H.df.fl, c->stream);
         }
@@ -637,7 +649,7 @@ static void build_graph(mhs_ctx* c, int mode) {
         cudaGraphConditionalHandle h2, h3;
         MHS_CUDA(cudaGraphConditionalHandleCreate(&h2, g, 0, cudaGraphCondAssignDefault));
         MHS_CUDA(cudaGraphConditionalHandleCreate(&h3, g, 0, cudaGraphCondAssignDefault));
-        Enq e2{c, mode, true, h2}, e3{c, mode, true, h3};
+        Enq e2{c, lower_mode(c, mode), true, h2}, e3{c, mode, true, h3};
         // kernel counts per section (prologues once, bodies once per cycle), so that
         // launch accounting can add what a graph launch actually ran
         const long long l0 = launches();
@@ -702,7 +714,10 @@ static bool read_cont(mhs_ctx* c, int which) {
 // in eager mode (kernel timing enabled) the host drives the cycles.
 void solve_begin(mhs_ctx* c, double tol, int mode) {
     cudaStream_t st = c->stream;
-    if (c->opts.flags & MHS_FLAG_SEPARABLE) sep_prepare(c, mode);   // allocations: not inside a graph capture
+    if (c->opts.flags & MHS_FLAG_SEPARABLE) {   // allocations: not inside a graph capture
+        sep_prepare(c, mode);
+        if (lower_mode(c, mode) != mode && sep_fp64_available(c)) sep_tables<double>(c, c->h2, 0);
+    }
     for (int q = 0; q < 2; ++q) {
         c->ctl_host[q] = SolveCtl{};
         c->ctl_host[q].tol = tol;
@@ -718,10 +733,10 @@ void solve_begin(mhs_ctx* c, double tol, int mode) {
         for (int q = 0; q < 4; ++q) c->launched_count[q] = e.count[q];
         MHS_CUDA(cudaGraphLaunch(e.exec, st));
     } else {
-        Enq e{c, mode, false, 0};
-        prologue_2d(e);
-        while (read_cont(c, 0)) cycle_body(e, c->h2, c->ctl + 0);
-        epilogue(e, c->h2);
+        Enq e{c, mode, false, 0}, e2{c, lower_mode(c, mode), false, 0};
+        prologue_2d(e2);
+        while (read_cont(c, 0)) cycle_body(e2, c->h2, c->ctl + 0);
+        epilogue(e2, c->h2);
         prologue_3d(e);
         while (read_cont(c, 1)) cycle_body(e, c->h3, c->ctl + 1);
         epilogue(e, c->h3);

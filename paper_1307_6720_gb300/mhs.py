@@ -24,7 +24,7 @@ MHS_XI_NONE, MHS_XI_EXP, MHS_XI_EXP_SIN = 0, 1, 2
 MHS_FP64, MHS_MIXED = 0, 1
 MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, MHS_FLAG_NO_TMA, MHS_FLAG_NO_FMG = \
     1, 2, 4, 8, 16, 32
-MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE = 64, 128, 256
+MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE, MHS_FLAG_LOWER_FP64 = 64, 128, 256, 512
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE, MHS_OP_EXACT = range(7)
 

@@ -164,3 +164,25 @@ def unknowns(pr) -> int:
     """3D interior unknowns plus the 2D lower-boundary interior unknowns."""
     nx, ny, nz = pr["nx"], pr["ny"], pr["nz"]
     return (nx - 2) * (ny - 2) * (nz - 2) + (nx - 2) * (ny - 2)
+
+
+def batched_instances(count=256):
+    """The uneven batch: grids 33^3, 65^3, 129^3 on [0,1]^3 and 129 x 129 x 65 on
+    [0,1]^2 x [0,0.5] in turn; alpha ~ U[0,0.8], xi = a exp(-kappa z) with
+    a ~ U[0,1), kappa ~ U[0.5,2], 8-spot magnetogram; instance i draws from
+    splitmix64(1000 + i)."""
+    shapes = [(33, 33, 1.0), (65, 65, 1.0), (129, 129, 1.0), (129, 65, 0.5)]
+    inst = []
+    for i in range(count):
+        n, nz, Lz = shapes[i % 4]
+        rng = SplitMix64(1000 + i)
+        alpha, a, kappa = rng.uniform(0.0, 0.8), rng.uniform(0.0, 1.0), rng.uniform(0.5, 2.0)
+        inst.append(dict(n=n, nz=nz, Lz=Lz, alpha=alpha, a=a, kappa=kappa,
+                         bz=magnetogram_random(n, n, seed=1000 + i)))
+    return inst
+
+
+def batched_problem(d):
+    """The problem dict of one batched instance."""
+    return problem(d["n"], d["n"], d["nz"], 1.0, 1.0, d["Lz"], alpha=d["alpha"], xi_kind=1,
+                   xi_a=d["a"], xi_kappa=d["kappa"])

@@ -313,6 +313,33 @@ def test_mixed_mode_reaches_fp64_class_residual(M):
     _compare(got, _oracle(pr, bz), 2e-10)
 
 
+def test_lower_boundary_fp64_flag_in_mixed_mode(M):
+    """MHS_FLAG_LOWER_FP64: the lower-boundary problem of a mixed-mode solve
+    runs the FP64 cycles of FP64 mode (same cycle count and residual, bit for
+    bit), the interior problem keeps the mixed loop, the solution matches the
+    exact discrete one, the eager path gives the same bits as the graph, and
+    groups refuse the flag in mixed mode."""
+    pr, bz = S.linear_mhs(129, seed=31)
+    flag = M.MHS_FLAG_LOWER_FP64
+    info64, _ = _gpu_solve(M, pr, bz, 1e-12, M.MHS_FP64)
+    info, got = _gpu_solve(M, pr, bz, 1e-12, M.MHS_MIXED, opts=dict(flags=flag))
+    assert info["cycles_2d"] == info64["cycles_2d"] and info["rel_res_2d"] == info64["rel_res_2d"]
+    assert info["rel_res_3d"] < 1e-12
+    _compare(got, _oracle(pr, bz), 1e-9)
+    info_e, got_e = _gpu_solve(M, pr, bz, 1e-12, M.MHS_MIXED, opts=dict(flags=flag | M.MHS_FLAG_NO_GRAPH))
+    assert info_e["cycles_3d"] == info["cycles_3d"]
+    for k in got:
+        assert np.array_equal(got_e[k], got[k]), k
+    pr2 = S.problem(17, 17, 17, alpha=0.3, xi_kind=1, xi_a=0.5, xi_kappa=1.0)
+    h = M.mhs_create(17, 17, 17, 1.0, 1.0, 1.0, 0.3, _xi(M, pr2))
+    M.mhs_set_options(h, flags=flag)
+    with pytest.raises(M.MhsError):
+        M.mhs_group_create([h], M.MHS_MIXED)
+    g = M.mhs_group_create([h], M.MHS_FP64)   # FP64 solves ignore the flag
+    M.mhs_group_destroy(g)
+    M.mhs_destroy(h)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_full_multigrid_start_saves_cycles_same_solution(M, mode):
     """The full-multigrid first cycle (default) reaches the tolerance in fewer
