@@ -555,13 +555,13 @@ def batched_leg(M, reps=3, count=256, tune=True):
     return res
 
 
-def serving_leg(M, requests=10000, load=0.8, inflight=16, budget_gb=64):
+def serving_leg(M, requests=10000, loads=(0.5, 0.8, 0.95), inflight=16, budget_gb=64):
     """Poisson arrivals of solve requests, grid sizes 65^3 / 129^3 / 257^3 at 60/30/10 %, random
     magnetograms and alpha / xi parameters (request r: splitmix64(r); arrivals: splitmix64(42)),
     served with HBM-budget admission and resident hierarchies (mixed precision, Phi + fields into
     device buffers).  Capacity is measured first with all requests queued at once; the Poisson
-    stream then runs at `load` x capacity.  Baseline: the same requests solved one after another in
-    FP64 through mhs_solve + mhs_fields."""
+    stream then runs at each of `loads` x capacity (the headline keys are those of 0.8).  Baseline:
+    the same requests solved one after another in FP64 through mhs_solve + mhs_fields."""
     import math as _m
     import torch
     sizes = []
@@ -603,28 +603,36 @@ def serving_leg(M, requests=10000, load=0.8, inflight=16, budget_gb=64):
     capacity = requests / (time.perf_counter() - t0)
     M.mhs_server_destroy(srv)
 
-    srv = M.mhs_server_create(budget_gb << 30, inflight)
-    warm(srv)
-    rate = load * capacity
-    arr = S.SplitMix64(42)
-    t_next = time.perf_counter()
-    tickets = []
-    t0 = time.perf_counter()
-    for r in range(requests):
-        t_next += -_m.log(1.0 - arr.uniform()) / rate
-        while time.perf_counter() < t_next:
-            pass
-        tickets.append(submit(srv, r))
-    lat = []
-    for t in tickets:
-        info, st, l = M.mhs_server_wait(srv, t, 600.0)
-        assert st == 0, st
-        lat.append(l)
-    span = time.perf_counter() - t0
-    stats = M.mhs_server_stats(srv)
-    M.mhs_server_destroy(srv)
-    lat.sort()
-    pct = lambda p: lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))]
+    def stream(load):
+        srv = M.mhs_server_create(budget_gb << 30, inflight)
+        warm(srv)
+        rate = load * capacity
+        arr = S.SplitMix64(42)
+        t_next = time.perf_counter()
+        tickets = []
+        t0 = time.perf_counter()
+        for r in range(requests):
+            t_next += -_m.log(1.0 - arr.uniform()) / rate
+            while time.perf_counter() < t_next:
+                pass
+            tickets.append(submit(srv, r))
+        lat = []
+        for t in tickets:
+            info, st, l = M.mhs_server_wait(srv, t, 600.0)
+            assert st == 0, st
+            lat.append(l)
+        span = time.perf_counter() - t0
+        stats = M.mhs_server_stats(srv)
+        M.mhs_server_destroy(srv)
+        lat.sort()
+        pct = lambda p: lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))]
+        return {"offered_load": load, "arrival_rate_per_s": rate, "solves_per_s": requests / span,
+                "p50_ms": pct(0.5), "p99_ms": pct(0.99), "server_p50_ms": stats["p50_ms"],
+                "server_p99_ms": stats["p99_ms"], "resident_hierarchies": stats["resident_hierarchies"],
+                "device_bytes": stats["device_bytes"]}
+
+    per_load = {str(load): stream(load) for load in loads}
+    head = per_load[str(0.8)] if str(0.8) in per_load else per_load[str(loads[0])]
 
     # sequential FP64 baseline on a sample of the same requests (one handle per size)
     hs = {n: M.mhs_create(n, n, n, 1.0, 1.0, 1.0, 0.0) for n in (65, 129, 257)}
@@ -649,13 +657,10 @@ def serving_leg(M, requests=10000, load=0.8, inflight=16, budget_gb=64):
         M.mhs_destroy(h)
     del ring
     torch.cuda.empty_cache()
-    return {"requests": requests, "mix": "65^3/129^3/257^3 at 60/30/10 %", "max_inflight": inflight,
-            "budget_gb": budget_gb, "capacity_solves_per_s": capacity, "offered_load": load,
-            "arrival_rate_per_s": rate, "solves_per_s": requests / span, "p50_ms": pct(0.5), "p99_ms": pct(0.99),
-            "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"],
-            "resident_hierarchies": stats["resident_hierarchies"], "device_bytes": stats["device_bytes"],
-            "sequential_fp64_solves_per_s": seq_rate, "sequential_sample": len(sample),
-            "speedup_vs_sequential_fp64": (requests / span) / seq_rate}
+    return dict({"requests": requests, "mix": "65^3/129^3/257^3 at 60/30/10 %", "max_inflight": inflight,
+                 "budget_gb": budget_gb, "capacity_solves_per_s": capacity}, **head,
+                sequential_fp64_solves_per_s=seq_rate, sequential_sample=len(sample),
+                speedup_vs_sequential_fp64=head["solves_per_s"] / seq_rate, loads=per_load)
 
 
 def main():
