@@ -13,8 +13,9 @@ field recovery.
   513 x 513 x 257 grid) with the lower-boundary problem in FP64 cycles
   (MHS_FLAG_LOWER_FP64): the double-float iterate of the default mixed loop
   bounds that problem's residual near 5e-12 on 257^2 and 2e-11 on 513^2
-  nodes, measured here.  The default mixed mode at the benchmark's 1e-10
-  must converge and match Phi and p within 1e-8.
+  nodes (100 outer steps end at 4.7e-12 and 1.6e-11 on these inputs).  The
+  default mixed mode at the benchmark's 1e-10 must converge and match Phi
+  and p within 1e-8.
   One exception to the FP64 bar, from the arithmetic: on the
   513 x 513 x 257 grid (h = 1/512) B_z and rho, the second and third
   differences of P, carry the rounding of P amplified by up to h^-2 and
