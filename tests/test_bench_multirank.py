@@ -46,3 +46,35 @@ def test_max_over_ranks_and_whole_job_value():
 def test_single_rank_needs_no_collective():
     import bench
     assert bench.aggregate(4.0, 500, 1) == (4.0, 500 / 4e-3)
+
+
+def _run_reference(env_extra):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, env=env, cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line with
+    the GPU arm's metric, unit and workload, the oracle as its CPU baseline and
+    an end-to-end entry without device copies."""
+    out = _run_reference({"RANK": "0"})
+    assert len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["metric"] == "unknowns solved/s to 1e-10 rel. residual" and d["unit"] == "unknowns/s"
+    assert d["config"]["workload"] == "linear_mhs_129"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
