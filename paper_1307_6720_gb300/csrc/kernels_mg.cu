@@ -275,6 +275,39 @@ __global__ void copy_plane_kernel(Geom g2, const double* __restrict__ src, Geom 
     copy_plane_body(g2, src, g3, dst, blockIdx);
 }
 
+// dst = src on the six boundary faces of a 3D level (face nodes enumerated:
+// the planes k = 0 and nz - 1, then the rows j = 0 and ny - 1 of the other
+// planes, then the columns i = 0 and nx - 1 of the remaining rows)
+template <typename T>
+__global__ void copy_faces_kernel(Geom g, const T* __restrict__ src, T* __restrict__ dst) {
+    const long long nxy = (long long)g.nx * g.ny, nxz = (long long)g.nx * (g.nz - 2),
+                    nyz = (long long)(g.ny - 2) * (g.nz - 2);
+    const long long total = 2 * (nxy + nxz + nyz);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (e < 2 * nxy) {
+            const long long q = e % nxy;
+            k = e < nxy ? 0 : g.nz - 1;
+            j = int(q / g.nx);
+            i = int(q - (long long)j * g.nx);
+        } else if (e < 2 * (nxy + nxz)) {
+            const long long q = (e - 2 * nxy) % nxz;
+            j = e - 2 * nxy < nxz ? 0 : g.ny - 1;
+            k = 1 + int(q / g.nx);
+            i = int(q - (long long)(k - 1) * g.nx);
+        } else {
+            const long long r = e - 2 * (nxy + nxz);
+            const long long q = r % nyz;
+            i = r < nyz ? 0 : g.nx - 1;
+            k = 1 + int(q / (g.ny - 2));
+            j = 1 + int(q - (long long)(k - 1) * (g.ny - 2));
+        }
+        const size_t o = at(g, i, j, k);
+        dst[o] = src[o];
+    }
+}
+
 __global__ void nonfinite_kernel(Geom g, const double* __restrict__ bz, int* flag) {
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -439,6 +472,15 @@ void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, doub
     MHS_CUDA(cudaGetLastError());
 }
 
+template <typename T>
+void launch_copy_faces(const Geom& g, const T* src, T* dst, cudaStream_t st) {
+    const long long total = 2 * ((long long)g.nx * g.ny + (long long)g.nx * (g.nz - 2) + (long long)(g.ny - 2) * (g.nz - 2));
+    const int blocks = int(std::min<long long>((total + 255) / 256, 152 * 4));
+    copy_faces_kernel<T><<<blocks, 256, 0, st>>>(g, src, dst);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
+}
+
 void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st) {
     const dim3 grid = grid_for(g, 0, g.nx - 2, 0);
     nonfinite_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, bz, flag);
@@ -464,7 +506,8 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
     template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t);           \
     template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \
     template void launch_coarse<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
-    template void launch_zero_interior<T>(const Geom&, int, T*, cudaStream_t);
+    template void launch_zero_interior<T>(const Geom&, int, T*, cudaStream_t);                                \
+    template void launch_copy_faces<T>(const Geom&, const T*, T*, cudaStream_t);
 MHS_INST(double)
 MHS_INST(float)
 #undef MHS_INST

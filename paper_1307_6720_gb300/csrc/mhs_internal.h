@@ -285,6 +285,9 @@ void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
 void launch_lower_rhs(const Geom& g, const double* bz, double* f64, cudaStream_t st);
 template <typename T>
 void launch_zero_interior(const Geom& g, int dim, T* u, cudaStream_t st);
+// dst = src on the six boundary faces of a 3D level
+template <typename T>
+void launch_copy_faces(const Geom& g, const T* src, T* dst, cudaStream_t st);
 void launch_copy_plane(const Geom& g2, const double* src2d, const Geom& g3, double* dst3d, cudaStream_t st);
 void launch_count_nonfinite(const Geom& g, const double* bz, int* flag, cudaStream_t st);
 // norm^2 of the lifted right-hand side of the interior problem: cz * P[k=0] on plane k=1

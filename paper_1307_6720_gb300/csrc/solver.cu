@@ -388,11 +388,34 @@ static void vcycle_rotated(mhs_ctx* c, Hierarchy& H) {
     smooth_n<double>(c, H, 0, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
 }
 
+// Levels whose red-black sweeps run out of place (u and its twin t taking
+// turns as input and output): FP32 3D levels of at least fused_min interior
+// nodes, FP64 3D levels with MHS_FLAG_FUSED_SWEEP64; not with z-line smoothing.
+template <typename T>
+static bool fused_level(const mhs_ctx* c, const Hierarchy& H, int l) {
+    if (H.dim != 3 || use_zline(c)) return false;
+    if (!arrays<T>(const_cast<Hierarchy&>(H), l).t) return false;
+    return sizeof(T) == 8 ? (c->opts.flags & MHS_FLAG_FUSED_SWEEP64) != 0
+                          : H.g[l].interior() >= size_t(c->opts.fused_min);
+}
+
+// An out-of-place sweep writes interior nodes only and reads t as the old
+// iterate on every second sweep, so t's boundary faces must hold u's.  t is
+// also scratch of the separable solver (a coarse-grid solve, or the inner
+// solve of MHS_FLAG_SEPARABLE) and may hold anything there after a solve with
+// other options: every solve, and every smoothing hook, copies the faces of
+// u into t on the levels it sweeps out of place first.
+template <typename T>
+static void sync_twin_faces(mhs_ctx* c, Hierarchy& H, int l) {
+    if (!fused_level<T>(c, H, l)) return;
+    LevelArrays<T>& A = arrays<T>(H, l);
+    launch_copy_faces<T>(H.g[l], A.u, A.t, c->stream);
+}
+
 template <typename T>
 void smooth_hook(mhs_ctx* c, Hierarchy& H, int l) {
-    const Geom& g = H.g[l];
+    sync_twin_faces<T>(c, H, l);
     smooth_n<T>(c, H, l, arrays<T>(H, l).f, 1, false, 0.0, 0.0);
-    (void)g;
 }
 template void smooth_hook<double>(mhs_ctx*, Hierarchy&, int);
 template void smooth_hook<float>(mhs_ctx*, Hierarchy&, int);
@@ -581,6 +604,11 @@ static void prologue_3d(const Enq& e) {
                 launch_df_split(c->h2.g[0], 2, c->h2.d[0].u, c->h2.df.hi, c->h2.df.lo, c->stream);
             launch_df_copy_plane(c->h2.g[0], c->h2.df.hi, c->h2.df.lo, g, H.df.hi, H.df.lo, c->stream);
             if (!c->f_zero_finest) launch_df_split(g, 3, H.d[0].f, H.df.fh, H.df.fl, c->stream);
+        }
+        // twins of the levels swept out of place: u's boundary faces (level 0: the Dirichlet data)
+        for (int l = 0; l < H.nlev(); ++l) {
+            if (e.mode == MHS_MIXED) sync_twin_faces<float>(c, H, l);
+            else sync_twin_faces<double>(c, H, l);
         }
         const int nl = launch_lift_norm(g, H.d[0].coef, H.d[0].u, c->ns.partial, c->stream);
         launch_bnorm(c->ns.partial, nl, c->ctl + 1, c->stream);

@@ -54,17 +54,24 @@ void apply_opts(mhs_ctx* c, const mhs_solver_opts& o) {
 }
 
 // fastest of `repeats` timed solves after one untimed solve (graph capture);
-// +inf when a solve fails (no convergence within max_cycles)
+// +inf when a solve of the candidate does not reach the tolerance (no
+// convergence within max_cycles, or a non-finite residual): the candidate
+// loses, the search goes on.  Other errors propagate.
 double time_opts(mhs_ctx* c, const mhs_solver_opts& o, double tol, int mode, int repeats) {
     apply_opts(c, o);
     mhs_solve_info info{};
-    if (solve(c, tol, mode, &info) != MHS_OK) return INFINITY;
-    double best = INFINITY;
-    for (int r = 0; r < repeats; ++r) {
-        if (solve(c, tol, mode, &info) != MHS_OK) return INFINITY;
-        best = std::min(best, info.ms);
+    try {
+        solve(c, tol, mode, &info);
+        double best = INFINITY;
+        for (int r = 0; r < repeats; ++r) {
+            solve(c, tol, mode, &info);
+            best = std::min(best, info.ms);
+        }
+        return best;
+    } catch (const Error& e) {
+        if (e.status == MHS_ERR_NO_CONVERGENCE || e.status == MHS_ERR_NONFINITE) return INFINITY;
+        throw;
     }
-    return best;
 }
 
 int clamp_int(size_t v) { return v > size_t(INT_MAX) ? INT_MAX : int(v); }

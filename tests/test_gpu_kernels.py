@@ -334,6 +334,44 @@ def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
     assert _rel(out[0], oracle.rbgs3d(pr, u32, f32, 5)) < 1e-4
 
 
+@pytest.mark.parametrize("mode", [1, 0])
+def test_out_of_place_sweeps_after_separable_solves(M, mode):
+    """The twin array of the out-of-place sweeps is also scratch of the
+    separable solver (exact coarse-grid solves, MHS_FLAG_SEPARABLE).  A solve
+    that sweeps out of place on a handle that ran separable solves on the
+    same levels before must equal that solve on a fresh handle bit for bit."""
+    pr, bz = S.linear_mhs(65, seed=77)
+    tol = 1e-10
+    fused = dict(fused_min=1, flags=M.MHS_FLAG_POINT) if mode == 1 else \
+        dict(flags=M.MHS_FLAG_POINT | M.MHS_FLAG_FUSED_SWEEP64)
+
+    def phi_of(h):
+        out = np.zeros((65, 65, 65))
+        M.mhs_get_phi(h, out)
+        return out
+
+    def make():
+        h = M.mhs_create(65, 65, 65, 1.0, 1.0, 1.0, pr["alpha"], M.xi_params(pr["xi_kind"], pr["xi_a"], pr["xi_kappa"]))
+        M.mhs_set_lower_bz(h, bz)
+        return h
+
+    fresh = make()
+    M.mhs_set_options(fresh, **fused)
+    info_f = M.mhs_solve(fresh, tol, mode)
+    want = phi_of(fresh)
+    M.mhs_destroy(fresh)
+    h = make()
+    M.mhs_set_options(h, flags=M.MHS_FLAG_SEPARABLE)        # level 0's twin as scratch
+    M.mhs_solve(h, tol, mode)
+    M.mhs_set_options(h, sep_coarse=31 ** 3)                 # exact coarse-grid solve on 33^3: level 1's twin
+    M.mhs_solve(h, tol, mode)
+    M.mhs_set_options(h, **fused)
+    info = M.mhs_solve(h, tol, mode)
+    assert info["cycles_3d"] == info_f["cycles_3d"]
+    assert np.array_equal(phi_of(h), want)
+    M.mhs_destroy(h)
+
+
 XI_STRONG = dict(xi_kind=1, xi_a=0.99, xi_kappa=0.5)   # 1 - xi(0) = 0.01: strong vertical coupling
 
 
