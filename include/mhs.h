@@ -143,9 +143,10 @@ typedef struct {
                                    loop; the interior problem keeps the mixed-precision loop.  The double-float
                                    iterate (48-bit significand) bounds the relative residual of the
                                    lower-boundary problem near 5e-12 on 257^2 and 2e-11 on 513^2 nodes (the
-                                   interior problem's, whose right-hand side is smoother, near 1e-13 and 1e-12);
-                                   with this flag both reach tolerances of 1e-12 on those grids.  The lower
-                                   boundary is a small part of the work (1 / nz of the unknowns).  Not in groups */
+                                   interior problem's, whose right-hand side is smoother, near 1e-13 and 8e-13);
+                                   with this flag a mixed solve reaches 1e-12 on 257^3 and 2e-12 on 513 x 513 x 257
+                                   nodes.  The lower boundary is a small part of the work (1 / nz of the
+                                   unknowns).  Not in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
