@@ -184,14 +184,20 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (profiling recipe table); ow
 
 
 def profiled_traffic(kind_name: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's source is unchanged: the text of
+    the measured device function when the summary names it (body, body_sha256), else the whole file."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
         ent = d["kernels"][kind_name]
         import hashlib
-        h = hashlib.sha256(open(os.path.join(ROOT, ent["source"]), "rb").read()).hexdigest()
-        return ent["bytes_per_launch"] if h == ent["sha256"] else None
+        src = open(os.path.join(ROOT, ent["source"])).read()
+        if "body" in ent:
+            start = src.index("__device__ __forceinline__ void " + ent["body"] + "(")
+            text, want = src[start:src.index("\n}\n", start) + 3], ent["body_sha256"]
+        else:
+            text, want = src, ent["sha256"]
+        return ent["bytes_per_launch"] if hashlib.sha256(text.encode()).hexdigest() == want else None
     except Exception:
         return None
 

@@ -158,7 +158,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     std::vector<std::vector<GItem>> pre_pt(L), post_pt(L), pre_ln(L), post_ln(L), res(L), restr(L), prol(L),
         fmg_restr(L), fmg_prol(L);
     std::vector<GItem> sub, sub8, subz, subz8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
-        res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
+        res_norm0, res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
     std::vector<SubParams<T>> params;
     std::vector<std::vector<GSepItem<T>>> exact_items;   // per stage of the separable solves
     D.max_nu1 = D.max_nu2 = 0;
@@ -197,12 +197,15 @@ void build_dim(GPart* G, GDim& D, int dim) {
             (line ? pre_ln : pre_pt)[l].push_back(s);
             s.ia[0] = nu2;
             (line ? post_ln : post_pt)[l].push_back(s);
-            GItem r = item(q, fat(residual_grid_plain_t<T>(g, d3)), g, ctl);
+            const bool red_l = dbl && red_residual_level(c, H);   // red nodes only, as the solo V-cycle
+            GItem r = item(q, fat(red_l ? residual_red_grid(g, d3, false, 0) : residual_grid_plain_t<T>(g, d3)), g,
+                           ctl);
             r.coef = A.coef;
             r.p[0] = A.u;
             r.p[1] = f;
             r.p[2] = A.r;
             r.ia[1] = top;
+            r.ia[2] = red_l ? 1 : 0;
             res[l].push_back(r);
             GItem rs = item(q, fat(restrict_grid(gc, d3)), g, ctl);
             rs.g2 = gc;
@@ -302,9 +305,12 @@ void build_dim(GPart* G, GDim& D, int dim) {
             z.ia[0] = w;
             return z;
         };
-        // residual with norm partials at the end of a cycle (and of the first test)
+        // residual with norm partials of the first test, at the end of a cycle and after the
+        // full-multigrid cycle (FP64: the last two on red nodes only where the solo solve does so)
         GItem rn;
         int nb;
+        GItem rn_cyc, rn_fmg;
+        int nb_cyc = 0, nb_fmg = 0;
         if (mixed) {
             const dim3 grid = df_residual_grid(g0, d3, c->ns.max_blocks);
             rn = item(q, grid, g0, ctl);
@@ -317,25 +323,39 @@ void build_dim(GPart* G, GDim& D, int dim) {
             rn.p[4] = H.s[0].f;
             rn.p[5] = c->ns.partial;
             nb = int(grid.x * grid.y * grid.z);
+            rn_cyc = rn_fmg = rn;
+            nb_cyc = nb_fmg = nb;
         } else {
-            const dim3 grid = residual_grid(g0, d3, true, c->ns.max_blocks);
-            rn = item(q, grid, g0, ctl);
-            rn.coef = H.d[0].coef;
-            rn.p[0] = H.d[0].u;
-            rn.p[1] = H.d[0].f;
-            rn.p[2] = H.d[0].r;
-            rn.p[3] = c->ns.partial;
-            nb = int(grid.x * grid.y * grid.z);
+            auto rn64 = [&](bool red, int& count) {
+                const dim3 grid = red ? residual_red_grid(g0, d3, true, c->ns.max_blocks)
+                                      : residual_grid(g0, d3, true, c->ns.max_blocks);
+                GItem it = item(q, grid, g0, ctl);
+                it.coef = H.d[0].coef;
+                it.p[0] = H.d[0].u;
+                it.p[1] = H.d[0].f;
+                it.p[2] = H.d[0].r;
+                it.p[3] = c->ns.partial;
+                it.ia[2] = red ? 1 : 0;
+                count = int(grid.x * grid.y * grid.z);
+                return it;
+            };
+            rn = rn64(false, nb);
+            rn_cyc = rn64(red_residual_cycle(c, H), nb_cyc);
+            rn_fmg = rn64(red_residual_fmg(c, H), nb_fmg);
         }
-        res_norm.push_back(rn);
+        res_norm0.push_back(rn);
+        res_norm.push_back(rn_cyc);
         GItem ck = item(q, dim3(1, 1, 1), g0, ctl);
         ck.p[0] = c->ns.partial;
         ck.ia[0] = nb;
-        check.push_back(ck);
         check1.push_back(ck);
+        GItem ck_cyc = ck, ck_fmg = ck;
+        ck_cyc.ia[0] = nb_cyc;
+        ck_fmg.ia[0] = nb_fmg;
+        check.push_back(ck_cyc);
         if (fmg) {
-            fmg_res_norm.push_back(rn);
-            fmg_check.push_back(ck);
+            fmg_res_norm.push_back(rn_fmg);
+            fmg_check.push_back(ck_fmg);
         }
         if (dim == 2) {
             zero_u.push_back(zero_item(H.d[0].u, g0.n, sizeof(double)));
@@ -444,6 +464,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     D.lift = upload(G, lift);
     D.bnorm = upload(G, bnorm);
     D.check1 = upload(G, check1);
+    D.res_norm0 = upload(G, res_norm0);
     D.res_norm = upload(G, res_norm);
     D.check = upload(G, check);
     D.fmg_res_norm = upload(G, fmg_res_norm);
@@ -559,8 +580,8 @@ void gprologue(GPart* G, GDim& D) {
             glaunch_zero(D.zero_lo, G_ALL, st);
             glaunch_df_split(D.split, 0, st);
         }
-        if (mixed) glaunch_df_residual(D.res_norm, 0, G_ALL, st);
-        else glaunch_residual_norm<double>(D.res_norm, 0, G_ALL, st);
+        if (mixed) glaunch_df_residual(D.res_norm0, 0, G_ALL, st);
+        else glaunch_residual_norm<double>(D.res_norm0, 0, G_ALL, st);
         glaunch_bnorm(D.bnorm, st);
     } else {
         glaunch_copy_plane(D.copy_u, st);
@@ -573,8 +594,8 @@ void gprologue(GPart* G, GDim& D) {
         }
         glaunch_lift_norm(D.lift, st);
         glaunch_bnorm(D.bnorm, st);
-        if (mixed) glaunch_df_residual(D.res_norm, 1, G_ALL, st);
-        else glaunch_residual_norm<double>(D.res_norm, 1, G_ALL, st);
+        if (mixed) glaunch_df_residual(D.res_norm0, 1, G_ALL, st);
+        else glaunch_residual_norm<double>(D.res_norm0, 1, G_ALL, st);
     }
     glaunch_check(D.check1, 1, G_ALL, st);
     gfmg<T>(G, D);

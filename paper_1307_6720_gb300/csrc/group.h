@@ -130,8 +130,8 @@ struct GDim {
     size_t sub_smem = 0;
     // once per solve
     GTable zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1;
-    // cycle end (every instance), and after the full-multigrid cycle (instances using it)
-    GTable res_norm, check, fmg_res_norm, fmg_check;
+    // the first test; cycle end (every instance), and after the full-multigrid cycle (instances using it)
+    GTable res_norm0, res_norm, check, fmg_res_norm, fmg_check;
     // mixed mode
     GTable zero_e, correct, fmg_zero_e, fmg_correct, to_double;
 };

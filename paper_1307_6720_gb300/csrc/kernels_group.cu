@@ -84,6 +84,12 @@ __global__ void g_residual_kernel(const GItem* items, int n, int fmg_step, int g
             return;
         }
     }
+    if (it.ia[2]) {   // right after a red-black sweep: red nodes only (as the solo launch)
+        residual_red_body<T, D3, NORM>(it.g, static_cast<const PlaneCoef<T>*>(it.coef),
+                                       static_cast<const T*>(it.p[0]), static_cast<const T*>(it.p[1]),
+                                       static_cast<T*>(it.p[2]), static_cast<double*>(it.p[3]), k.b, k.gd);
+        return;
+    }
     residual_body<T, D3, NORM>(it.g, static_cast<const PlaneCoef<T>*>(it.coef), static_cast<const T*>(it.p[0]),
                                static_cast<const T*>(it.p[1]), static_cast<T*>(it.p[2]),
                                static_cast<double*>(it.p[3]), k.b, k.gd);

@@ -165,6 +165,12 @@ __global__ void residual_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, c
     residual_body<T, D3, NORM>(g, coef, u, f, r, partial, blockIdx, gridDim);
 }
 
+template <typename T, bool D3, bool NORM>
+__global__ void residual_red_kernel(Geom g, const PlaneCoef<T>* __restrict__ coef, const T* __restrict__ u,
+                                    const T* __restrict__ f, T* __restrict__ r, double* __restrict__ partial) {
+    residual_red_body<T, D3, NORM>(g, coef, u, f, r, partial, blockIdx, gridDim);
+}
+
 __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
     // one block, fixed summation order: thread t sums t, t+blockDim, ...; then a fixed tree
     double s = 0.0;
@@ -381,8 +387,21 @@ void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const
 
 template <typename T>
 int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r, double* partial,
-                    int max_blocks, cudaStream_t st) {
+                    int max_blocks, cudaStream_t st, bool red) {
     const int d3 = dim == 3;
+    if (red) {   // right after a red-black sweep: red nodes computed, black nodes 0
+        const dim3 grid = residual_red_grid(g, d3, partial != nullptr, max_blocks);
+        if (partial) {
+            if (d3) residual_red_kernel<T, true, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+            else residual_red_kernel<T, false, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+        } else {
+            if (d3) residual_red_kernel<T, true, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+            else residual_red_kernel<T, false, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, r, partial);
+        }
+        count_launches(1);
+        MHS_CUDA(cudaGetLastError());
+        return int(grid.x * grid.y * grid.z);
+    }
     // with norm partials, few enough blocks (a multiple of the SM count) that
     // the fixed-order finish stays short; every thread then covers several planes
     if constexpr (sizeof(T) == 4) {
@@ -502,7 +521,7 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
     template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                                 \
     template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
     template int launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*, double*,    \
-                                    int, cudaStream_t);                                                        \
+                                    int, cudaStream_t, bool);                                                  \
     template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t);           \
     template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \
     template void launch_coarse<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \

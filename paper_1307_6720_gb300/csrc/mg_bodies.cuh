@@ -72,6 +72,43 @@ __device__ __forceinline__ void residual_body(const Geom& g, const PlaneCoef<T>*
     if (threadIdx.x == 0 && threadIdx.y == 0) partial[b.x + gd.x * (b.y + gd.y * b.z)] = s;
 }
 
+// The residual right after a red-black sweep: the black nodes, updated last,
+// satisfy their own rows of A u = f given the final red values, so their
+// residual is zero to rounding and is stored as 0; the red nodes' residual is
+// computed as in residual_body (same operations).  Thread t of row (j, k)
+// takes the pair of nodes 1 + 2t and 2 + 2t, one red and one black (the
+// colour pass's mapping), so the FP64 work is that of half the nodes.  NORM:
+// the block's sum of r^2 over its red nodes, at the same partial index as
+// residual_body.  Every thread of the block must call it.
+template <typename T, bool D3, bool NORM>
+__device__ __forceinline__ void residual_red_body(const Geom& g, const PlaneCoef<T>* __restrict__ coef,
+                                                  const T* __restrict__ u, const T* __restrict__ f,
+                                                  T* __restrict__ r, double* __restrict__ partial, dim3 b, dim3 gd) {
+    const int t = b.x * blockDim.x + threadIdx.x;
+    const int j = 1 + b.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (j <= g.ny - 2 && 1 + 2 * t <= g.nx - 2) {
+        for (int k = D3 ? 1 + b.z : 0; k <= (D3 ? g.nz - 2 : 0); k += gd.z) {
+            const int red = ((1 + j + k) & 1);   // the red node of the pair is 1 + red + 2t
+            const int ir = 1 + red + 2 * t, ib = 2 - red + 2 * t;
+            if (ib <= g.nx - 2) r[at(g, ib, j, k)] = T(0);
+            if (ir > g.nx - 2) continue;
+            const PlaneCoef<T> c = coef[k];
+            const size_t o = at(g, ir, j, k);
+            T v = f ? f[o] : T(0);
+            if (D3) v = fma(-c.cz, u[o + g.plane] + u[o - g.plane], v);
+            v = fma(-c.cy, u[o + g.px] + u[o - g.px], v);
+            v = fma(-c.cx, u[o + 1] + u[o - 1], v);
+            const T rv = fma(-c.d, u[o], v);
+            r[o] = rv;
+            if (NORM) acc += double(rv) * double(rv);
+        }
+    }
+    if (!NORM) return;
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[b.x + gd.x * (b.y + gd.y * b.z)] = s;
+}
+
 // FP32 3D forms of the colour pass and the residual that give each thread
 // the four consecutive nodes i0 .. i0+3 (i0 = 4t) of a row: the centre row,
 // the four neighbour rows and f are read as 16-byte vectors (rows start on
@@ -287,6 +324,10 @@ inline dim3 residual_grid_plain_t(const Geom& g, int d3) {
 // reduction for 256 nodes; the fixed-order finish stays short too
 inline dim3 residual_grid(const Geom& g, int d3, bool norm, int max_blocks) {
     return mg_grid(g, d3, g.nx - 2, norm ? (max_blocks < 152 * 8 ? max_blocks : 152 * 8) : 0);
+}
+// the same for residual_red_body: one thread per pair of x positions
+inline dim3 residual_red_grid(const Geom& g, int d3, bool norm, int max_blocks) {
+    return mg_grid(g, d3, (g.nx - 2 + 1) / 2, norm ? (max_blocks < 152 * 8 ? max_blocks : 152 * 8) : 0);
 }
 inline dim3 restrict_grid(const Geom& gc, int d3) { return mg_grid(gc, d3, gc.nx - 2, 0); }
 inline dim3 prolong_grid(const Geom& gc, int d3) {

@@ -269,10 +269,12 @@ void launch_fill(T* a, size_t n, T v, cudaStream_t st);
 template <typename T>
 void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
 // residual r = f - A u; with partial != nullptr also per-block partial sums
-// of r^2; returns the number of partials written
+// of r^2; returns the number of partials written.  red: u comes straight out
+// of a red-black sweep, so the black nodes' residual is zero to rounding; they
+// are stored as 0 and only the red nodes are computed (half the work)
 template <typename T>
 int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u, const T* f, T* r,
-                    double* partial, int max_blocks, cudaStream_t st);
+                    double* partial, int max_blocks, cudaStream_t st, bool red = false);
 // finish partial sums into *out (fixed order)
 void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t st);
 template <typename T>

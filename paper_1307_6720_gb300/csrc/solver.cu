@@ -340,6 +340,15 @@ static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>
     }
 }
 
+// Residuals taken right after red-black point sweeps (FP64 cycles; the FP32
+// residuals of mixed mode stay full): red nodes computed, black nodes 0, as
+// the black nodes, updated last, satisfy their own rows to rounding.  The
+// solo solve and grouped solves take the same choices from these.
+static bool point_smoothing(const mhs_ctx* c, const Hierarchy& H) { return H.dim == 2 || !use_zline(c); }
+
+// a V-cycle level's residual after its pre-smoothing
+bool red_residual_level(const mhs_ctx* c, const Hierarchy& H) { return point_smoothing(c, H) && c->opts.nu1 >= 1; }
+
 template <typename T>
 void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     cudaStream_t st = c->stream;
@@ -364,7 +373,7 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     smooth_n<T>(c, H, l, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
     {
         TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, sweep_bytes, o.N * o.res_flops, st, o.fine);
-        launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st);
+        launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st, dbl && red_residual_level(c, H));
     }
     coarse_correction<T>(c, H, l, o);
     smooth_n<T>(c, H, l, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
@@ -378,7 +387,22 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
 // two.  Levels of nu1 + nu2 sweeps per cycle as in vcycle; the solve returns
 // the iterate whose residual passed the test.  Needs level 0 above the
 // sub-cycle cut-off.
-static bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H) { return H.cut64 >= 1 && H.nlev() > 1; }
+bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H) {
+    (void)c;
+    return H.cut64 >= 1 && H.nlev() > 1;
+}
+
+// the convergence test of a rotated cycle (after the pre-smoothing, or the
+// post-smoothing when nu1 = 0), unless the step is a separable direct solve
+bool red_residual_cycle(const mhs_ctx* c, const Hierarchy& H) {
+    return rotated_cycles(c, H) && point_smoothing(c, H) && c->opts.nu1 + c->opts.nu2 >= 1 &&
+           !((c->opts.flags & MHS_FLAG_SEPARABLE) && sep_fp64_available(c));
+}
+
+// the test after the full-multigrid first cycle (after level 0's post-smoothing)
+bool red_residual_fmg(const mhs_ctx* c, const Hierarchy& H) {
+    return rotated_cycles(c, H) && point_smoothing(c, H) && c->opts.nu2 >= 1;
+}
 
 static void vcycle_rotated(mhs_ctx* c, Hierarchy& H) {
     const LevelOps<double> o(c, H, 0);
@@ -483,7 +507,7 @@ static int lower_mode(const mhs_ctx* c, int mode) {
 
 // residual of the current iterate (FP64, or FP64 rounded into the FP32
 // right-hand side in mixed mode) with norm partials; returns their count
-static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
+static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode, bool red = false) {
     const Geom& g = H.g[0];
     LevelArrays<double>& A = H.d[0];
     const double N = double(g.interior());
@@ -499,9 +523,9 @@ static int residual_partials(mhs_ctx* c, Hierarchy& H, int mode) {
         return launch_df_residual(g, H.dim, H.df.coef, H.df.hi, H.df.lo, fz ? nullptr : H.df.fh,
                                   fz ? nullptr : H.df.fl, H.s[0].f, c->ns.partial, c->ns.max_blocks, c->stream);
     }
-    TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl, c->stream, H.dim == 3);
+    TimedScope t(c->timer, MHS_KT_RESID64, N * (16.0 + fb), N * fl * (red ? 0.5 : 1.0), c->stream, H.dim == 3);
     return launch_residual<double>(g, H.dim, A.coef, A.u, fz ? nullptr : A.f, A.r, c->ns.partial, c->ns.max_blocks,
-                                   c->stream);
+                                   c->stream, red);
 }
 
 static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
@@ -529,7 +553,7 @@ static void cycle_body(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     } else {
         vcycle<double>(c, H, 0);
     }
-    const int nb = residual_partials(c, H, e.mode);
+    const int nb = residual_partials(c, H, e.mode, e.mode == MHS_FP64 && red_residual_cycle(c, H));
     launch_check(c->ns.partial, nb, ctl, 0, e.hnd, e.graph ? 1 : 0, c->stream);
 }
 
@@ -553,7 +577,7 @@ static void fmg_cycle(const Enq& e, Hierarchy& H, SolveCtl* ctl) {
     } else {
         fmg<double>(c, H, H.d[0].r);
     }
-    const int nb = residual_partials(c, H, e.mode);
+    const int nb = residual_partials(c, H, e.mode, e.mode == MHS_FP64 && red_residual_fmg(c, H));
     launch_check(c->ns.partial, nb, ctl, 2, e.hnd, e.graph ? 1 : 0, c->stream);
 }
 

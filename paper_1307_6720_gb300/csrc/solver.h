@@ -75,6 +75,14 @@ bool sep_fp64_available(const mhs_ctx* c);          // FP64 direct solves: sep_l
 void sep_correct64(mhs_ctx* c, Hierarchy& H);       // FP64 mode: P += A^{-1} r on the finest level
 void ensure_staging(mhs_ctx* c);
 
+// FP64 cycles of the finest level with the test after the pre-smoothing (level 0 above the sub-cycle cut-off)
+bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H);
+// residuals right after red-black point sweeps, computed on red nodes only (FP64): a V-cycle level after its
+// pre-smoothing, the test of a rotated cycle, the test after the full-multigrid first cycle
+bool red_residual_level(const mhs_ctx* c, const Hierarchy& H);
+bool red_residual_cycle(const mhs_ctx* c, const Hierarchy& H);
+bool red_residual_fmg(const mhs_ctx* c, const Hierarchy& H);
+
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)
 void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
 void launch_pack(const double* src, double* dst, int nx, int px, size_t rows, cudaStream_t st);   // pitched -> dense

@@ -95,6 +95,29 @@ def test_residual_parity_3d(M, shape, prec):
     M.mhs_destroy(h)
 
 
+@pytest.mark.parametrize("shape", [(33, 17, 9), (65, 33, 33), (17, 9, 13)])
+def test_residual_after_sweep_vanishes_on_black_nodes(M, shape):
+    """FP64 cycles compute the residual that follows a red-black sweep on red
+    nodes only and store 0 on black ones.  Its premise, checked on the GPU
+    path: after one sweep (red, then black) the full residual of every black
+    node (i + j + k odd) is rounding, at most 1e-12 of the largest red one."""
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz)
+    rng = np.random.default_rng(11)
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, 0, rng.standard_normal((nz, ny, nx)))
+    M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, 0, rng.standard_normal((nz, ny, nx)) * 50)
+    M.mhs_level_op(h, 3, 0, M.MHS_OP_SMOOTH, 0)
+    M.mhs_level_op(h, 3, 0, M.MHS_OP_RESIDUAL, 0)
+    r = _read(M, h, 3, 0, M.MHS_FIELD_R, 0)
+    M.mhs_destroy(h)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    inner = (i > 0) & (i < nx - 1) & (j > 0) & (j < ny - 1) & (k > 0) & (k < nz - 1)
+    black = inner & ((i + j + k) % 2 == 1)
+    red = inner & ((i + j + k) % 2 == 0)
+    assert np.abs(r[red]).max() > 0
+    assert np.abs(r[black]).max() <= 1e-12 * np.abs(r[red]).max()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dim", [3, 2])
 def test_restriction_and_prolongation_parity(M, dim, prec):
