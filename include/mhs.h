@@ -243,7 +243,8 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * parameters when that moves it to another anisotropy class) and captures
  * the graphs.  The handles must outlive the group and must not be used for
  * other work while a group solve runs.  Not supported: MHS_FLAG_WARM,
- * inner_cycles other than 1 (MHS_ERR_INVALID_ARG).
+ * MHS_FLAG_SEPARABLE, MHS_FLAG_LOWER_FP64 in mixed mode, inner_cycles other
+ * than 1 (MHS_ERR_INVALID_ARG).
  * Errors: MHS_ERR_INVALID_ARG (n < 1, NULL or repeated handle, bad mode,
  * nstreams outside [0, 64]), MHS_ERR_OUT_OF_MEMORY, MHS_ERR_CUDA. */
 typedef struct mhs_group* mhs_group_t;
