@@ -78,3 +78,29 @@ def test_reference_arm_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_profiled_traffic_follows_the_measured_kernel_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu record only while
+    the measured device function is unchanged: editing another function of the
+    file keeps it, editing the function itself drops it (None)."""
+    import json
+    import shutil
+    import bench
+    assert bench.profiled_traffic("smooth64") is not None
+    root = tmp_path
+    (root / "profiles").mkdir()
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    src_rel = rec["kernels"]["smooth64"]["source"]
+    (root / os.path.dirname(src_rel)).mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
+    src = open(os.path.join(bench.ROOT, src_rel)).read()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    (root / src_rel).write_text(src + "\n// another function edited\n")
+    assert bench.profiled_traffic("smooth64") == rec["kernels"]["smooth64"]["bytes_per_launch"]
+    body = src.index("void colour_body(")
+    edited = src[:body] + src[body:].replace("if (j > g.ny - 2) return;", "if (j >= g.ny - 1) return;", 1)
+    assert edited != src
+    (root / src_rel).write_text(edited)
+    assert bench.profiled_traffic("smooth64") is None
+    assert bench.profiled_traffic("no_such_kernel") is None
