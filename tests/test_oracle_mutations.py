@@ -44,6 +44,9 @@ MUTANTS = {
     "rk4_stage_weight": ("(((k1[a] + 2.0 * k2[a]) + 2.0 * k3[a]) + k4[a])", "(((k1[a] + 2.0 * k2[a]) + k3[a]) + 2.0 * k4[a])"),
     "exact_level_one_cycle": ("if (rn <= 1e-15 * fn || rn > 0.5 * prev) break;", "if (it > 0) break;"),
     "exact_level_ignored": ("if (l == mg->exact_level) { exact_solve", "if (l == -2) { exact_solve"),
+    "bnorm_scaled": ("const double bnorm = mg_norm(mg, 0, mg->r[0]);", "const double bnorm = 2.0 * mg_norm(mg, 0, mg->r[0]);"),
+    "lift_bottom_face_only": ("for (int k = (mg->dim == 3 ? 1 : 0); k < (mg->dim == 3 ? L->nz - 1 : 1); ++k)\n        for (int j = 1; j < L->ny - 1; ++j)\n            for (int i = 1; i < L->nx - 1; ++i) lift[",
+                              "for (int k = (mg->dim == 3 ? 1 : 0); k < (mg->dim == 3 ? L->nz : 1); ++k)\n        for (int j = 0; j < L->ny; ++j)\n            for (int i = 0; i < L->nx; ++i) lift["),
     "gs_divides_wrong_diag": ("u[c] = ((f ? f[c] : 0.0) - off) / L->diag[k];", "u[c] = ((f ? f[c] : 0.0) - off) / L->diag[0];"),
 }
 

@@ -111,6 +111,84 @@ def _max_err_continuum(n, alpha=0.5, c=0.3, Lx=1.0, Ly=1.5, Lz=1.0):
     return np.abs(P - Pc(X, Y, Z)).max()
 
 
+def _stencil3d_hand(pr, u):
+    """A u at the interior nodes of a full [nz][ny][nx] array, the coefficients
+    of eq. (scalar_pot) written out: (1 - xi_k)/h_x^2, (1 - xi_k)/h_y^2, 1/h_z^2
+    and the centre -2 (cx + cy + cz) + alpha^2."""
+    nx, ny, nz = pr["nx"], pr["ny"], pr["nz"]
+    hx, hy, hz = pr["Lx"] / (nx - 1), pr["Ly"] / (ny - 1), pr["Lz"] / (nz - 1)
+    z = np.arange(1, nz - 1) * hz
+    om = 1.0 - exact._xi(pr, z)
+    cx, cy, cz = om / hx**2, om / hy**2, 1.0 / hz**2
+    c = u[1:-1, 1:-1, 1:-1]
+    out = (cx[:, None, None] * (u[1:-1, 1:-1, 2:] + u[1:-1, 1:-1, :-2])
+           + cy[:, None, None] * (u[1:-1, 2:, 1:-1] + u[1:-1, :-2, 1:-1])
+           + cz * (u[2:, 1:-1, 1:-1] + u[:-2, 1:-1, 1:-1])
+           + (-2.0 * (cx + cy + cz) + pr["alpha"] ** 2)[:, None, None] * c)
+    return out, cz
+
+
+def test_relative_residual_normaliser_of_the_paper_problem():
+    """The quantity every throughput figure is quoted at: ||b - A P|| / ||b||
+    with b the interior right-hand side after lifting the Dirichlet data
+    (Sect. 2.2: P = 0 start, P0 on z = 0, P = 0 on top and sides).  For the
+    paper's problem b lives on the plane k = 1 only, b = -P0/h_z^2 there, so
+    ||b|| = ||P0[interior]|| / h_z^2.  From the P = 0 start the first relative
+    residual is exactly 1; after one V-cycle it equals the hand-written
+    residual of the returned P over that norm."""
+    pr = S.problem(17, 13, 21, Lx=1.0, Ly=0.75, Lz=1.25, alpha=0.5, **XI2)
+    bz = S.magnetogram_random(17, 13, 1.0, 0.75, seed=23)
+    P0 = exact.separable_solve2d(pr, bz)
+    u = np.zeros((21, 13, 17))
+    u[0] = P0
+    _, c0, rel0, hist0, _ = oracle.solve3d(pr, u, tol=1e-12, max_cycles=0)
+    assert c0 == 0 and rel0 == 1.0 and hist0[0] == 1.0
+    P1, c1, rel1, hist1, _ = oracle.solve3d(pr, u, tol=1e-30, max_cycles=1)
+    assert c1 == 1 and hist1[0] == 1.0
+    Au, cz = _stencil3d_hand(pr, P1)
+    bnorm = cz * np.linalg.norm(P0[1:-1, 1:-1])
+    want = np.linalg.norm(-Au) / bnorm
+    assert 0.0 < rel1 < 0.2
+    assert abs(rel1 - want) <= 1e-12 * want, (rel1, want)
+
+
+def test_relative_residual_lifts_every_face_and_the_source():
+    """General Dirichlet data on all six faces and an interior source f: the
+    oracle's relative residual is ||b - A_int u_int|| / ||b|| with
+    b = f - (boundary part of A) u, A_int the Kronecker-assembled interior
+    matrix and the boundary part taken from the hand-written stencil of the
+    array whose interior is zeroed."""
+    pr = S.problem(13, 9, 11, Lx=1.0, Ly=0.7, Lz=0.9, alpha=0.3, **XI1)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((11, 9, 13))
+    f = rng.standard_normal((11, 9, 13))
+    lift = u.copy()
+    lift[1:-1, 1:-1, 1:-1] = 0.0
+    Ab, _ = _stencil3d_hand(pr, lift)
+    b = f[1:-1, 1:-1, 1:-1] - Ab
+    Aint = exact.kron_matrix3d(pr) @ u[1:-1, 1:-1, 1:-1].ravel()
+    want = np.linalg.norm(b.ravel() - Aint) / np.linalg.norm(b)
+    _, _, rel, hist, _ = oracle.solve3d(pr, u, f, tol=1e-12, max_cycles=0)
+    assert abs(rel - want) <= 1e-12 * want and hist[0] == rel, (rel, want)
+
+
+def test_lower_boundary_relative_residual_normaliser():
+    """Eq. (lower_bound): b = -B_z on the interior of z = 0 (edges zero), so
+    ||b|| = ||B_z[interior]||; the P = 0 start gives exactly 1, one V-cycle the
+    hand-written 5-point residual of the returned P0 over ||B_z[interior]||."""
+    pr = S.problem(33, 17, 3, Lx=1.0, Ly=0.5)
+    bz = S.magnetogram_random(33, 17, 1.0, 0.5, seed=29)
+    _, c0, rel0, h0 = oracle.solve2d(pr, bz, tol=1e-12, max_cycles=0)
+    assert c0 == 0 and rel0 == 1.0 and h0[0] == 1.0
+    P, c1, rel1, _ = oracle.solve2d(pr, bz, tol=1e-30, max_cycles=1)
+    hx, hy = 1.0 / 32, 0.5 / 16
+    lap = ((P[1:-1, 2:] - 2 * P[1:-1, 1:-1] + P[1:-1, :-2]) / hx**2
+           + (P[2:, 1:-1] - 2 * P[1:-1, 1:-1] + P[:-2, 1:-1]) / hy**2)
+    want = np.linalg.norm(-bz[1:-1, 1:-1] - lap) / np.linalg.norm(bz[1:-1, 1:-1])
+    assert c1 == 1 and 0.0 < rel1 < 0.2
+    assert abs(rel1 - want) <= 1e-11 * want, (rel1, want)
+
+
 def test_constant_xi_continuum_second_order():
     """Constant xi = c: P = P0(x,y) sinh(k(Lz - z))/sinh(k Lz), k^2 = (1-c)K^2 - alpha^2,
     solves eq. (scalar_pot) with eq. (lower_bound) on z = 0 and P = 0 on the
