@@ -116,6 +116,9 @@ typedef struct {
                             the levels below it are never visited; the one-CTA sub-cycle handles the coarse end
                             when no level qualifies or when the sub-cycle cut-off lies above it.  -1: never
                             [300000] */
+    int tile;            /* thread-block shape of the red-black point passes (threads along x, each owning an
+                            x pair of nodes, x rows): 1 = 32 x 8, 2 = 64 x 4, 3 = 16 x 16, 4 = 32 x 16,
+                            5 = 128 x 2 (results do not depend on it) [1] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */
@@ -149,17 +152,25 @@ typedef struct {
                                    unknowns).  Not in groups */
 #define MHS_FLAG_NO_TMA 16      /* FP32 levels sweep with plain global loads instead of TMA-staged planes (same
                                    results; for comparison) */
+#define MHS_FLAG_STAGED_TRANSFORMS 1024 /* separable solves of a level (the exact coarse-grid solves, MHS_OP_EXACT)
+                                   launch one kernel per sine-transform pass instead of the per-plane kernels
+                                   on thread-block clusters (same results bit for bit; for comparison) */
 #define MHS_FLAG_NO_GRAPH 4     /* launch the solve kernel by kernel with host-side convergence checks instead of
                                    one captured CUDA graph (same kernels, same results; for profilers that cannot
                                    see kernels inside conditional graph nodes) */
 
 typedef struct {
-    int cycles_2d;       /* V-cycles (or outer steps) of the lower-boundary solve */
-    int cycles_3d;       /* V-cycles (or outer steps) of the interior solve */
+    int cycles_2d;       /* iterations of the lower-boundary solve: FP64 V-cycles (or separable direct steps)
+                            when it runs in FP64, defect-correction steps in mixed mode */
+    int cycles_3d;       /* the same for the interior solve */
     double rel_res_2d;   /* final ||b - A P||_2 / ||b||_2 of eq. (lower_bound) */
     double rel_res_3d;   /* same for eq. (scalar_pot), b = right-hand side after lifting the z = 0 data */
     double conv_factor;  /* geometric-mean residual reduction per interior cycle */
     double ms;           /* device time of the solve (CUDA events on the handle's stream) */
+    int outer_iters_2d;  /* outer defect-correction steps of the lower-boundary solve (each: double-float
+                            residual, inner_cycles FP32 V-cycles or one FP32 separable solve, correction);
+                            0 when that problem runs in FP64 cycles (FP64 mode, MHS_FLAG_LOWER_FP64) */
+    int outer_iters_3d;  /* the same for the interior solve (0 in FP64 mode) */
 } mhs_solve_info;
 
 /* Create a solver for an nx*ny*nz node grid on [0,Lx]x[0,Ly]x[0,Lz].
@@ -235,8 +246,10 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * mode), are packed into parts of at most part_bytes of working set (0:
  * half the L2 cache), so that a part holds instances of similar size; each
  * part is one graph, and the parts are launched round-robin on nstreams
- * streams (0: 16), so that several parts run at once.  part_bytes = SIZE_MAX makes one
- * part of all instances.
+ * streams (0: 16), so that several parts run at once.  A part that holds a
+ * single instance (an instance whose working set alone fills the part
+ * budget) runs that instance's own solve, as mhs_solve would, on its launch
+ * stream.  part_bytes = SIZE_MAX makes one part of all instances.
  *
  * mhs_group_create snapshots the handles' options, cut-offs and smoother
  * choice (recreate the group after changing a member's options, or its
@@ -418,6 +431,10 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
  *   MHS_OP_PROLONG:  u[level] += (bi/tri)linear interpolation of u[level+1] (Sect. 4)
  *   MHS_OP_COARSE:   coarsest-level solve of A u = f (u from 0)
  *   MHS_OP_VCYCLE:   one V(nu1,nu2)-cycle on A u = f from level down
+ *   MHS_OP_RESID_RESTRICT: f[level+1] = full-weighting restriction of
+ *                    f - A u on level (residual and restriction in one pass,
+ *                    the residual not stored; u[level+1] zeroed; as the
+ *                    V-cycles run them)                                (Sect. 4)
  *   MHS_OP_EXACT:    u = A^{-1} f on the interior by the separable solver
  *                    (zero boundary values; the level's r and t are
  *                    scratch); levels whose sine transforms are fast
@@ -434,6 +451,7 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
 #define MHS_OP_COARSE 4
 #define MHS_OP_VCYCLE 5
 #define MHS_OP_EXACT 6
+#define MHS_OP_RESID_RESTRICT 7
 MHS_API mhs_status mhs_level_write(mhs_handle h, int dim, int level, int field, int prec, const double* src);
 MHS_API mhs_status mhs_level_read(mhs_handle h, int dim, int level, int field, int prec, double* dst);
 MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec);
@@ -475,25 +493,31 @@ MHS_API const char* mhs_kernel_kind_name(int kind);
  * service for callers that may not allocate device memory: applications
  * whose device memory is owned entirely by their own pool allocator, and
  * loops that cannot afford the device-wide synchronisation that cudaMalloc
- * or cudaFree may imply).  It evaluates, for a caller-supplied potential P,
- * the interior residual of eq. (scalar_pot) exactly as mhs_solve's stopping
- * test does:
- *   out[0] = ||b - A P||_2 over the interior nodes (the z = 0 plane of P is
- *            the Dirichlet data, the other faces are taken from P as well),
- *   out[1] = ||b||_2, b = the right-hand side after lifting the z = 0 data,
+ * or cudaFree may imply).  It evaluates, for a caller-supplied potential P
+ * whose six faces are Dirichlet data, the relative residual of the interior
+ * problem of eq. (scalar_pot) with zero interior source:
+ *   out[0] = ||b - A P||_2 over the interior nodes,
+ *   out[1] = ||b||_2, b = the right-hand side after lifting the Dirichlet
+ *            data (every face value of P enters the row of its interior
+ *            neighbour, weighted by that row's coefficient),
  *   out[2] = out[0] / out[1] (0 when ||b|| = 0).
+ * For a P returned by mhs_get_phi (faces zero except z = 0) this is the
+ * quantity mhs_solve's stopping test and rel_res_3d report.
  * P: device pointer, dense [nz][ny][nx] doubles; out: device pointer to 3
  * doubles; stream: cudaStream_t (NULL = legacy default stream).  The call is
  * asynchronous on that stream and allocates nothing: no cudaMalloc, no
  * cudaFree, no allocating library routine.  Its scratch is one fixed
  * device array of about 176 KB inside the library, which every GPU that
  * loads the library holds until the process exits.  Limits: nx, ny, nz >= 3
- * and nz <= 4097 (MHS_ERR_INVALID_ARG beyond); P and out must be device
+ * and nz <= 4097; finite, positive lengths; finite alpha and xi parameters,
+ * a known xi kind (MHS_ERR_INVALID_ARG otherwise); P and out must be device
  * pointers (MHS_ERR_INVALID_ARG otherwise).  The first call on each device
  * looks up the scratch array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  Every call
- * shares the one scratch array: calls whose work overlaps on the GPU (other
- * streams, other threads) race on it, so serialise them. */
+ * caches it for the life of the process; make that first call before any
+ * stream capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of that device (the cached address would be stale).
+ * Every call shares the one scratch array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race on it, so serialise them. */
 MHS_API mhs_status mhs_interior_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz,
                                                  double alpha, const mhs_xi_params* xi, const double* P,
                                                  double* out, void* stream);
@@ -508,6 +532,16 @@ MHS_API const char* mhs_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles; for launch accounting around a timed region). */
 MHS_API long long mhs_kernel_launches(void);
+
+/* Device arithmetic-rate probe (a measurement aid for the roofline of the
+ * FP64 stencil kernels, which the FP64 pipe bounds on this part): the
+ * sustained fused multiply-add rate of the current device in flop/s (two
+ * flops per FMA), FP64 for precision = MHS_FP64, FP32 for MHS_MIXED.  Every
+ * thread of a grid of 8 blocks of 256 threads per SM runs eight independent
+ * FMA chains; one launch of about 10 ms (FP64) or 5 ms (FP32) is timed with
+ * CUDA events on `stream` after one warm-up launch.  Synchronises the
+ * stream.  Errors: MHS_ERR_INVALID_ARG, MHS_ERR_CUDA. */
+MHS_API mhs_status mhs_probe_fma_rate(int precision, void* stream, double* flops_per_s);
 
 /* Library version string (static storage). */
 MHS_API const char* mhs_version(void);

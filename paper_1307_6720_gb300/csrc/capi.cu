@@ -12,6 +12,7 @@
 #include "solver.h"
 
 namespace mhs {
+double fma_rate(int precision, cudaStream_t st);
 mhs_status interior_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
                                      const mhs_xi_params* xi, const double* P, double* out, cudaStream_t st);
 }
@@ -51,7 +52,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 12000000, 300000}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 12000000, 300000, 1}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -64,6 +65,7 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->cut32 > 0) o->cut32 = in->cut32;
     if (in->fused_min > 0) o->fused_min = in->fused_min;
     if (in->sep_coarse != 0) o->sep_coarse = in->sep_coarse < 0 ? -1 : in->sep_coarse;
+    if (in->tile > 0) o->tile = in->tile;
     o->flags = in->flags;
 }
 
@@ -144,6 +146,15 @@ extern "C" {
 const char* mhs_version(void) { return "mhs-gb300 0.1"; }
 
 long long mhs_kernel_launches(void) { return mhs::launches(); }
+
+mhs_status mhs_probe_fma_rate(int precision, void* stream, double* flops_per_s) {
+    if (!flops_per_s || (precision != MHS_FP64 && precision != MHS_MIXED))
+        return fail(MHS_ERR_INVALID_ARG, "precision must be MHS_FP64 or MHS_MIXED (FP32) and the result non-NULL");
+    return guarded([&] {
+        *flops_per_s = mhs::fma_rate(precision, static_cast<cudaStream_t>(stream));
+        return MHS_OK;
+    });
+}
 
 const char* mhs_last_error(void) { return g_last_error.c_str(); }
 
@@ -561,9 +572,9 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
     mhs_status s = level_check(h, dim, level, MHS_FIELD_U, prec);
     if (s != MHS_OK) return s;
     mhs::Hierarchy& H = dim == 3 ? h->h3 : h->h2;
-    if ((op == MHS_OP_RESTRICT || op == MHS_OP_PROLONG) && level >= H.nlev() - 1)
+    if ((op == MHS_OP_RESTRICT || op == MHS_OP_PROLONG || op == MHS_OP_RESID_RESTRICT) && level >= H.nlev() - 1)
         return fail(MHS_ERR_INVALID_ARG, "no coarser level");
-    if (op < MHS_OP_SMOOTH || op > MHS_OP_EXACT) return fail(MHS_ERR_INVALID_ARG, "unknown op");
+    if (op < MHS_OP_SMOOTH || op > MHS_OP_RESID_RESTRICT) return fail(MHS_ERR_INVALID_ARG, "unknown op");
     if (op == MHS_OP_EXACT && !mhs::sep_level_ok(H.g[level]))
         return fail(MHS_ERR_INVALID_ARG, "exact solve needs nx - 1 and ny - 1 powers of two, or nx, ny <= 66");
     return guarded([&] {
@@ -587,6 +598,9 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
             case MHS_OP_EXACT:
                 mhs::sep_tables<T>(h, H, level);
                 mhs::sep_exact<T>(h, H, level);
+                break;
+            case MHS_OP_RESID_RESTRICT:
+                mhs::launch_resid_restrict<T>(g, H.g[level + 1], dim, A.coef, A.u, A.f, C.f, C.u, st);
                 break;
             }
         };

@@ -155,7 +155,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     D.L = 0;
     for (mhs_ctx* c : G->hs) D.L = std::max(D.L, (dim == 3 ? c->h3 : c->h2).nlev());
     const int L = D.L;
-    std::vector<std::vector<GItem>> pre_pt(L), post_pt(L), pre_ln(L), post_ln(L), res(L), restr(L), prol(L),
+    std::vector<std::vector<GItem>> pre_pt(L), post_pt(L), pre_ln(L), post_ln(L), res(L), restr(L), resr(L), prol(L),
         fmg_restr(L), fmg_prol(L);
     std::vector<GItem> sub, sub8, subz, subz8, zero_u, lower_rhs, zero_hi, zero_lo, split, copy_u, copy_t, df_copy, lift, bnorm, check1,
         res_norm0, res_norm, check, fmg_res_norm, fmg_check, zero_e, correct, fmg_zero_e, fmg_correct, to_double;
@@ -197,23 +197,35 @@ void build_dim(GPart* G, GDim& D, int dim) {
             (line ? pre_ln : pre_pt)[l].push_back(s);
             s.ia[0] = nu2;
             (line ? post_ln : post_pt)[l].push_back(s);
-            const bool red_l = dbl && red_residual_level(c, H);   // red nodes only, as the solo V-cycle
-            GItem r = item(q, fat(red_l ? residual_red_grid(g, d3, false, 0) : residual_grid_plain_t<T>(g, d3)), g,
-                           ctl);
-            r.coef = A.coef;
-            r.p[0] = A.u;
-            r.p[1] = f;
-            r.p[2] = A.r;
-            r.ia[1] = top;
-            r.ia[2] = red_l ? 1 : 0;
-            res[l].push_back(r);
-            GItem rs = item(q, fat(restrict_grid(gc, d3)), g, ctl);
-            rs.g2 = gc;
-            rs.p[0] = A.r;
-            rs.p[1] = C.f;
-            rs.p[2] = C.u;
-            rs.ia[1] = top;
-            restr[l].push_back(rs);
+            if (dbl) {
+                const bool red_l = red_residual_level(c, H);   // red nodes only, as the solo V-cycle
+                GItem r = item(q, fat(red_l ? residual_red_grid(g, d3, false, 0) : residual_grid_plain_t<T>(g, d3)),
+                               g, ctl);
+                r.coef = A.coef;
+                r.p[0] = A.u;
+                r.p[1] = f;
+                r.p[2] = A.r;
+                r.ia[1] = top;
+                r.ia[2] = red_l ? 1 : 0;
+                res[l].push_back(r);
+                GItem rs = item(q, fat(restrict_grid(gc, d3)), g, ctl);
+                rs.g2 = gc;
+                rs.p[0] = A.r;
+                rs.p[1] = C.f;
+                rs.p[2] = C.u;
+                rs.ia[1] = top;
+                restr[l].push_back(rs);
+            } else {   // FP32 levels: the solo V-cycle's fused residual and restriction
+                GItem r = item(q, fat(resid_restrict_grid(gc, d3)), g, ctl);
+                r.g2 = gc;
+                r.coef = A.coef;
+                r.p[0] = A.u;
+                r.p[1] = f;
+                r.p[2] = C.f;
+                r.p[3] = C.u;
+                r.ia[1] = top;
+                resr[l].push_back(r);
+            }
             GItem pr = item(q, fat(prolong_grid(gc, d3)), gc, ctl);
             pr.g2 = g;
             pr.p[0] = C.u;
@@ -443,6 +455,7 @@ void build_dim(GPart* G, GDim& D, int dim) {
     up(post_ln, D.post_ln);
     up(res, D.res);
     up(restr, D.restr);
+    up(resr, D.resr);
     up(prol, D.prol);
     up(fmg_restr, D.fmg_restr);
     up(fmg_prol, D.fmg_prol);
@@ -509,6 +522,7 @@ void gvcycle_from(GPart* G, GDim& D, int s, int fmg_step, int gate, bool with_z)
         gsmooth<T>(G, D, D.pre_pt, D.pre_ln, l, D.max_nu1, fmg_step, gate);
         glaunch_residual<T>(D.res[l], d3, fmg_step, gate, st);
         glaunch_restrict<T>(D.restr[l], d3, fmg_step, gate, st);
+        glaunch_resid_restrict<T>(D.resr[l], d3, fmg_step, gate, st);
     }
     const SubParams<T>* params = static_cast<const SubParams<T>*>(D.params);
     glaunch_subcycle<T>(D.sub, params, d3, s, fmg_step, gate, D.sub_smem, 32, st);
@@ -709,6 +723,10 @@ GPart* part_create(mhs_ctx** hs, int n, int mode) {
         if (mode == MHS_MIXED && (c->opts.flags & MHS_FLAG_LOWER_FP64))
             throw Error(MHS_ERR_INVALID_ARG, "group: MHS_FLAG_LOWER_FP64 is not available in groups");
     }
+    if (n == 1) {
+        G->solo = true;
+        return G.release();
+    }
     gsubcycle_prepare();
     MHS_CUDA(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
     MHS_CUDA(cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));
@@ -780,6 +798,24 @@ void geager(GPart* G) {
 void part_launch(GPart* G, double tol, cudaStream_t st) {
     const int n = int(G->hs.size());
     G->tol = tol;
+    if (G->solo) {
+        mhs_ctx* c = G->hs[0];
+        const cudaStream_t user = c->stream;
+        const bool graphs = c->use_graphs;
+        c->stream = st;
+        c->use_graphs = !G->eager;
+        try {
+            solve_begin(c, tol, G->mode);
+        } catch (...) {
+            c->stream = user;
+            c->use_graphs = graphs;
+            throw;
+        }
+        c->stream = user;
+        c->use_graphs = graphs;
+        G->launch_stream = st;
+        return;
+    }
     const cudaStream_t own = G->stream;
     G->stream = st;
     for (int q = 0; q < n; ++q) {
@@ -815,6 +851,27 @@ void part_launch(GPart* G, double tol, cudaStream_t st) {
 mhs_status part_wait(GPart* G, mhs_solve_info* infos, mhs_status* statuses, double* ms_out) {
     const int n = int(G->hs.size());
     const double tol = G->tol;
+    if (G->solo) {
+        mhs_ctx* c = G->hs[0];
+        const cudaStream_t user = c->stream;
+        c->stream = G->launch_stream;
+        mhs_solve_info info{};
+        mhs_status s = MHS_OK;
+        try {
+            s = solve_end(c, tol, G->mode, &info);
+        } catch (const Error& e) {
+            s = e.status;
+            if (s == MHS_ERR_CUDA) {
+                c->stream = user;
+                throw;
+            }
+        }
+        c->stream = user;
+        if (infos) infos[0] = info;
+        if (statuses) statuses[0] = s;
+        if (ms_out) *ms_out = info.ms;
+        return s;
+    }
     MHS_CUDA(cudaEventSynchronize(G->ev1));
     MHS_CUDA(cudaStreamSynchronize(G->launch_stream));
     float ms = 0.f;
@@ -841,6 +898,8 @@ mhs_status part_wait(GPart* G, mhs_solve_info* infos, mhs_status* statuses, doub
             i.rel_res_3d = b.rel;
             i.conv_factor = (b.cycles > 0 && b.rel0 > 0 && b.rel > 0) ? std::pow(b.rel / b.rel0, 1.0 / b.cycles) : 0.0;
             i.ms = ms;
+            i.outer_iters_2d = G->mode == MHS_MIXED ? a.cycles : 0;
+            i.outer_iters_3d = G->mode == MHS_MIXED ? b.cycles : 0;
         }
         if (statuses) statuses[q] = s;
         if (s != MHS_OK && worst == MHS_OK) worst = s;

@@ -47,6 +47,10 @@ template <typename T>
 void glaunch_residual_norm(const GTable& t, int d3, int gate, cudaStream_t st);
 template <typename T>
 void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
+// residual and restriction in one pass (FP32 levels; items: p = u, f, coarse
+// f, coarse u)
+template <typename T>
+void glaunch_resid_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
 template <typename T>
 void glaunch_prolong(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
 template <typename T>
@@ -116,7 +120,7 @@ struct GDim {
     int L = 0;                                   // most levels of any instance
     int max_nu1 = 0, max_nu2 = 0, max_top = -1;  // largest sweep counts and FMG top level
     // per level l (items of the instances for which l is a global level)
-    std::vector<GTable> pre_pt, post_pt, pre_ln, post_ln, res, restr, prol;
+    std::vector<GTable> pre_pt, post_pt, pre_ln, post_ln, res, restr, resr, prol;   // resr: the fused pass (FP32)
     // full multigrid: restriction of the residual and prolongation of the
     // coarse solution, per level, for the instances using it
     std::vector<GTable> fmg_restr, fmg_prol;
@@ -141,6 +145,10 @@ struct GDim {
 struct GPart {
     std::vector<mhs_ctx*> hs;
     int mode = MHS_MIXED;
+    // a part of one instance runs that instance's own solve (its captured
+    // graph, or the host-driven sequence when eager) on the part's launch
+    // stream: the grouped launches would serve no second instance
+    bool solo = false;
     cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;

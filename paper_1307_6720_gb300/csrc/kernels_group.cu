@@ -96,6 +96,17 @@ __global__ void g_residual_kernel(const GItem* items, int n, int fmg_step, int g
 }
 
 template <typename T, bool D3>
+__global__ void __launch_bounds__(RR_THREADS) g_resid_restrict_kernel(const GItem* items, int n, int fmg_step,
+                                                                     int gate) {
+    GBlock k;
+    if (!locate(items, n, gate, -1, fmg_step, k)) return;
+    const GItem& it = *k.it;
+    resid_restrict_body<T, D3>(it.g, it.g2, static_cast<const PlaneCoef<T>*>(it.coef), static_cast<const T*>(it.p[0]),
+                               static_cast<const T*>(it.p[1]), static_cast<T*>(it.p[2]), static_cast<T*>(it.p[3]), k.b,
+                               k.gd);
+}
+
+template <typename T, bool D3>
 __global__ void g_restrict_kernel(const GItem* items, int n, int fmg_step, int gate) {
     GBlock k;
     if (!locate(items, n, gate, -1, fmg_step, k)) return;
@@ -272,6 +283,14 @@ void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStrea
 }
 
 template <typename T>
+void glaunch_resid_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st) {
+    if (!t.n) return;
+    if (d3) g_resid_restrict_kernel<T, true><<<t.blocks, RR_THREADS, 0, st>>>(t.items, t.n, fmg_step, gate);
+    else g_resid_restrict_kernel<T, false><<<t.blocks, RR_THREADS, 0, st>>>(t.items, t.n, fmg_step, gate);
+    after_launch();
+}
+
+template <typename T>
 void glaunch_prolong(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st) {
     if (!t.n) return;
     if (d3) g_prolong_kernel<T, true><<<t.blocks, kMG, 0, st>>>(t.items, t.n, fmg_step, gate);
@@ -382,6 +401,7 @@ void glaunch_gather_ctl(SolveCtl* const* ctls, int n, SolveCtl* out, cudaStream_
     template void glaunch_residual<T>(const GTable&, int, int, int, cudaStream_t);                            \
     template void glaunch_residual_norm<T>(const GTable&, int, int, cudaStream_t);                            \
     template void glaunch_restrict<T>(const GTable&, int, int, int, cudaStream_t);                            \
+    template void glaunch_resid_restrict<T>(const GTable&, int, int, int, cudaStream_t);                      \
     template void glaunch_prolong<T>(const GTable&, int, int, int, cudaStream_t);                             \
     template void glaunch_subcycle<T>(const GTable&, const SubParams<T>*, int, int, int, int, size_t, int, cudaStream_t);
 MHS_GINST(double)

@@ -171,6 +171,13 @@ __global__ void residual_red_kernel(Geom g, const PlaneCoef<T>* __restrict__ coe
     residual_red_body<T, D3, NORM>(g, coef, u, f, r, partial, blockIdx, gridDim);
 }
 
+template <typename T, bool D3>
+__global__ void __launch_bounds__(RR_THREADS) resid_restrict_kernel(Geom gf, Geom gc, const PlaneCoef<T>* __restrict__ coef,
+                                                                   const T* __restrict__ u, const T* __restrict__ f,
+                                                                   T* __restrict__ fc, T* __restrict__ uc) {
+    resid_restrict_body<T, D3>(gf, gc, coef, u, f, fc, uc, blockIdx, gridDim);
+}
+
 __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
     // one block, fixed summation order: thread t sums t, t+blockDim, ...; then a fixed tree
     double s = 0.0;
@@ -363,23 +370,24 @@ void launch_fill(T* a, size_t n, T v, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st) {
+void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st, int tile) {
     const int d3 = dim == 3;
+    const dim3 blk = tile_block(tile);
     if constexpr (sizeof(T) == 4) {
         if (d3 && use_v4(g)) {
-            const dim3 grid = quad_grid(g);
+            const dim3 grid = tile_grid(g, 1, (g.nx - 2) / 4 + 1, blk);
             for (int colour = 0; colour < 2; ++colour) {
-                colour_v4_kernel<<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+                colour_v4_kernel<<<grid, blk, 0, st>>>(g, coef, u, f, colour);
                 count_launches(1);
             }
             MHS_CUDA(cudaGetLastError());
             return;
         }
     }
-    const dim3 grid = smooth_grid(g, d3);
+    const dim3 grid = tile_grid(g, d3, (g.nx - 2 + 1) / 2, blk);
     for (int colour = 0; colour < 2; ++colour) {
-        if (d3) colour_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
-        else colour_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(g, coef, u, f, colour);
+        if (d3) colour_kernel<T, true><<<grid, blk, 0, st>>>(g, coef, u, f, colour);
+        else colour_kernel<T, false><<<grid, blk, 0, st>>>(g, coef, u, f, colour);
         count_launches(1);
     }
     MHS_CUDA(cudaGetLastError());
@@ -423,6 +431,17 @@ int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
     return int(grid.x * grid.y * grid.z);
+}
+
+template <typename T>
+void launch_resid_restrict(const Geom& gf, const Geom& gc, int dim, const PlaneCoef<T>* coef, const T* u, const T* f,
+                           T* fc, T* uc, cudaStream_t st) {
+    const int d3 = dim == 3;
+    const dim3 grid = resid_restrict_grid(gc, d3);
+    if (d3) resid_restrict_kernel<T, true><<<grid, RR_THREADS, 0, st>>>(gf, gc, coef, u, f, fc, uc);
+    else resid_restrict_kernel<T, false><<<grid, RR_THREADS, 0, st>>>(gf, gc, coef, u, f, fc, uc);
+    count_launches(1);
+    MHS_CUDA(cudaGetLastError());
 }
 
 void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t st) {
@@ -519,10 +538,12 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
 #define MHS_INST(T)                                                                                          \
     template void launch_coef<T>(const Geom&, int, double, const mhs_xi_params&, PlaneCoef<T>*, cudaStream_t); \
     template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                                 \
-    template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
+    template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t, int);    \
     template int launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*, double*,    \
                                     int, cudaStream_t, bool);                                                  \
     template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t);           \
+    template void launch_resid_restrict<T>(const Geom&, const Geom&, int, const PlaneCoef<T>*, const T*, const T*, \
+                                           T*, T*, cudaStream_t);                                                 \
     template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \
     template void launch_coarse<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t);         \
     template void launch_zero_interior<T>(const Geom&, int, T*, cudaStream_t);                                \

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "dst_body.cuh"
 #include "group.h"
 #include "mhs_internal.h"
 #include "solver.h"
@@ -316,7 +317,8 @@ __device__ __forceinline__ void divide_body(const ModeArgs<T>& a, int bx, int by
     const int m = bx * blockDim.x + threadIdx.x;
     const int n = by;
     if (m >= a.nfast) return;
-    a.t[size_t(n) * a.nfast + m] /= a.cf * a.mufast[m] + a.cs * a.muslow[n];
+    T& t = a.t[size_t(n) * a.nfast + m];
+    t = mode_divide(t, a.cf, a.mufast[m], a.cs, a.muslow[n]);
 }
 
 template <typename T>
@@ -473,6 +475,17 @@ void launch_stage(const SepStage<T>& s, cudaStream_t st) {
     MHS_CUDA(cudaGetLastError());
 }
 
+}  // namespace
+
+template <typename T>
+void launch_sep_stage(const SepStage<T>& s, cudaStream_t st) {
+    launch_stage<T>(s, st);
+}
+template void launch_sep_stage<double>(const SepStage<double>&, cudaStream_t);
+template void launch_sep_stage<float>(const SepStage<float>&, cudaStream_t);
+
+namespace {
+
 template <typename T>
 void level_solve(mhs_ctx* c, const Geom& g, int dim, const PlaneCoef<T>* coef, const SepTables& tab, const T* f,
                  T* t1, T* t2, T* out, bool accumulate) {
@@ -535,6 +548,7 @@ void sep_tables(mhs_ctx* c, Hierarchy& H, int l) {
         void* p = nullptr;
         MHS_CUDA(cudaMalloc(&p, std::max<size_t>(h.size(), 1) * sizeof(T)));
         c->allocations.push_back(p);
+        c->dev_bytes += round_up(std::max<size_t>(h.size(), 1) * sizeof(T), 256);
         MHS_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
         return p;
     };
@@ -560,10 +574,13 @@ void sep_tables(mhs_ctx* c, Hierarchy& H, int l) {
     t.mux = upload(mu(g.nx));
     t.muy = upload(mu(g.ny));
     if (pow2(g.nx - 1) && pow2(g.ny - 1)) {
-        t.twx = make_twiddles<T>(g.nx - 1);
+        size_t tb = 0;
+        t.twx = make_twiddles<T>(g.nx - 1, &tb);
         c->allocations.push_back(t.twx);
-        t.twy = make_twiddles<T>(g.ny - 1);
+        c->dev_bytes += round_up(tb, 256);
+        t.twy = make_twiddles<T>(g.ny - 1, &tb);
         c->allocations.push_back(t.twy);
+        c->dev_bytes += round_up(tb, 256);
     } else {
         t.sx = upload(sine(g.nx));
         t.sy = upload(sine(g.ny));
@@ -573,6 +590,7 @@ void sep_tables(mhs_ctx* c, Hierarchy& H, int l) {
         for (void** p : {&t.inv, &t.sup}) {
             MHS_CUDA(cudaMalloc(p, n * sizeof(T)));
             c->allocations.push_back(*p);
+            c->dev_bytes += round_up(n * sizeof(T), 256);
         }
         compute_pivots<T>(c, H, l, t);
     }
@@ -589,7 +607,15 @@ void sep_refresh(mhs_ctx* c, Hierarchy& H) {
 template <typename T>
 void sep_exact(mhs_ctx* c, Hierarchy& H, int l) {
     LevelArrays<T>& A = arrays_of<T>(H, l);
-    level_solve<T>(c, H.g[l], H.dim, A.coef, tables<T>(H, l), A.f, A.r, A.t, A.u, false);
+    const Geom& g = H.g[l];
+    const SepTables& tab = tables<T>(H, l);
+    if (!(c->opts.flags & MHS_FLAG_STAGED_TRANSFORMS) && tab.twx) {
+        // per-plane transforms in thread-block clusters (same results as the staged passes)
+        const SepStage<T> ms = mode_stage<T>(g, H.dim, A.coef, tab, g.ny - 2, g.nx - 2, static_cast<const T*>(tab.muy),
+                                             static_cast<const T*>(tab.mux), true, A.t);
+        if (plane_level_solve<T>(g, H.dim, tab, A.f, A.t, A.u, false, &ms, c->stream)) return;
+    }
+    level_solve<T>(c, g, H.dim, A.coef, tab, A.f, A.r, A.t, A.u, false);
 }
 
 template <typename T>

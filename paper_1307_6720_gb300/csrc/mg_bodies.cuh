@@ -10,6 +10,8 @@
 // Blocks are BX x BY threads.
 #pragma once
 
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "mhs_internal.h"
 
@@ -257,6 +259,159 @@ __device__ __forceinline__ void prolong_body(const Geom& gc, const Geom& gf, con
     }
 }
 
+// Residual and full-weighting restriction in one pass (Sect. 4: the
+// residual of the smoothed iterate, restricted to the coarse right-hand
+// side), without storing the residual: a block owns a tile of RX x RR_Y
+// coarse nodes and a chunk of coarse planes, and marches up the fine planes
+// of the chunk's support.  The tile's fine window is the fine nodes 2I - 1 ..
+// 2I + 1, 2J - 1 .. 2J + 1 of its coarse nodes (2 RX + 1 by 2 RR_Y + 1).  On
+// each fine plane the residual r = f - A u of the window is formed by quads
+// of four consecutive x nodes (x from 2 RX bx, a multiple of four, so FP32
+// quads are 16-byte vectors of u, of its four neighbour rows and of f, the
+// outer x neighbours scalars; stencil reuse across quads, rows and planes
+// comes from L1) into shared memory; then the x row sums at the coarse x
+// positions, the y sums at the coarse nodes, and three consecutive fine
+// planes give f_c.  Per node these are the operations of residual_body and
+// of restrict_body, in their order, so the result equals the two separate
+// launches bit for bit.  Fine planes shared by two chunks and fine columns
+// and rows shared by two tiles are computed by both.  uc != nullptr: the
+// coarse iterate is zeroed at the same nodes.  RX = 32 coarse nodes along x
+// (threads 32 x 8, one per coarse node in the last step).  The V-cycles run
+// it on FP32 levels, which are bound by memory traffic; on FP64 levels the
+// FP64 pipe is the bound and the pass saves no FP64 operation.  Blocks of
+// RR_THREADS threads; every thread must call it.
+constexpr int RR_X = 32, RR_Y = 8, RR_THREADS = 256;
+
+template <typename T, bool D3>
+__device__ __forceinline__ void resid_restrict_body(const Geom& gf, const Geom& gc, const PlaneCoef<T>* __restrict__ coef,
+                                                    const T* __restrict__ u, const T* __restrict__ f,
+                                                    T* __restrict__ fc, T* __restrict__ uc, dim3 b, dim3 gd) {
+    constexpr int WX = 2 * RR_X + 1, WY = 2 * RR_Y + 1;   // residual window
+    constexpr int NQ = (WX + 1 + 3) / 4;                   // quads per window row (from one node left of it)
+    constexpr int RP = NQ * 4 + 1;                         // row pitch of r (odd)
+    __shared__ T rw[WY][RP];                               // rw[y][x]: r at (x0 + x, fy0 + y)
+    __shared__ T rs[WY][RR_X];                             // row sums at the coarse x positions
+    const int tid = threadIdx.x;
+    const int tx = tid % RR_X, ty = tid / RR_X;
+    const int Ib = 1 + int(b.x) * RR_X, Jb = 1 + int(b.y) * RR_Y;
+    const int fy0 = 2 * Jb - 1;                            // first window row
+    const int x0 = 2 * Ib - 2;                             // first quad column: one node left of the window
+    const int I = Ib + tx, J = Jb + ty;
+    const bool node = I <= gc.nx - 2 && J <= gc.ny - 2;
+    // residual of the quad (x0 + 4 q .. + 3, fy0 + y) of fine plane kf into rw (0 off the interior)
+    auto resid_quad = [&](int q, int y, int kf, const PlaneCoef<T>& c) {
+        const int i0 = x0 + 4 * q, j = fy0 + y;
+        T res[4] = {T(0), T(0), T(0), T(0)};
+        if (j <= gf.ny - 2 && i0 <= gf.nx - 2) {
+            const size_t o = at(gf, i0, j, kf);
+            T cc[4], nn[4], ss[4], uu[4], dd[4], ff[4];
+            if constexpr (sizeof(T) == 4) {
+                // the quad lies inside the padded row (px a multiple of four, i0 < nx)
+                auto ld4 = [](const T* ptr, T* out) {
+                    const float4 v = *reinterpret_cast<const float4*>(ptr);
+                    out[0] = v.x, out[1] = v.y, out[2] = v.z, out[3] = v.w;
+                };
+                ld4(u + o, cc);
+                ld4(u + o + gf.px, nn);
+                ld4(u + o - gf.px, ss);
+                if (D3) {
+                    ld4(u + o + gf.plane, uu);
+                    ld4(u + o - gf.plane, dd);
+                }
+                if (f) ld4(f + o, ff);
+            } else {
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    cc[l] = u[o + l];
+                    nn[l] = u[o + l + gf.px];
+                    ss[l] = u[o + l - gf.px];
+                    if (D3) {
+                        uu[l] = u[o + l + gf.plane];
+                        dd[l] = u[o + l - gf.plane];
+                    }
+                    if (f) ff[l] = f[o + l];
+                }
+            }
+            const T west = i0 > 0 ? u[o - 1] : T(0);
+            const T east = i0 + 3 <= gf.nx - 2 ? u[o + 4] : T(0);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int i = i0 + l;
+                if (i < 1 || i > gf.nx - 2) continue;
+                const T e = l < 3 ? cc[l + 1] : east;
+                const T w = l > 0 ? cc[l - 1] : west;
+                T v = f ? ff[l] : T(0);
+                if (D3) v = fma(-c.cz, uu[l] + dd[l], v);
+                v = fma(-c.cy, nn[l] + ss[l], v);
+                v = fma(-c.cx, e + w, v);
+                res[l] = fma(-c.d, cc[l], v);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) rw[y][4 * q + l] = res[l];
+    };
+    auto resid_plane = [&](int kf) {
+        const PlaneCoef<T> c = coef[kf];
+        for (int e = tid; e < WY * NQ; e += RR_THREADS) {
+            const int y = e / NQ, q = e - y * NQ;
+            resid_quad(q, y, kf, c);
+        }
+    };
+    // full-weighting y-x sum of the window at this thread's coarse node (window node x at rw
+    // column x + 1)
+    auto plane_sum = [&]() {
+        __syncthreads();
+        for (int y = ty; y < WY; y += RR_THREADS / RR_X) {
+            const int w = 2 * tx + 2;
+            rs[y][tx] = fma(T(2), rw[y][w], rw[y][w - 1] + rw[y][w + 1]);
+        }
+        __syncthreads();
+        const int w = 2 * ty + 1;
+        return node ? fma(T(2), rs[w][tx], rs[w - 1][tx] + rs[w + 1][tx]) : T(0);
+    };
+    if (D3) {
+        const int nkc = gc.nz - 2;
+        const int per = (nkc + int(gd.z) - 1) / int(gd.z);
+        const int K0 = 1 + int(b.z) * per, K1 = min(nkc, K0 + per - 1);
+        if (K0 <= K1) {
+            resid_plane(2 * K0 - 1);
+            T lo = plane_sum();
+            for (int K = K0; K <= K1; ++K) {
+                // plane_sum's barriers order these writes of rw after every read of the previous plane
+                resid_plane(2 * K);
+                const T mid = plane_sum();
+                resid_plane(2 * K + 1);
+                const T hi = plane_sum();
+                if (node) {
+                    fc[at(gc, I, J, K)] = fma(T(2), mid, lo + hi) * T(1.0 / 64.0);
+                    if (uc) uc[at(gc, I, J, K)] = T(0);
+                }
+                lo = hi;
+            }
+        }
+    } else {
+        resid_plane(0);
+        const T sum = plane_sum();
+        if (node) {
+            fc[at(gc, I, J, 0)] = sum * T(1.0 / 16.0);
+            if (uc) uc[at(gc, I, J, 0)] = T(0);
+        }
+    }
+}
+
+// grid of resid_restrict_body: coarse tiles in x and y, chunks of `per`
+// coarse planes along z, per chosen so that the grid is about eight blocks per
+// SM while a chunk spans at least four coarse planes where the level has them
+// (every chunk recomputes one fine plane of its neighbour)
+inline dim3 resid_restrict_grid(const Geom& gc, int d3) {
+    const int gx = (gc.nx - 2 + RR_X - 1) / RR_X, gy = (gc.ny - 2 + RR_Y - 1) / RR_Y;
+    if (!d3) return dim3(gx, gy, 1);
+    const int nkc = gc.nz - 2;
+    int per = std::max(1, (nkc * gx * gy + 152 * 8 - 1) / (152 * 8));
+    per = std::max(per, std::min(4, nkc));
+    return dim3(gx, gy, (nkc + per - 1) / per);
+}
+
 // f = -B_z on the interior of the lower-boundary plane (eq. lower_bound)
 __device__ __forceinline__ void lower_rhs_body(const Geom& g, const double* __restrict__ bz, double* __restrict__ f,
                                                dim3 b) {
@@ -304,6 +459,26 @@ inline dim3 mg_grid(const Geom& g, int d3, int xcount, int max_blocks) {
         if (gz > cap) gz = cap > 0 ? cap : 1;
         if (gz > 65535) gz = 65535;
     }
+    return dim3(gx, gy, gz);
+}
+
+// thread-block shapes of the red-black colour passes (option `tile`, 1-based)
+constexpr int N_TILES = 5;
+inline dim3 tile_block(int tile) {
+    switch (tile) {
+    case 2: return dim3(64, 4);
+    case 3: return dim3(16, 16);
+    case 4: return dim3(32, 16);
+    case 5: return dim3(128, 2);
+    default: return dim3(MG_BX, MG_BY);
+    }
+}
+// grid of a colour pass with block shape blk (xcount threads along x)
+inline dim3 tile_grid(const Geom& g, int d3, int xcount, dim3 blk) {
+    const int gx = (xcount + int(blk.x) - 1) / int(blk.x);
+    const int gy = (g.ny - 2 + int(blk.y) - 1) / int(blk.y);
+    int gz = d3 ? g.nz - 2 : 1;
+    if (gz > 65535) gz = 65535;
     return dim3(gx, gy, gz);
 }
 

@@ -205,9 +205,9 @@ namespace mhs {
 // Everything a captured solve depends on besides device memory: the options
 // and the choices derived from them and from the problem.
 struct GraphKey {
-    int v[10];
+    int v[11];
     bool operator==(const GraphKey& o) const {
-        for (int q = 0; q < 10; ++q)
+        for (int q = 0; q < 11; ++q)
             if (v[q] != o.v[q]) return false;
         return true;
     }
@@ -240,6 +240,7 @@ struct mhs_ctx {
     bool have_bz = false, have_solution = false;
     bool f_zero_finest = true;     // the finest interior right-hand side is identically zero (no hook wrote it)
     std::vector<void*> allocations;
+    size_t dev_bytes = 0;          // bytes of every device allocation the handle holds (server budget)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     mhs::KernelTimer timer;
     mhs::SolveCtl* ctl = nullptr;       // device control blocks [0] lower boundary, [1] interior
@@ -267,7 +268,7 @@ void launch_profiles(const Geom& g, const mhs_xi_params& xi, const mhs_atmos_par
 template <typename T>
 void launch_fill(T* a, size_t n, T v, cudaStream_t st);
 template <typename T>
-void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
+void launch_smooth(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st, int tile = 1);
 // residual r = f - A u; with partial != nullptr also per-block partial sums
 // of r^2; returns the number of partials written.  red: u comes straight out
 // of a red-black sweep, so the black nodes' residual is zero to rounding; they
@@ -281,6 +282,11 @@ template <typename T>
 void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st);
 template <typename T>
 void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st);
+// residual of u and its full-weighting restriction to fc in one launch (the
+// residual is not stored), uc zeroed
+template <typename T>
+void launch_resid_restrict(const Geom& gf, const Geom& gc, int dim, const PlaneCoef<T>* coef, const T* u, const T* f,
+                           T* fc, T* uc, cudaStream_t st);
 template <typename T>
 void launch_coarse(const Geom& g, int dim, const PlaneCoef<T>* coef, T* u, const T* f, cudaStream_t st);
 // lower-boundary right-hand side f = -B_z at interior nodes (FP64 and FP32 copies)
@@ -316,7 +322,7 @@ struct DstArgs {
     const void* tw = nullptr;   // complex twiddles e^{-2 pi i q / (2L)}, q < L
 };
 template <typename T>
-void* make_twiddles(int L);
+void* make_twiddles(int L, size_t* bytes = nullptr);
 
 // ---- stages of one separable solve (kernels_sep.cu, kernels_dst.cu) ----
 // C_b = scale A_b B_b (+ C_b with accumulate), b < batch, row-major with
@@ -363,6 +369,17 @@ template <typename T>
 void dst_shape(DstArgs<T>& a, dim3& grid, int& threads, size_t& smem);
 template <typename T>
 void launch_dst_stage(const SepStage<T>& s, cudaStream_t st);
+// any stage of a separable solve (transform, dense product, mode solves)
+template <typename T>
+void launch_sep_stage(const SepStage<T>& s, cudaStream_t st);
+// separable solve of one level with per-plane transforms in thread-block
+// clusters (kernels_sepplane.cu); false (nothing launched) when the level does
+// not qualify.  mode_solve: the 3D mode-solve stage on t.
+template <typename T>
+bool plane_level_solve(const Geom& g, int dim, const SepTables& tab, const T* f, T* t, T* out, bool accumulate,
+                       const SepStage<T>* mode_solve, cudaStream_t st);
+template <typename T>
+int plane_cluster_size(const Geom& g, int dim);
 
 // ---- zebra z-line Gauss-Seidel sweep, both colours (kernels_line.cu); scratch holds g.n elements ----
 template <typename T>

@@ -5,11 +5,15 @@
 // device allocation: its scratch (per-block partial sums and the per-plane
 // coefficient table) lives in one file-scope __device__ array of fixed size,
 // which every GPU that loads this library keeps until the process exits.
+// b is the right-hand side after lifting every Dirichlet face of P (the
+// values on the six faces enter the rows of their interior neighbours); the
+// interior source is zero, as in the paper's problem (Sect. 2.2).
 //
 // Host code may not use the array's name as a device address (it is a host
 // stand-in), so the address is looked up once per device with
 // cudaGetSymbolAddress and cached.  That look-up happens inside the first
-// call on each device.
+// call on each device.  A cudaDeviceReset destroys the context the address
+// belongs to; the cached address is then stale.
 //
 // All calls share the one array and it keeps the last call's contents:
 // every slot a call reads is written earlier by that same call (partials by
@@ -57,8 +61,9 @@ __global__ void na_coef_kernel(int nz, double hx, double hy, double hz, double a
     tab[5 * k + 4] = 0.0;
 }
 
-// r = 0 - A P on interior nodes of a dense [nz][ny][nx] array; the lifted
-// right-hand side b is cz P(i,j,0) on the plane k = 1
+// r = 0 - A P on interior nodes of a dense [nz][ny][nx] array (every face of
+// P is Dirichlet data); the lifted right-hand side b of a node is minus the
+// coefficient-weighted sum of its neighbours that lie on a face
 __global__ void na_residual_kernel(int nx, int ny, int nz, const double* __restrict__ P,
                                    const double* __restrict__ tab, double* __restrict__ part_r,
                                    double* __restrict__ part_b) {
@@ -76,10 +81,14 @@ __global__ void na_residual_kernel(int nx, int ny, int nz, const double* __restr
         au += cz * (P[o + plane] + P[o - plane]);
         const double rv = 0.0 - au;
         ar += rv * rv;
-        if (k == 1) {
-            const double bv = cz * P[o - plane];
-            ab += bv * bv;
-        }
+        double lift = 0.0;
+        if (i == 1) lift += cx * P[o - 1];
+        if (i == nx - 2) lift += cx * P[o + 1];
+        if (j == 1) lift += cy * P[o - nx];
+        if (j == ny - 2) lift += cy * P[o + nx];
+        if (k == 1) lift += cz * P[o - plane];
+        if (k == nz - 2) lift += cz * P[o + plane];
+        ab += lift * lift;
     }
     const double sr = block_sum(ar);
     const double sb = block_sum(ab);
@@ -142,7 +151,14 @@ mhs_status interior_residual_noalloc(int nx, int ny, int nz, double Lx, double L
     if (nz > NA_MAX_NZ)
         throw Error(MHS_ERR_INVALID_ARG, "nz = " + std::to_string(nz) + " exceeds the allocation-free limit of " +
                                              std::to_string(NA_MAX_NZ) + " planes");
-    if (!(Lx > 0) || !(Ly > 0) || !(Lz > 0)) throw Error(MHS_ERR_INVALID_ARG, "domain lengths must be > 0");
+    if (!(Lx > 0) || !(Ly > 0) || !(Lz > 0) || !std::isfinite(Lx) || !std::isfinite(Ly) || !std::isfinite(Lz))
+        throw Error(MHS_ERR_INVALID_ARG, "domain lengths must be finite and > 0");
+    if (!std::isfinite(alpha)) throw Error(MHS_ERR_INVALID_ARG, "alpha must be finite");
+    if (xi) {
+        if (xi->kind < MHS_XI_NONE || xi->kind > MHS_XI_EXP_SIN) throw Error(MHS_ERR_INVALID_ARG, "unknown xi kind");
+        if (!std::isfinite(xi->a) || !std::isfinite(xi->kappa) || !std::isfinite(xi->b) || !std::isfinite(xi->omega))
+            throw Error(MHS_ERR_INVALID_ARG, "xi parameters must be finite");
+    }
     if (!P || !out || !is_device(P) || !is_device(out))
         throw Error(MHS_ERR_INVALID_ARG, "P and out must be device pointers");
     const mhs_xi_params x = xi ? *xi : mhs_xi_params{MHS_XI_NONE, 0, 0, 0, 0};

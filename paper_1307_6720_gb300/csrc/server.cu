@@ -90,30 +90,9 @@ struct Server {
 
 namespace {
 
-size_t handle_bytes(mhs_ctx* c) {
-    size_t b = 0;
-    for (Hierarchy* H : {&c->h3, &c->h2})
-        for (const Geom& g : H->g) b += g.n * (3 * sizeof(double) + 3 * sizeof(float));
-    b += 6 * c->h3.g[0].n * sizeof(double);   // field buffers (allocated on first use)
-    return b;
-}
+size_t handle_bytes(mhs_ctx* c) { return handle_bytes_held(c); }
 
-size_t estimate_bytes(const mhs_request& r) {
-    size_t b = 0;
-    int nx = r.nx, ny = r.ny, nz = r.nz;
-    auto can = [](int n) { return n >= 5 && (n - 1) % 2 == 0; };
-    for (;;) {
-        const size_t px = (size_t(nx) + 3) / 4 * 4;
-        b += px * ny * nz * (3 * sizeof(double) + 3 * sizeof(float)) + px * ny * (3 * sizeof(double) + 3 * sizeof(float));
-        if (!(can(nx) && can(ny) && can(nz))) break;
-        nx = (nx - 1) / 2 + 1;
-        ny = (ny - 1) / 2 + 1;
-        nz = (nz - 1) / 2 + 1;
-    }
-    const size_t px = (size_t(r.nx) + 3) / 4 * 4;
-    b += 6 * px * r.ny * r.nz * sizeof(double);
-    return b;
-}
+size_t estimate_bytes(const mhs_request& r) { return handle_bytes_estimate(r.nx, r.ny, r.nz, r.Lx, r.Ly, r.Lz); }
 
 }  // namespace
 

@@ -48,6 +48,7 @@ static void* dev_alloc(mhs_ctx* c, size_t bytes) {
         throw Error(MHS_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     c->allocations.push_back(p);
+    c->dev_bytes += round_up(bytes ? bytes : 16, 256);
     MHS_CUDA(cudaMemsetAsync(p, 0, bytes ? bytes : 16, c->stream));
     return p;
 }
@@ -288,7 +289,7 @@ static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fi
         } else if (fused) {
             launch_sweep<T>(g, A.coef, even ? A.u : A.t, f, even ? A.t : A.u, c->stream);
         } else {
-            launch_smooth<T>(g, H.dim, A.coef, A.u, f, c->stream);
+            launch_smooth<T>(g, H.dim, A.coef, A.u, f, c->stream, c->opts.tile);
         }
     }
     if (fused && (n & 1)) MHS_CUDA(cudaMemcpyAsync(A.u, A.t, g.n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
@@ -319,16 +320,17 @@ struct LevelOps {
     }
 };
 
-// the coarse-grid correction of level l from its residual in A.r: restriction,
-// the coarser cycle, interpolation added to u
+// the coarse-grid correction of level l from its residual: restriction of
+// the residual in A.r (unless the fused pass of FP32 levels has already
+// restricted it), the coarser cycle, interpolation added to u
 template <typename T>
-static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>& o) {
+static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>& o, bool restricted) {
     cudaStream_t st = c->stream;
     const bool dbl = sizeof(T) == 8;
     LevelArrays<T>& A = arrays<T>(H, l);
     LevelArrays<T>& C = arrays<T>(H, l + 1);
     const double N = o.N, s = o.s, Nc = double(H.g[l + 1].interior());
-    {
+    if (!restricted) {
         TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
                      Nc * (H.dim == 3 ? 54.0 : 18.0), st, o.fine);
         launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, A.r, C.f, C.u, st);
@@ -371,11 +373,22 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
     const LevelOps<T> o(c, H, l);
     const double sweep_bytes = o.N * (2 * o.s + o.fs);
     smooth_n<T>(c, H, l, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
-    {
-        TimedScope t(c->timer, dbl ? MHS_KT_RESID64 : MHS_KT_RESID32, sweep_bytes, o.N * o.res_flops, st, o.fine);
-        launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st, dbl && red_residual_level(c, H));
+    if (!dbl) {
+        // FP32 levels (bandwidth-bound): residual and restriction in one pass, the residual not
+        // stored (u and f read, the coarse right-hand side and iterate written; flops of the
+        // residual and of the 27-point (9-point) weighting per coarse node)
+        LevelArrays<T>& C = arrays<T>(H, l + 1);
+        const double Nc = double(H.g[l + 1].interior());
+        TimedScope t(c->timer, MHS_KT_RESID32, o.N * (o.s + o.fs) + 2 * Nc * o.s,
+                     o.N * o.res_flops + Nc * (H.dim == 3 ? 54.0 : 18.0), st, o.fine);
+        launch_resid_restrict<T>(g, H.g[l + 1], H.dim, A.coef, A.u, o.f, C.f, C.u, st);
+    } else {
+        // FP64 levels (bound by the FP64 pipe, which the fused pass would not relieve): the
+        // residual on red nodes after the sweep, then the restriction
+        TimedScope t(c->timer, MHS_KT_RESID64, sweep_bytes, o.N * o.res_flops, st, o.fine);
+        launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st, red_residual_level(c, H));
     }
-    coarse_correction<T>(c, H, l, o);
+    coarse_correction<T>(c, H, l, o, !dbl);
     smooth_n<T>(c, H, l, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
 }
 
@@ -407,7 +420,7 @@ bool red_residual_fmg(const mhs_ctx* c, const Hierarchy& H) {
 static void vcycle_rotated(mhs_ctx* c, Hierarchy& H) {
     const LevelOps<double> o(c, H, 0);
     const double sweep_bytes = o.N * (2 * o.s + o.fs);
-    coarse_correction<double>(c, H, 0, o);
+    coarse_correction<double>(c, H, 0, o, false);
     smooth_n<double>(c, H, 0, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
     smooth_n<double>(c, H, 0, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
 }
@@ -684,7 +697,8 @@ static void add_while(mhs_ctx* c, cudaGraphConditionalHandle hnd, F&& fn) {
 static GraphKey graph_key(mhs_ctx* c) {
     const int flags = c->opts.flags & ~(MHS_FLAG_NO_GRAPH | MHS_FLAG_ZLINE | MHS_FLAG_POINT | MHS_FLAG_BZ_MIMETIC);
     return GraphKey{{c->opts.nu1, c->opts.nu2, c->opts.inner_cycles, flags, c->opts.cut64, c->opts.cut32,
-                     c->opts.fused_min, c->opts.sep_coarse, c->f_zero_finest ? 1 : 0, use_zline(c) ? 1 : 0}};
+                     c->opts.fused_min, c->opts.sep_coarse, c->f_zero_finest ? 1 : 0, use_zline(c) ? 1 : 0,
+                     c->opts.tile}};
 }
 
 constexpr size_t GRAPH_CACHE = 8;   // captured solves kept per precision mode
@@ -817,6 +831,8 @@ mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
         info->rel_res_3d = b.rel;
         info->conv_factor = (b.cycles > 0 && b.rel0 > 0 && b.rel > 0) ? std::pow(b.rel / b.rel0, 1.0 / b.cycles) : 0.0;
         info->ms = ms;
+        info->outer_iters_2d = lower_mode(c, mode) == MHS_MIXED ? a.cycles : 0;
+        info->outer_iters_3d = mode == MHS_MIXED ? b.cycles : 0;
     }
     c->have_solution = true;
     if (c->flag_host[1]) throw Error(MHS_ERR_TIMEOUT, "a kernel's bounded wait for its TMA loads expired");
@@ -895,6 +911,52 @@ void ensure_post_buffers(mhs_ctx* c) {
 void ensure_staging(mhs_ctx* c) {
     if (c->staging) return;
     MHS_CUDA(cudaMalloc(&c->staging, c->h3.g[0].n * sizeof(double)));
+    c->dev_bytes += round_up(c->h3.g[0].n * sizeof(double), 256);
+}
+
+// Device bytes of a handle for an nx*ny*nz grid, from the same level
+// geometry as build_hierarchy: per level of the interior and lower-boundary
+// hierarchies u, f, r, t in FP64 and FP32 and the plane coefficients; the
+// double-float state of each finest level; the norm scratch; the five field
+// buffers; and separable-solver tables (mode pivots in both precisions) for
+// every coarse level, an upper bound of what any coarse-grid choice builds.
+size_t handle_bytes_estimate(int nx, int ny, int nz, double Lx, double Ly, double Lz) {
+    const size_t q = 256;
+    size_t b = 0;
+    for (int dim : {3, 2}) {
+        int x = nx, y = ny, z = dim == 3 ? nz : 1;
+        for (int l = 0;; ++l) {
+            const Geom g = make_geom(x, y, z, Lx, Ly, Lz);
+            b += 4 * round_up(g.n * sizeof(double), q) + 4 * round_up(g.n * sizeof(float), q);
+            b += round_up(g.nz * sizeof(PlaneCoef<double>), q) + round_up(g.nz * sizeof(PlaneCoef<float>), q);
+            if (l == 0) {
+                b += 4 * round_up(g.n * sizeof(float), q) + round_up(g.nz * sizeof(PlaneCoefDF), q);
+                if (dim == 2) b += round_up(g.n * sizeof(double), q);   // B_z
+            } else {
+                if (dim == 3) b += 2 * round_up(g.interior() * (sizeof(double) + sizeof(float)), q);
+                // mode eigenvalues and twiddles, or sine matrices of short rows, in both precisions
+                b += 4 * round_up(size_t(x + y) * 2 * sizeof(double), q);
+                if (x <= 66 && y <= 66) b += 2 * round_up(size_t(x * x + y * y) * sizeof(double), q);
+            }
+            const bool can = coarsenable(x) && coarsenable(y) && (dim == 2 || coarsenable(z));
+            if (!can || l + 1 == MAX_SUB_LEVELS) break;
+            x = (x - 1) / 2 + 1;
+            y = (y - 1) / 2 + 1;
+            if (dim == 3) z = (z - 1) / 2 + 1;
+        }
+    }
+    const Geom g0 = make_geom(nx, ny, nz, Lx, Ly, Lz);
+    b += 5 * round_up(g0.n * sizeof(double), q);                 // B_x, B_y, B_z, p, rho
+    b += 65536 * sizeof(double) + 4096 + 8 * size_t(nz) * sizeof(double);   // norm scratch, flags, profiles
+    return b;
+}
+
+// Bytes a resident handle holds now, plus the field buffers its first field
+// recovery allocates.
+size_t handle_bytes_held(const mhs_ctx* c) {
+    size_t b = c->dev_bytes;
+    if (!c->fld[0]) b += 5 * round_up(c->h3.g[0].n * sizeof(double), 256);
+    return b;
 }
 
 }  // namespace mhs

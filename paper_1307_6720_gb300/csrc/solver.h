@@ -74,6 +74,11 @@ void sep_solve(mhs_ctx* c, Hierarchy& H);           // mixed mode: FP32 e = A^{-
 bool sep_fp64_available(const mhs_ctx* c);          // FP64 direct solves: sep_level_ok of the finest grid
 void sep_correct64(mhs_ctx* c, Hierarchy& H);       // FP64 mode: P += A^{-1} r on the finest level
 void ensure_staging(mhs_ctx* c);
+// device bytes of a handle for a grid (upper bound used for admission) and
+// the bytes a handle holds (every allocation it made, plus field buffers not
+// yet allocated)
+size_t handle_bytes_estimate(int nx, int ny, int nz, double Lx, double Ly, double Lz);
+size_t handle_bytes_held(const mhs_ctx* c);
 
 // FP64 cycles of the finest level with the test after the pre-smoothing (level 0 above the sub-cycle cut-off)
 bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H);

@@ -13,6 +13,7 @@
 //     candidate per level that the sub-cycle could start from,
 //   - the fused TMA sweep threshold on FP32 levels (mixed mode, point smoother),
 //   - the full-multigrid first cycle (MHS_FLAG_NO_FMG),
+//   - the thread-block shape of the red-black point passes (tile),
 // at most two rounds, a change kept only when it saves at least 3 %.  The
 // winner is stored in a process-wide table keyed by the problem class
 // (grid, mode, anisotropy class), so that other handles of the class, such
@@ -27,6 +28,7 @@
 #include <tuple>
 #include <vector>
 
+#include "mg_bodies.cuh"
 #include "mhs_internal.h"
 #include "solver.h"
 
@@ -151,6 +153,13 @@ void autotune(mhs_ctx* c, double tol, int mode, int repeats, mhs_tune_result* ou
             mhs_solver_opts o = best;
             o.flags ^= MHS_FLAG_NO_FMG;
             consider(o);
+        }
+        if (!line) {   // thread-block shape of the point passes
+            for (int t = 1; t <= N_TILES; ++t) {
+                mhs_solver_opts o = best;
+                o.tile = t;
+                consider(o);
+            }
         }
         if (same_opts(before, best)) break;
     }

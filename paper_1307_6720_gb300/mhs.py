@@ -25,8 +25,10 @@ MHS_FP64, MHS_MIXED = 0, 1
 MHS_FLAG_WARM, MHS_FLAG_BZ_MIMETIC, MHS_FLAG_NO_GRAPH, MHS_FLAG_FUSED_SWEEP64, MHS_FLAG_NO_TMA, MHS_FLAG_NO_FMG = \
     1, 2, 4, 8, 16, 32
 MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE, MHS_FLAG_LOWER_FP64 = 64, 128, 256, 512
+MHS_FLAG_STAGED_TRANSFORMS = 1024
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
-MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE, MHS_OP_EXACT = range(7)
+(MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE, MHS_OP_EXACT,
+ MHS_OP_RESID_RESTRICT) = range(8)
 
 
 class XiParams(ctypes.Structure):
@@ -42,12 +44,14 @@ class AtmosParams(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int), ("cut64", ctypes.c_int),
-                ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int), ("sep_coarse", ctypes.c_int)]
+                ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int), ("sep_coarse", ctypes.c_int),
+                ("tile", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("cycles_2d", ctypes.c_int), ("cycles_3d", ctypes.c_int), ("rel_res_2d", ctypes.c_double),
-                ("rel_res_3d", ctypes.c_double), ("conv_factor", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("rel_res_3d", ctypes.c_double), ("conv_factor", ctypes.c_double), ("ms", ctypes.c_double),
+                ("outer_iters_2d", ctypes.c_int), ("outer_iters_3d", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +132,7 @@ _SIGS = {
     "mhs_kernel_timing_reset": [_H],
     "mhs_kernel_kind_name": [_I],
     "mhs_kernel_launches": [],
+    "mhs_probe_fma_rate": [_I, _P, ctypes.POINTER(_D)],
     "mhs_interior_residual_noalloc": [_I, _I, _I, _D, _D, _D, _D, ctypes.POINTER(XiParams), _P, _P, _P],
     "mhs_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_H)],
     "mhs_server_submit": [_H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)],
@@ -230,8 +235,8 @@ def mhs_set_stream(h, stream) -> None:
 
 
 def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0, fused_min=0,
-                    sep_coarse=0) -> None:
-    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min, sep_coarse)
+                    sep_coarse=0, tile=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min, sep_coarse, tile)
     _check(LIB.mhs_set_options(h, ctypes.byref(o)))
 
 
@@ -403,6 +408,15 @@ def mhs_kernel_kind_name(kind: int) -> str:
 
 def mhs_kernel_launches() -> int:
     return int(LIB.mhs_kernel_launches())
+
+
+def mhs_probe_fma_rate(precision, stream=None) -> float:
+    """Sustained FMA rate of the device in flop/s (FP64 for MHS_FP64, FP32 for MHS_MIXED)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    r = _D()
+    _check(LIB.mhs_probe_fma_rate(precision, stream, ctypes.byref(r)))
+    return r.value
 
 
 def mhs_interior_residual_noalloc(nx, ny, nz, Lx, Ly, Lz, alpha, xi: XiParams | None, P, out, stream=None) -> None:

@@ -73,3 +73,27 @@ def test_autotune_requires_bz(M):
         M.mhs_autotune(h, 1e-10, M.MHS_FP64)
     assert e.value.status == M.MHS_ERR_BAD_STATE
     M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tile_shapes_give_identical_solves(M, mode):
+    """The thread-block shape of the red-black point passes (option tile,
+    one of the autotuner's coordinates) changes how nodes are distributed
+    over threads, not which values a pass computes: every shape gives the
+    same P bit for bit, FP64 and mixed, including the FP32 quad passes of
+    large levels (257 x 129 x 129 interior planes of 4.2 M nodes)."""
+    import torch
+    pr = S.problem(257, 129, 129, Lx=1.0, Ly=0.5, Lz=0.5, alpha=0.5, xi_kind=1, xi_a=0.5, xi_kappa=1.0)
+    bz = S.magnetogram_random(257, 129, 1.0, 0.5, seed=43)
+    h = _handle(M, pr, bz)
+    P = torch.empty((129, 129, 257), dtype=torch.float64, device="cuda")
+    ref = None
+    for tile in range(1, 6):
+        M.mhs_set_options(h, tile=tile)
+        M.mhs_solve(h, 1e-10, mode)
+        M.mhs_get_phi(h, P)
+        got = P.cpu().numpy()
+        if ref is None:
+            ref = got
+        assert np.array_equal(got, ref), tile
+    M.mhs_destroy(h)

@@ -245,6 +245,88 @@ def test_exact_op_parity(M, shape, dim, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dim", [3, 2])
+@pytest.mark.parametrize("shape", [(65, 33, 17), (49, 25, 37), (17, 9, 13), (5, 5, 5), (193, 97, 41)])
+def test_fused_residual_restriction_equals_separate_launches(M, shape, dim, prec):
+    """The residual + full-weighting restriction pass the V-cycles run
+    (MHS_OP_RESID_RESTRICT: tiles of 16 x 8 coarse nodes, chunks of coarse
+    planes, the fine residual kept in shared memory) equals the residual
+    launch followed by the restriction launch bit for bit, on every level
+    with a coarser one: ragged tiles, odd and even coarse counts, the zeroed
+    coarse iterate; and the restriction of the oracle's residual within the
+    kernel tolerance."""
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=(ny - 1) / (nx - 1), Lz=(nz - 1) / (nx - 1))
+    rng = np.random.default_rng(nx + 3 * ny + 7 * nz + dim)
+    for level in range(M.mhs_num_levels(h, dim) - 1):
+        lx, ly, lz = M.mhs_level_shape(h, dim, level)
+        cx, cy, cz = M.mhs_level_shape(h, dim, level + 1)
+        shp = (lz, ly, lx) if dim == 3 else (ly, lx)
+        cshp = (cz, cy, cx) if dim == 3 else (cy, cx)
+        u, f = rng.standard_normal(shp), rng.standard_normal(shp)
+        M.mhs_level_write(h, dim, level, M.MHS_FIELD_U, prec, u)
+        M.mhs_level_write(h, dim, level, M.MHS_FIELD_F, prec, f)
+        M.mhs_level_op(h, dim, level, M.MHS_OP_RESIDUAL, prec)
+        M.mhs_level_op(h, dim, level, M.MHS_OP_RESTRICT, prec)
+        want = _read(M, h, dim, level + 1, M.MHS_FIELD_F, prec)
+        M.mhs_level_write(h, dim, level + 1, M.MHS_FIELD_F, prec, np.full(cshp, 7.0))
+        M.mhs_level_write(h, dim, level + 1, M.MHS_FIELD_U, prec, np.full(cshp, 5.0))
+        M.mhs_level_op(h, dim, level, M.MHS_OP_RESID_RESTRICT, prec)
+        got = _read(M, h, dim, level + 1, M.MHS_FIELD_F, prec)
+        uc = _read(M, h, dim, level + 1, M.MHS_FIELD_U, prec)
+        inner = (slice(1, -1),) * (3 if dim == 3 else 2)
+        assert np.array_equal(got[inner], want[inner]), (level, np.abs(got - want)[inner].max())
+        assert np.all(uc[inner] == 0.0)
+        prl = _level_problem(M, h, pr, dim, level)
+        uu = _read(M, h, dim, level, M.MHS_FIELD_U, prec)
+        ff = _read(M, h, dim, level, M.MHS_FIELD_F, prec)
+        r = oracle.residual3d(prl, uu, ff) if dim == 3 else oracle.residual2d(prl, uu, ff)
+        assert _rel(got[inner], oracle.restrict(r)[inner]) < _tol(prec) * 10, level
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(65, 65, 65), (129, 65, 33), (33, 17, 9), (257, 257, 17), (17, 33, 5)])
+def test_plane_transforms_equal_staged_transforms_bitwise(M, shape, prec):
+    """The per-plane separable solve (row and column transforms of a plane in
+    one thread-block cluster, columns read from the other CTAs' shared
+    memory) performs the staged solve's operations on every line: on every
+    level with fast transforms, 2D and 3D, FP64 and FP32, its result equals
+    the staged passes' (MHS_FLAG_STAGED_TRANSFORMS) bit for bit.  The launch
+    counts show which path ran: one kernel for a lower-boundary level, three
+    for an interior level (forward transforms, mode solves, inverse
+    transforms), against five staged launches."""
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz, Lx=1.0, Ly=(ny - 1) / (nx - 1), Lz=(nz - 1) / (nx - 1))
+    rng = np.random.default_rng(nx * ny + nz)
+    checked = 0
+    for dim in (3, 2):
+        for level in range(M.mhs_num_levels(h, dim)):
+            lx, ly, lz = M.mhs_level_shape(h, dim, level)
+            if not ((lx - 1) & (lx - 2) == 0 and (ly - 1) & (ly - 2) == 0):
+                continue
+            shape_l = (lz, ly, lx) if dim == 3 else (ly, lx)
+            f = rng.standard_normal(shape_l) * 10
+            outs, counts = [], []
+            for flags in (0, M.MHS_FLAG_STAGED_TRANSFORMS):
+                M.mhs_set_options(h, flags=flags)
+                M.mhs_level_write(h, dim, level, M.MHS_FIELD_U, prec, np.zeros(shape_l))
+                M.mhs_level_write(h, dim, level, M.MHS_FIELD_F, prec, f)
+                M.mhs_level_op(h, dim, level, M.MHS_OP_EXACT, prec)   # tables built on first use
+                M.mhs_level_write(h, dim, level, M.MHS_FIELD_U, prec, np.zeros(shape_l))
+                n0 = M.mhs_kernel_launches()
+                M.mhs_level_op(h, dim, level, M.MHS_OP_EXACT, prec)
+                counts.append(M.mhs_kernel_launches() - n0)
+                outs.append(_read(M, h, dim, level, M.MHS_FIELD_U, prec))
+            assert counts == [1 if dim == 2 else 3, 5], (dim, level, counts)
+            assert np.abs(outs[0]).max() > 0
+            assert np.array_equal(outs[0], outs[1]), (dim, level, (lx, ly, lz), np.abs(outs[0] - outs[1]).max())
+            checked += 1
+    assert checked >= 2
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
 @pytest.mark.parametrize("exact_level", [1, 2])
 def test_vcycle_exact_coarse_parity(M, exact_level, dim, prec):
     """One V(2,2)-cycle whose coarse-grid system on level 1 or 2 is solved

@@ -83,3 +83,66 @@ def test_server_rejects_nonfinite_input(M):
         M.mhs_server_submit(srv, 17, 17, 17, 1.0, 1.0, 1.0, 0.5, None, bz)
     assert e.value.status == M.MHS_ERR_NONFINITE
     M.mhs_server_destroy(srv)
+
+
+def test_server_budget_counts_every_device_allocation(M):
+    """The bytes the server books for a resident hierarchy cover what the
+    hierarchy really holds: the fall of free device memory over one 129^3
+    request (handle creation, graph capture, solve, field recovery) stays
+    within the server's device_bytes plus a small allowance for the CUDA
+    graph and stream objects, and the booking is not wildly above it."""
+    import torch
+    n = 129
+    bz = S.magnetogram_random(n, n, seed=41)
+    outs = [torch.empty((n, n, n), dtype=torch.float64, device="cuda") for _ in range(6)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    srv = M.mhs_server_create(64 << 30, 1)
+    try:
+        t = M.mhs_server_submit(srv, n, n, n, 1.0, 1.0, 1.0, 0.5, M.xi_params(M.MHS_XI_EXP, 0.5, 1.0), bz, 1e-10,
+                                M.MHS_MIXED, phi=outs[0], Bx=outs[1], By=outs[2], Bz=outs[3], p=outs[4], rho=outs[5])
+        _, st, _ = M.mhs_server_wait(srv, t, 120.0)
+        assert st == 0
+        torch.cuda.synchronize()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        booked = M.mhs_server_stats(srv)["device_bytes"]
+    finally:
+        M.mhs_server_destroy(srv)
+    assert used <= booked + (48 << 20), (used, booked)
+    assert booked <= 1.5 * used + (48 << 20), (used, booked)
+
+
+def test_server_mix_of_large_requests_matches_exact_solution(M):
+    """Requests of 129^3 and 257^3 nodes (the large part of the served mix)
+    in flight together.  Each Phi against the oracle's exact discrete
+    solution at the mixed bar 1e-8; each B, p and rho against the oracle's
+    field recovery (Sect. 2.2, eqs. pressure, density) of the Phi the server
+    returned, at the FP64 bar 1e-10 (at the served tolerance 1e-10 the fields'
+    own distance from the exact solution is set by the tolerance: B and rho,
+    first to third differences of P, amplify the solve error by up to h^-3)."""
+    import torch
+    import oracle
+    from oracle import exact
+    reqs = [(129, 0.5, 0.5, 1.0, 61), (257, 0.3, 0.8, 0.7, 62), (129, 0.7, 0.2, 1.5, 63)]
+    srv = M.mhs_server_create(32 << 30, 3)
+    tickets, outs = [], []
+    try:
+        for n, alpha, a, kappa, seed in reqs:
+            bz = S.magnetogram_random(n, n, seed=seed)
+            o = [torch.empty((n, n, n), dtype=torch.float64, device="cuda") for _ in range(6)]
+            outs.append((bz, o))
+            tickets.append(M.mhs_server_submit(srv, n, n, n, 1.0, 1.0, 1.0, alpha, M.xi_params(M.MHS_XI_EXP, a, kappa),
+                                               bz, 1e-10, M.MHS_MIXED, phi=o[0], Bx=o[1], By=o[2], Bz=o[3], p=o[4],
+                                               rho=o[5]))
+        results = [M.mhs_server_wait(srv, t, 300.0) for t in tickets]
+    finally:
+        M.mhs_server_destroy(srv)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for (n, alpha, a, kappa, _), (bz, o), (info, st, _) in zip(reqs, outs, results):
+        assert st == 0 and info["rel_res_3d"] < 1e-10 and info["rel_res_2d"] < 1e-10
+        pr = S.problem(n, n, n, alpha=alpha, xi_kind=1, xi_a=a, xi_kappa=kappa)
+        got = dict(zip(["phi", "Bx", "By", "Bz", "p", "rho"], (t.cpu().numpy() for t in o)))
+        assert rel(got["phi"], exact.exact_solution(pr, bz)) < 1e-8, n
+        F = oracle.fields(pr, got["phi"])
+        err = {k: rel(got[k], F[k]) for k in F}
+        assert all(e < 1e-10 for e in err.values()), (n, err)

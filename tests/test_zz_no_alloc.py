@@ -8,7 +8,9 @@ calls it through the C ABI twice in a row, on two different problems, and
 checks each result against the existing entry points: the relative residual
 that mhs_solve reports and the residual the MHS_OP_RESIDUAL level hook
 writes.  Solves stop early (a few cycles) so the residual is far above
-rounding and the comparison can use the suite's FP64 bar of 1e-10.
+rounding and the comparison can use the suite's FP64 bar of 1e-10.  A third
+case gives P non-zero values on all six faces and checks the residual and
+the lifted right-hand side against the oracle.
 
 The file is named so that pytest collects it last.
 """
@@ -73,6 +75,30 @@ def test_noalloc_residual_matches_solver_twice_in_a_row(M):
     assert not np.allclose(outs[0], outs[1])
 
 
+def test_noalloc_lifts_every_face_like_the_oracle(M):
+    """P with Dirichlet data on all six faces: out[0] is the oracle's interior
+    residual norm, out[1] the norm of the oracle's residual of P with its
+    interior zeroed (the lifted right-hand side), out[2] their ratio."""
+    import torch
+    import oracle
+    pr = S.problem(33, 17, 25, Lx=1.0, Ly=0.5, Lz=0.75, alpha=0.4, xi_kind=2, xi_a=0.6, xi_b=0.3,
+                   xi_omega=np.pi, xi_kappa=0.2)
+    P = np.random.default_rng(77).standard_normal((25, 17, 33))
+    r = oracle.residual3d(pr, P)
+    lift = P.copy()
+    lift[1:-1, 1:-1, 1:-1] = 0.0
+    b = oracle.residual3d(pr, lift)
+    want = np.array([np.linalg.norm(r), np.linalg.norm(b), np.linalg.norm(r) / np.linalg.norm(b)])
+    xi = M.xi_params(2, 0.6, 0.2, 0.3, np.pi)
+    Pd = torch.from_numpy(P).cuda()
+    for _ in range(2):
+        out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+        M.mhs_interior_residual_noalloc(33, 17, 25, 1.0, 0.5, 0.75, 0.4, xi, Pd, out, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.all(np.abs(o - want) <= BAR * want), (o, want)
+
+
 def test_noalloc_rejects_out_of_range_inputs(M):
     import torch
     P = torch.zeros((5, 5, 5), dtype=torch.float64, device="cuda")
@@ -83,3 +109,8 @@ def test_noalloc_rejects_out_of_range_inputs(M):
     with pytest.raises(M.MhsError) as e:
         M.mhs_interior_residual_noalloc(5, 5, 5, 1.0, 1.0, 1.0, 0.0, None, np.zeros((5, 5, 5)), out)
     assert e.value.status == M.MHS_ERR_INVALID_ARG
+    for xi, alpha in ((M.xi_params(7, 0.5, 1.0), 0.0), (M.xi_params(1, float("nan"), 1.0), 0.0),
+                      (None, float("inf"))):
+        with pytest.raises(M.MhsError) as e:
+            M.mhs_interior_residual_noalloc(5, 5, 5, 1.0, 1.0, 1.0, alpha, xi, P, out)
+        assert e.value.status == M.MHS_ERR_INVALID_ARG
