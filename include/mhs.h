@@ -246,10 +246,12 @@ MHS_API mhs_status mhs_batch_solve(mhs_handle* hs, int n, double tol, int mode, 
  * mode), are packed into parts of at most part_bytes of working set (0:
  * half the L2 cache), so that a part holds instances of similar size; each
  * part is one graph, and the parts are launched round-robin on nstreams
- * streams (0: 16), so that several parts run at once.  A part that holds a
- * single instance (an instance whose working set alone fills the part
- * budget) runs that instance's own solve, as mhs_solve would, on its launch
- * stream.  part_bytes = SIZE_MAX makes one part of all instances.
+ * streams (0: 16), so that several parts run at once.  An instance whose
+ * working set exceeds a sixteenth of part_bytes takes a part of its own, and a
+ * part that holds a single instance runs that instance's own solve, as
+ * mhs_solve would, on a stream of its own, as in mhs_batch_solve: grouping
+ * pays where launch latency dominates.  part_bytes = SIZE_MAX makes one part
+ * of all instances.
  *
  * mhs_group_create snapshots the handles' options, cut-offs and smoother
  * choice (recreate the group after changing a member's options, or its
