@@ -584,10 +584,13 @@ def batched_instances(count=256):
 
 def batched_leg(M, reps=3, count=256, tune=True):
     """The 256 uneven instances solved together in mixed precision: as one grouped solve (one launch per
-    multigrid operation and level for all instances, one CUDA graph) and as mhs_batch_solve (every
+    multigrid operation and level for the instances of a part, one CUDA graph per part; instances with a
+    large working set run their own graphs on their own streams) and as mhs_batch_solve (every
     instance's own graph on its own stream), against solving them one after another in FP64 and in mixed
-    mode.  Then the autotuner picks options per problem class (untimed set-up) and the grouped solve is
-    timed again with them."""
+    mode.  The grouped and per-stream forms are timed alternately, `reps` rounds of two batches each,
+    and the median is reported (so that neither form gains from running second).  Then the autotuner
+    picks options per problem class (untimed set-up) and the grouped solve is timed again with them.
+    A batch of 1024 small instances (33^3, the linear-MHS workload's physics) shows where grouping pays."""
     import torch
     inst = batched_instances(count)
     hs = []
@@ -602,36 +605,55 @@ def batched_leg(M, reps=3, count=256, tune=True):
         for h in hs:
             M.mhs_solve(h, TOL, mode)
 
-    def bat():
-        infos, sts = M.mhs_batch_solve(hs, TOL, M.MHS_MIXED)
+    def bat(handles=hs):
+        infos, sts = M.mhs_batch_solve(handles, TOL, M.MHS_MIXED)
         assert all(s == 0 for s in sts), sts
         return infos
 
-    groups = {}
-
-    def grp(key):
-        infos, sts = M.mhs_group_solve(groups[key], count, TOL)
+    def grp(g, n=count):
+        infos, sts = M.mhs_group_solve(g, n, TOL)
         assert all(s == 0 for s in sts), sts
         return infos
 
     res = {}
+
+    def timed_rounds(fns, n=count, rounds=reps):
+        """{name: fn}: alternate rounds of two batches each; median solves/s per form"""
+        for fn in fns.values():
+            fn()
+        torch.cuda.synchronize()
+        rates, last = {k: [] for k in fns}, {}
+        for _ in range(rounds):
+            for k, fn in fns.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                last[k] = fn()
+                torch.cuda.synchronize()
+                rates[k].append(2 * n / (time.perf_counter() - t0))
+        out = {}
+        for k, v in rates.items():
+            r = sorted(v)[len(v) // 2]
+            out[k] = {"solves_per_s": r, "unknowns_per_s": r * unknowns / count if n == count else None,
+                      "s_per_batch": n / r}
+            if last.get(k) is not None:
+                out[k]["max_cycles_3d"] = max(i["cycles_3d"] for i in last[k])
+                out[k]["max_rel_res_3d"] = max(i["rel_res_3d"] for i in last[k])
+        return out
 
     def run(name, fn):
         fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
-            out = fn()
+            fn()
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         res[name] = {"solves_per_s": count / dt, "unknowns_per_s": unknowns / dt, "s_per_batch": dt}
-        if out is not None:
-            res[name]["max_cycles_3d"] = max(i["cycles_3d"] for i in out)
-            res[name]["max_rel_res_3d"] = max(i["rel_res_3d"] for i in out)
 
-    groups["default"] = M.mhs_group_create(hs, M.MHS_MIXED)
-    run("grouped_mixed", lambda: grp("default"))
-    run("batched_mixed", bat)
+    g = M.mhs_group_create(hs, M.MHS_MIXED)
+    res.update(timed_rounds({"grouped_mixed": lambda: grp(g), "batched_mixed": bat}))
+    M.mhs_group_destroy(g)
     run("sequential_fp64", lambda: seq(M.MHS_FP64))
     run("sequential_mixed", lambda: seq(M.MHS_MIXED))
     if tune:
@@ -643,14 +665,27 @@ def batched_leg(M, reps=3, count=256, tune=True):
                 tuned_classes += 1
             M.mhs_set_options(h, **M.mhs_tune_lookup(h, M.MHS_MIXED))
         res["autotune"] = {"classes": tuned_classes, "seconds": time.perf_counter() - t0}
-        groups["tuned"] = M.mhs_group_create(hs, M.MHS_MIXED)
-        run("grouped_mixed_tuned", lambda: grp("tuned"))
+        gt = M.mhs_group_create(hs, M.MHS_MIXED)
+        tuned = timed_rounds({"grouped_mixed_tuned": lambda: grp(gt), "batched_mixed_tuned": bat})
+        res.update(tuned)
+        M.mhs_group_destroy(gt)
     res["instances"] = count
-    best = max(v["solves_per_s"] for k, v in res.items() if k.startswith("grouped") or k == "batched_mixed")
+    best = max(v["solves_per_s"] for k, v in res.items() if k.startswith(("grouped", "batched")))
     res["speedup_vs_sequential_fp64"] = best / res["sequential_fp64"]["solves_per_s"]
-    for g in groups.values():
-        M.mhs_group_destroy(g)
     for h in hs:
+        M.mhs_destroy(h)
+    # a batch of small instances: grouping's launches for all of them against one graph per instance
+    small = []
+    for i in range(1024):
+        _, bz = S.linear_mhs(33, seed=5000 + i)
+        h = M.mhs_create(33, 33, 33, 1.0, 1.0, 1.0, 0.5, M.xi_params(M.MHS_XI_EXP, 0.5, 1.0))
+        M.mhs_set_lower_bz(h, torch.from_numpy(bz).cuda())
+        small.append(h)
+    gs = M.mhs_group_create(small, M.MHS_MIXED)
+    sm = timed_rounds({"grouped": lambda: grp(gs, 1024), "batched": lambda: bat(small)}, n=1024, rounds=2)
+    res["small_1024x33"] = {k: v["solves_per_s"] for k, v in sm.items()}
+    M.mhs_group_destroy(gs)
+    for h in small:
         M.mhs_destroy(h)
     torch.cuda.empty_cache()
     return res
