@@ -478,7 +478,7 @@ def run_op(args):
     h = M.mhs_create(pr["nx"], pr["ny"], pr["nz"], pr["Lx"], pr["Ly"], pr["Lz"], pr["alpha"], xi)
     M.mhs_set_stream(h, torch.cuda.current_stream())
     M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE if args.smoother == "zline" else M.MHS_FLAG_POINT,
-                      fused_min=1 if args.tma else 0)
+                      fused_min=1 if args.tma else 0, tma_rows=args.tma_rows)
     prec = M.MHS_FP64 if args.prec == "fp64" else M.MHS_MIXED
     rng = np.random.default_rng(0)
     shape = (pr["nz"], pr["ny"], pr["nx"])
@@ -494,8 +494,20 @@ def run_op(args):
     for _ in range(args.steps):
         M.mhs_level_op(h, 3, 0, op, prec)
     torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3 / args.steps
+    # device time of each kernel kind (CUDA events around every launch, on the library's stream)
+    M.mhs_set_kernel_timing(h, True)
+    M.mhs_kernel_timing_reset(h)
+    for _ in range(args.steps):
+        M.mhs_level_op(h, 3, 0, op, prec)
+    torch.cuda.synchronize()
+    kt = [M.mhs_kernel_timing(h, k) for k in range(M.MHS_KT_COUNT)]
+    M.mhs_set_kernel_timing(h, False)
+    kernels = {k["name"]: {"ms_per_launch": k["ms"] / k["launches"], "launches_per_op": k["launches"] / args.steps,
+                           "gbs": k["bytes"] / (k["ms"] * 1e-3) / 1e9 if k["ms"] > 0 else None}
+               for k in kt if k["launches"]}
     print(json.dumps({"op": args.op, "prec": args.prec, "grid": list(args.grid), "smoother": args.smoother,
-                      "tma": bool(args.tma), "ms_per_op_wall": (time.perf_counter() - t0) * 1e3 / args.steps}))
+                      "tma": bool(args.tma), "tma_rows": args.tma_rows, "ms_per_op_wall": wall, "kernels": kernels}))
     M.mhs_destroy(h)
 
 
@@ -841,6 +853,8 @@ def main():
                     help="grid of --op")
     ap.add_argument("--smoother", choices=["point", "zline"], default="point", help="smoother of --op smooth")
     ap.add_argument("--tma", action="store_true", help="--op smooth in FP32: the fused TMA-staged sweep")
+    ap.add_argument("--tma-rows", type=int, choices=[0, 8, 16], default=0,
+                    help="tile height of the fused TMA-staged sweep (0: the library's default)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the large-grid, batched and serving legs")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the serving leg")

@@ -119,6 +119,9 @@ typedef struct {
     int tile;            /* thread-block shape of the red-black point passes (threads along x, each owning an
                             x pair of nodes, x rows): 1 = 32 x 8, 2 = 64 x 4, 3 = 16 x 16, 4 = 32 x 16,
                             5 = 128 x 2 (results do not depend on it) [1] */
+    int tma_rows;        /* rows of the tiles of the fused, TMA-staged FP32 sweep: 8 (64 x 8 tiles, 256 threads)
+                            or 16 (64 x 16, 512 threads, fewer halo updates per node); results do not depend on
+                            it [8] */
 } mhs_solver_opts;
 
 #define MHS_FLAG_WARM 1         /* start the interior solve from the resident P instead of P = 0 */

@@ -52,7 +52,7 @@ bool is_device_ptr(const void* p) {
 
 mhs_atmos_params default_atmos() { return mhs_atmos_params{1.0, 0.5, 150.0, 5.0, 10.0}; }
 
-mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 12000000, 300000, 1}; }
+mhs_solver_opts default_opts() { return mhs_solver_opts{2, 2, 100, 1, 0, 1200, 4000, 12000000, 300000, 1, 8}; }
 
 void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     *o = default_opts();
@@ -66,6 +66,7 @@ void fill_opts(mhs_solver_opts* o, const mhs_solver_opts* in) {
     if (in->fused_min > 0) o->fused_min = in->fused_min;
     if (in->sep_coarse != 0) o->sep_coarse = in->sep_coarse < 0 ? -1 : in->sep_coarse;
     if (in->tile > 0) o->tile = in->tile;
+    if (in->tma_rows > 0) o->tma_rows = in->tma_rows;
     o->flags = in->flags;
 }
 
@@ -224,7 +225,8 @@ mhs_status mhs_set_stream(mhs_handle h, void* stream) {
 mhs_status mhs_set_options(mhs_handle h, const mhs_solver_opts* opts) {
     if (!h) return fail(MHS_ERR_INVALID_ARG, "handle is NULL");
     if (opts && (opts->nu1 < 0 || opts->nu2 < 0 || opts->max_cycles < 0 || opts->inner_cycles < 0 ||
-                 opts->nu1 > 16 || opts->nu2 > 16 || opts->inner_cycles > 16))
+                 opts->nu1 > 16 || opts->nu2 > 16 || opts->inner_cycles > 16 ||
+                 (opts->tma_rows != 0 && opts->tma_rows != 8 && opts->tma_rows != 16)))
         return fail(MHS_ERR_INVALID_ARG, "options out of range");
     fill_opts(&h->opts, opts);
     return guarded([&] {

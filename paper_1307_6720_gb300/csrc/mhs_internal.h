@@ -116,7 +116,7 @@ struct Hierarchy {
     std::vector<SepTables> sep64, sep32;  // separable-solver tables per level (built on demand)
     DFState df;                           // finest-level double-float state (mixed mode)
     // TMA plane maps of the FP32 arrays u, t, f per level (3D levels; see kernels_tma.cu)
-    std::vector<CUtensorMap> tm_u, tm_t, tm_f;
+    std::vector<CUtensorMap> tm_u, tm_t, tm_f;   // index 2 l + (tiles of 16 rows)
     int nlev() const { return int(g.size()); }
 };
 
@@ -205,9 +205,9 @@ namespace mhs {
 // Everything a captured solve depends on besides device memory: the options
 // and the choices derived from them and from the problem.
 struct GraphKey {
-    int v[11];
+    int v[12];
     bool operator==(const GraphKey& o) const {
-        for (int q = 0; q < 11; ++q)
+        for (int q = 0; q < 12; ++q)
             if (v[q] != o.v[q]) return false;
         return true;
     }
@@ -393,8 +393,8 @@ void launch_trace(int nx, int ny, int nz, double Lx, double Ly, double Lz, size_
                   double dir, double* points, int* lengths, cudaStream_t st);
 
 // ---- TMA-staged fused sweep for FP32 levels (kernels_tma.cu) ----
-void make_plane_map(CUtensorMap* map, const Geom& g, const float* base);
-void launch_sweep_tma(const Geom& g, const CUtensorMap& tm_in, const CUtensorMap& tm_f,
+void make_plane_map(CUtensorMap* map, const Geom& g, const float* base, int rows);
+void launch_sweep_tma(const Geom& g, int rows, const CUtensorMap& tm_in, const CUtensorMap& tm_f,
                       const PlaneCoef<float>* coef, float* uout, int* err, cudaStream_t st);
 
 // ---- control and sub-cycle (kernels_ctl.cu) ----

@@ -105,14 +105,15 @@ static void build_hierarchy(mhs_ctx* c, Hierarchy& H, int dim) {
         H.s.push_back(s);
     }
     if (dim == 3) {
-        H.tm_u.resize(H.g.size());
-        H.tm_t.resize(H.g.size());
-        H.tm_f.resize(H.g.size());
-        for (size_t l = 0; l < H.g.size(); ++l) {
-            make_plane_map(&H.tm_u[l], H.g[l], H.s[l].u);
-            make_plane_map(&H.tm_t[l], H.g[l], H.s[l].t);
-            make_plane_map(&H.tm_f[l], H.g[l], H.s[l].f);
-        }
+        H.tm_u.resize(2 * H.g.size());
+        H.tm_t.resize(2 * H.g.size());
+        H.tm_f.resize(2 * H.g.size());
+        for (size_t l = 0; l < H.g.size(); ++l)
+            for (int r = 0; r < 2; ++r) {   // tiles of 8 and of 16 rows
+                make_plane_map(&H.tm_u[2 * l + r], H.g[l], H.s[l].u, 8 << r);
+                make_plane_map(&H.tm_t[2 * l + r], H.g[l], H.s[l].t, 8 << r);
+                make_plane_map(&H.tm_f[2 * l + r], H.g[l], H.s[l].f, 8 << r);
+            }
     }
     const Geom& g0 = H.g[0];
     H.df.hi = static_cast<float*>(dev_alloc(c, g0.n * sizeof(float)));
@@ -284,8 +285,9 @@ static void smooth_n(mhs_ctx* c, Hierarchy& H, int l, const T* f, int n, bool fi
         TimedScope t(c->timer, dbl ? MHS_KT_SMOOTH64 : MHS_KT_SMOOTH32, bytes, flops, c->stream, fine);
         const bool even = (q & 1) == 0;
         if (tma) {
-            launch_sweep_tma(g, even ? H.tm_u[l] : H.tm_t[l], H.tm_f[l], H.s[l].coef, even ? H.s[l].t : H.s[l].u,
-                             c->flag + 1, c->stream);
+            const int rows = c->opts.tma_rows, m = 2 * l + (rows == 16 ? 1 : 0);
+            launch_sweep_tma(g, rows, even ? H.tm_u[m] : H.tm_t[m], H.tm_f[m], H.s[l].coef,
+                             even ? H.s[l].t : H.s[l].u, c->flag + 1, c->stream);
         } else if (fused) {
             launch_sweep<T>(g, A.coef, even ? A.u : A.t, f, even ? A.t : A.u, c->stream);
         } else {
@@ -698,7 +700,7 @@ static GraphKey graph_key(mhs_ctx* c) {
     const int flags = c->opts.flags & ~(MHS_FLAG_NO_GRAPH | MHS_FLAG_ZLINE | MHS_FLAG_POINT | MHS_FLAG_BZ_MIMETIC);
     return GraphKey{{c->opts.nu1, c->opts.nu2, c->opts.inner_cycles, flags, c->opts.cut64, c->opts.cut32,
                      c->opts.fused_min, c->opts.sep_coarse, c->f_zero_finest ? 1 : 0, use_zline(c) ? 1 : 0,
-                     c->opts.tile}};
+                     c->opts.tile, c->opts.tma_rows}};
 }
 
 constexpr size_t GRAPH_CACHE = 8;   // captured solves kept per precision mode

@@ -11,7 +11,8 @@
 //   - the sweep counts (nu1, nu2),
 //   - the sub-cycle cut-off (cut64 in FP64 mode, cut32 in mixed mode), one
 //     candidate per level that the sub-cycle could start from,
-//   - the fused TMA sweep threshold on FP32 levels (mixed mode, point smoother),
+//   - the fused TMA sweep threshold on FP32 levels (mixed mode, point smoother)
+//     and the height of its tiles (tma_rows),
 //   - the full-multigrid first cycle (MHS_FLAG_NO_FMG),
 //   - the thread-block shape of the red-black point passes (tile),
 // at most two rounds, a change kept only when it saves at least 3 %.  The
@@ -148,6 +149,12 @@ void autotune(mhs_ctx* c, double tol, int mode, int repeats, mhs_tune_result* ou
                 o.fused_min = fm;
                 consider(o);
             }
+            if (best.fused_min != INT_MAX)
+                for (int rows : {8, 16}) {   // tile height of the fused sweep
+                    mhs_solver_opts o = best;
+                    o.tma_rows = rows;
+                    consider(o);
+                }
         }
         {
             mhs_solver_opts o = best;

@@ -45,7 +45,8 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_int), ("cut64", ctypes.c_int),
                 ("cut32", ctypes.c_int), ("fused_min", ctypes.c_int), ("sep_coarse", ctypes.c_int),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int),
+                ("tma_rows", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -235,8 +236,8 @@ def mhs_set_stream(h, stream) -> None:
 
 
 def mhs_set_options(h, nu1=0, nu2=0, max_cycles=0, inner_cycles=0, flags=0, cut64=0, cut32=0, fused_min=0,
-                    sep_coarse=0, tile=0) -> None:
-    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min, sep_coarse, tile)
+                    sep_coarse=0, tile=0, tma_rows=0) -> None:
+    o = SolverOpts(nu1, nu2, max_cycles, inner_cycles, flags, cut64, cut32, fused_min, sep_coarse, tile, tma_rows)
     _check(LIB.mhs_set_options(h, ctypes.byref(o)))
 
 

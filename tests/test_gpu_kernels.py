@@ -415,11 +415,15 @@ def test_fused_sweep_fp64_solve_matches_default(M):
     assert np.array_equal(res[0][1], res[1][1])
 
 
-@pytest.mark.parametrize("shape", [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5), (129, 9, 65), (129, 129, 65)])
-def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
+@pytest.mark.parametrize("rows", [8, 16])
+@pytest.mark.parametrize("shape", [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5), (129, 9, 65), (129, 129, 65),
+                                   (67, 19, 21), (131, 35, 11)])
+def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape, rows):
     """FP32 sweeps with TMA-staged planes (mbarrier pipeline) give bitwise the
     results of the same sweep with plain global loads, over several sweeps
-    and z-chunks, with non-zero Dirichlet data on every face."""
+    and z-chunks, with non-zero Dirichlet data on every face, for tiles of 8
+    and of 16 rows (ragged last tiles in x and y: 65 and 129 interior columns,
+    17 and 33 interior rows)."""
     nx, ny, nz = shape
     rng = np.random.default_rng(2 * nx + ny + nz)
     u = rng.standard_normal((nz, ny, nx))
@@ -427,7 +431,7 @@ def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
     out = []
     for flags in (0, M.MHS_FLAG_NO_TMA):
         pr, h = _make(M, nx, ny, nz)
-        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT, fused_min=1)
+        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT, fused_min=1, tma_rows=rows)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, 1, u)
         M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, 1, f)
         for _ in range(5):
@@ -437,6 +441,16 @@ def test_tma_sweep_equals_plain_fused_sweep_fp32(M, shape):
     assert np.array_equal(out[0], out[1])
     u32, f32 = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
     assert _rel(out[0], oracle.rbgs3d(pr, u32, f32, 5)) < 1e-4
+
+
+def test_tma_rows_other_than_8_or_16_are_rejected(M):
+    pr, h = _make(M, 17, 9, 13)
+    try:
+        for rows in (4, 12, 32):
+            with pytest.raises(M.MhsError):
+                M.mhs_set_options(h, flags=M.MHS_FLAG_POINT, tma_rows=rows)
+    finally:
+        M.mhs_destroy(h)
 
 
 @pytest.mark.parametrize("mode", [1, 0])
