@@ -481,33 +481,40 @@ def run_op(args):
                       fused_min=1 if args.tma else 0, tma_rows=args.tma_rows)
     prec = M.MHS_FP64 if args.prec == "fp64" else M.MHS_MIXED
     rng = np.random.default_rng(0)
-    shape = (pr["nz"], pr["ny"], pr["nx"])
+    dim = args.dim
+    shape = (pr["nz"], pr["ny"], pr["nx"]) if dim == 3 else (pr["ny"], pr["nx"])
     for field in (M.MHS_FIELD_U, M.MHS_FIELD_F, M.MHS_FIELD_R):
-        M.mhs_level_write(h, 3, 0, field, prec, rng.standard_normal(shape))
+        M.mhs_level_write(h, dim, 0, field, prec, rng.standard_normal(shape))
     op = {"smooth": M.MHS_OP_SMOOTH, "residual": M.MHS_OP_RESIDUAL, "restrict": M.MHS_OP_RESTRICT,
           "prolong": M.MHS_OP_PROLONG, "vcycle": M.MHS_OP_VCYCLE, "exact": M.MHS_OP_EXACT,
           "resid_restrict": M.MHS_OP_RESID_RESTRICT}[args.op]
     for _ in range(args.warmup):
-        M.mhs_level_op(h, 3, 0, op, prec)
+        M.mhs_level_op(h, dim, 0, op, prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        M.mhs_level_op(h, 3, 0, op, prec)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s in range(args.steps):   # every level op ends with a synchronisation of the library's stream
+        ev[s][0].record(stream)
+        M.mhs_level_op(h, dim, 0, op, prec)
+        ev[s][1].record(stream)
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) * 1e3 / args.steps
+    dev_ms = sorted(a.elapsed_time(b) for a, b in ev)
     # device time of each kernel kind (CUDA events around every launch, on the library's stream)
     M.mhs_set_kernel_timing(h, True)
     M.mhs_kernel_timing_reset(h)
     for _ in range(args.steps):
-        M.mhs_level_op(h, 3, 0, op, prec)
+        M.mhs_level_op(h, dim, 0, op, prec)
     torch.cuda.synchronize()
     kt = [M.mhs_kernel_timing(h, k) for k in range(M.MHS_KT_COUNT)]
     M.mhs_set_kernel_timing(h, False)
     kernels = {k["name"]: {"ms_per_launch": k["ms"] / k["launches"], "launches_per_op": k["launches"] / args.steps,
                            "gbs": k["bytes"] / (k["ms"] * 1e-3) / 1e9 if k["ms"] > 0 else None}
                for k in kt if k["launches"]}
-    print(json.dumps({"op": args.op, "prec": args.prec, "grid": list(args.grid), "smoother": args.smoother,
-                      "tma": bool(args.tma), "tma_rows": args.tma_rows, "ms_per_op_wall": wall, "kernels": kernels}))
+    print(json.dumps({"op": args.op, "dim": dim, "prec": args.prec, "grid": list(args.grid), "smoother": args.smoother,
+                      "tma": bool(args.tma), "tma_rows": args.tma_rows, "ms_per_op_wall": wall,
+                      "ms_per_op_device_median": dev_ms[len(dev_ms) // 2], "kernels": kernels}))
     M.mhs_destroy(h)
 
 
@@ -852,6 +859,8 @@ def main():
     ap.add_argument("--grid", type=int, nargs=3, default=[129, 129, 129], metavar=("NX", "NY", "NZ"),
                     help="grid of --op")
     ap.add_argument("--smoother", choices=["point", "zline"], default="point", help="smoother of --op smooth")
+    ap.add_argument("--dim", type=int, choices=[2, 3], default=3,
+                    help="--op on the finest level of the interior (3) or lower-boundary (2) hierarchy")
     ap.add_argument("--tma", action="store_true", help="--op smooth in FP32: the fused TMA-staged sweep")
     ap.add_argument("--tma-rows", type=int, choices=[0, 8, 16], default=0,
                     help="tile height of the fused TMA-staged sweep (0: the library's default)")

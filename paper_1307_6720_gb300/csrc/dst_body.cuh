@@ -95,14 +95,26 @@ __device__ __forceinline__ void fft_pass(C* z, const C* tw, int P, int PS, int b
     }
 }
 
-// The first three stages (half-sizes 1, 2, 4) as one radix-8 pass whose
-// twiddles are the eighth roots of unity e^{-i pi q / 4}: multiplications by
-// 1 and -i become additions and swaps, those by (+-1 - i)/sqrt(2) two
-// additions and two multiplications.
+// Butterfly of the first three stages (half-sizes 1, 2, 4), whose twiddles
+// are eighth roots of unity e^{-i pi q / 4}: multiplications by 1 and -i
+// become additions and swaps, those by (+-1 - i)/sqrt(2) two additions and
+// two rounded multiplications.  a, b <- a + t, a - t with t = b e^{-i pi q / 4}.
 template <typename C>
-__device__ __forceinline__ void fft_first(C* z, int P, int PS, int bits) {
+__device__ __forceinline__ void first_bfly(C& a, C& b, int q) {
     using T = decltype(C{}.x);
     const T c = T(0.70710678118654752440);
+    C t;
+    if (q == 0) t = b;
+    else if (q == 1) t = C{mul_rn(b.x + b.y, c), mul_rn(b.y - b.x, c)};
+    else if (q == 2) t = C{b.y, -b.x};
+    else t = C{mul_rn(b.y - b.x, c), -mul_rn(b.x + b.y, c)};
+    b = C{a.x - t.x, a.y - t.y};
+    a = C{a.x + t.x, a.y + t.y};
+}
+
+// The first three stages as one radix-8 pass in registers.
+template <typename C>
+__device__ __forceinline__ void fft_first(C* z, int P, int PS, int bits) {
     const int ub = bits - 3;
     const int units = P << ub;
     for (int e = threadIdx.x; e < units; e += blockDim.x) {
@@ -112,25 +124,40 @@ __device__ __forceinline__ void fft_first(C* z, int P, int PS, int bits) {
         C v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = zp[phys(base + j)];
-        auto add = [](C& a, C& b, const C t) {   // a, b <- a + t, a - t
-            b = C{a.x - t.x, a.y - t.y};
-            a = C{a.x + t.x, a.y + t.y};
-        };
         // half-size 1: twiddle 1
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) add(v[j], v[j + 1], v[j + 1]);
+        for (int j = 0; j < 8; j += 2) first_bfly(v[j], v[j + 1], 0);
         // half-size 2: twiddles 1, -i
-        add(v[0], v[2], v[2]);
-        add(v[4], v[6], v[6]);
-        add(v[1], v[3], C{v[3].y, -v[3].x});
-        add(v[5], v[7], C{v[7].y, -v[7].x});
+        first_bfly(v[0], v[2], 0);
+        first_bfly(v[4], v[6], 0);
+        first_bfly(v[1], v[3], 2);
+        first_bfly(v[5], v[7], 2);
         // half-size 4: twiddles 1, (1 - i)/sqrt2, -i, (-1 - i)/sqrt2
-        add(v[0], v[4], v[4]);
-        add(v[1], v[5], C{(v[5].x + v[5].y) * c, (v[5].y - v[5].x) * c});
-        add(v[2], v[6], C{v[6].y, -v[6].x});
-        add(v[3], v[7], C{(v[7].y - v[7].x) * c, -(v[7].x + v[7].y) * c});
+#pragma unroll
+        for (int j = 0; j < 4; ++j) first_bfly(v[j], v[j + 4], j);
 #pragma unroll
         for (int j = 0; j < 8; ++j) zp[phys(base + j)] = v[j];
+    }
+}
+
+// One radix-2 stage (half-size H = 2^s) of every pair, one butterfly per
+// unit: the operations of the radix-8 passes, butterfly for butterfly
+// (first_bfly below half-size 8, bfly with the table twiddle from there on),
+// spread over more threads, for blocks with few pairs.
+template <typename C>
+__device__ __forceinline__ void fft_stage(C* z, const C* tw, int P, int PS, int bits, int L, int s) {
+    const int H = 1 << s, hb = bits - 1;
+    const int units = P << hb;
+    for (int e = threadIdx.x; e < units; e += blockDim.x) {
+        const int pair = e >> hb, b = e & ((1 << hb) - 1);
+        const int r = b & (H - 1);
+        const int i0 = ((b >> s) << (s + 1)) + r;
+        C* zp = z + pair * PS;
+        C va = zp[phys(i0)], vb = zp[phys(i0 + H)];
+        if (s < 3) first_bfly(va, vb, r << (2 - s));
+        else bfly(va, vb, tw[r * (L >> s)]);
+        zp[phys(i0)] = va;
+        zp[phys(i0 + H)] = vb;
     }
 }
 
@@ -216,10 +243,25 @@ __device__ __forceinline__ void dst_load(typename Cplx<T>::type* z, int PS, int 
 
 // The FFT of every pair of the block: radix-8 passes (the first with
 // constant twiddles), the remaining one or two stages last.  Synchronises
-// after every pass.
+// after every pass.  An FP64 block with fewer radix-8 units than four
+// warps' lanes (few pairs) runs the same butterflies stage by stage instead:
+// the FP64 pipe charges each warp instruction whatever its active lanes, so a
+// lone warp's radix-8 units cost their full length in issue time, while one
+// butterfly per thread per stage spreads them over several warps.  Both
+// schedules give the same words.  Not inlined: a kernel that transforms along
+// x and y, forward and back, runs one copy of this code (fetched once into
+// the instruction cache) instead of four, and every kernel family runs the
+// same compiled operations.
 template <typename T>
-__device__ __forceinline__ void dst_fft(typename Cplx<T>::type* z, const typename Cplx<T>::type* tw, int P, int PS,
+__device__ __noinline__ void dst_fft(typename Cplx<T>::type* z, const typename Cplx<T>::type* tw, int P, int PS,
                                         int bits, int L) {
+    if (sizeof(T) == 8 && bits >= 3 && (P << (bits - 3)) < 128) {
+        for (int s = 0; s < bits; ++s) {
+            fft_stage(z, tw, P, PS, bits, L, s);
+            __syncthreads();
+        }
+        return;
+    }
     int s = 0;
     if (bits >= 3) {
         fft_first(z, P, PS, bits);
@@ -245,7 +287,7 @@ __device__ __forceinline__ void dst_fft(typename Cplx<T>::type* z, const typenam
 // .. + R_k (lane runs of `per` k's, then a warp scan of the run totals); FP32:
 // X_a = -Im(Z_m)/2, X_b = Re(Z_m)/2.  The caller synchronises afterwards.
 template <typename T>
-__device__ __forceinline__ void dst_post(const typename Cplx<T>::type* z, int PS, int nl, int N, T* ob) {
+__device__ __noinline__ void dst_post(const typename Cplx<T>::type* z, int PS, int nl, int N, T* ob) {
     using C = typename Cplx<T>::type;
     if constexpr (sizeof(T) == 8) {
         const int H = N / 2;
