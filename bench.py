@@ -188,17 +188,20 @@ def measured_peaks():
 FP64_NOMINAL_TFLOPS = 1.25   # nominal GB300 FP64 rate (profiling recipe table)
 
 
-def profiled_traffic(kind_name: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's source is unchanged: the text of
-    the measured device function when the summary names it (body, body_sha256), else the whole file."""
+def profiled_traffic(kind_name: str, grid=None):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's source is unchanged (the text of the
+    measured function when the summary names it: body_prefix, or the device function `body`; else the whole
+    file) and, when the summary names one, the finest grid is the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
         ent = d["kernels"][kind_name]
+        if "grid" in ent and grid is not None and list(grid) != list(ent["grid"]):
+            return None
         import hashlib
         src = open(os.path.join(ROOT, ent["source"])).read()
-        if "body" in ent:
-            start = src.index("__device__ __forceinline__ void " + ent["body"] + "(")
+        if "body" in ent or "body_prefix" in ent:
+            start = src.index(ent.get("body_prefix", "__device__ __forceinline__ void " + ent.get("body", "") + "("))
             text, want = src[start:src.index("\n}\n", start) + 3], ent["body_sha256"]
         else:
             text, want = src, ent["sha256"]
@@ -243,7 +246,7 @@ def kernel_roofline(M, h, run, steps, hbm_peak, peak_src, fp64_peak):
     gbs = dom["bytes"] / dom["launches"] / (avg_ms * 1e-3) / 1e9
     tfl = dom["flops"] / dom["launches"] / (avg_ms * 1e-3) / 1e12
     alu_bound = dom["name"].endswith("64") or dom["name"] == "fields"   # FP64-pipe-bound kernels
-    traffic = profiled_traffic(dom["name"])
+    traffic = profiled_traffic(dom["name"], M.mhs_level_shape(h, 3, 0))
     kname = dom["name"] + (" (finest level)" if finest else "")
     if alu_bound:
         roof = {"bound": "alu", "achieved": tfl, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tfl / fp64_peak,
