@@ -187,7 +187,8 @@ void build_dim(GPart* G, GDim& D, int dim) {
             const Geom& g = H.g[l];
             const Geom& gc = H.g[l + 1];
             T* f = (fz && l == 0) ? nullptr : A.f;
-            GItem s = item(q, line ? zline_grid(g) : fat(smooth_grid_t<T>(g, d3)), g, ctl);
+            GItem s = item(q, line ? (sizeof(T) == 4 ? zline_part_grid(g) : zline_grid(g)) : fat(smooth_grid_t<T>(g, d3)),
+                           g, ctl);
             s.coef = A.coef;
             s.p[0] = A.u;
             s.p[1] = f;
@@ -453,6 +454,17 @@ void build_dim(GPart* G, GDim& D, int dim) {
     up(post_pt, D.post_pt);
     up(pre_ln, D.pre_ln);
     up(post_ln, D.post_ln);
+    // launch shape of the partitioned FP32 z-line passes: the most segments and
+    // the largest shared-memory need among the items of a launch
+    for (auto* pr : {&pre_ln, &post_ln}) {
+        std::vector<GTable>& dst = pr == &pre_ln ? D.pre_ln : D.post_ln;
+        for (size_t l = 0; l < pr->size(); ++l)
+            for (const GItem& it : (*pr)[l]) {
+                const int n = it.g.nz - 2, S = zpart_segments(n);
+                dst[l].ty = std::max(dst[l].ty, S);
+                dst[l].smem = std::max(dst[l].smem, unsigned(zpart_smem(n, S)));
+            }
+    }
     up(res, D.res);
     up(restr, D.restr);
     up(resr, D.resr);

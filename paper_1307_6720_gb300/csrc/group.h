@@ -33,6 +33,8 @@ struct GTable {
     GItem* items = nullptr;   // device
     int n = 0;                // items
     int blocks = 0;           // sum of the items' grid sizes
+    int ty = 0;               // FP32 z-line passes: warps per block (most segments of the items' columns)
+    unsigned smem = 0;        // and their dynamic shared memory (the largest item's)
 };
 
 // launchers (kernels_group.cu); `sweep` gates smoothing items by ia[0] > sweep,

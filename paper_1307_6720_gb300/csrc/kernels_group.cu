@@ -72,6 +72,18 @@ __global__ void __launch_bounds__(LX* LY) g_zline_kernel(const GItem* items, int
                      static_cast<const T*>(it.p[1]), static_cast<T*>(it.p[2]), colour, zline_hx(it.g), k.b);
 }
 
+// FP32 levels: the partitioned column solve; the block has as many warps as
+// the most segments among the launch's items
+template <int SY>
+__global__ void __launch_bounds__(32 * SY) g_zline_part_kernel(const GItem* items, int n, int colour,
+                                                                               int sweep, int fmg_step, int gate) {
+    GBlock k;
+    if (!locate(items, n, gate, sweep, fmg_step, k)) return;
+    const GItem& it = *k.it;
+    zline_part_body(it.g, static_cast<const PlaneCoef<float>*>(it.coef), static_cast<float*>(it.p[0]),
+                    static_cast<const float*>(it.p[1]), colour, zline_hx(it.g), k.b);
+}
+
 template <typename T, bool D3, bool NORM>
 __global__ void g_residual_kernel(const GItem* items, int n, int fmg_step, int gate) {
     GBlock k;
@@ -254,7 +266,19 @@ void glaunch_colour(const GTable& t, int d3, int colour, int sweep, int fmg_step
 template <typename T>
 void glaunch_zline(const GTable& t, int colour, int sweep, int fmg_step, int gate, cudaStream_t st) {
     if (!t.n) return;
-    g_zline_kernel<T, ZLINE_U<T>><<<t.blocks, kLine, 0, st>>>(t.items, t.n, colour, sweep, fmg_step, gate);
+    if constexpr (sizeof(T) == 4) {
+        static bool attr = false;
+        if (!attr) {
+            MHS_CUDA(cudaFuncSetAttribute(g_zline_part_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            MHS_CUDA(cudaFuncSetAttribute(g_zline_part_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            attr = true;
+        }
+        const dim3 blk(32, t.ty);
+        if (t.ty <= 8) g_zline_part_kernel<8><<<t.blocks, blk, t.smem, st>>>(t.items, t.n, colour, sweep, fmg_step, gate);
+        else g_zline_part_kernel<32><<<t.blocks, blk, t.smem, st>>>(t.items, t.n, colour, sweep, fmg_step, gate);
+    } else {
+        g_zline_kernel<T, ZLINE_U<T>><<<t.blocks, kLine, 0, st>>>(t.items, t.n, colour, sweep, fmg_step, gate);
+    }
     after_launch();
 }
 

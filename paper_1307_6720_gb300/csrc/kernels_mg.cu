@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "device_util.cuh"
+#include "line_body.cuh"
 #include "mg_bodies.cuh"
 #include "mhs_internal.h"
 #include "solver.h"
@@ -74,10 +75,13 @@ __global__ void coef_kernel(Geom g, int dim, double alpha, mhs_xi_params xi, Pla
 // Elimination factors of the z-line smoother's column systems: the plane
 // coefficients in FP64 by all threads of the block (into shared memory),
 // then the pivot recursion over the interior planes by one thread; rounded
-// to T at the end.  Levels have at most 1026 planes.
+// to T at the end.  Levels have at most 1026 planes.  Also the factors of the
+// partitioned column solve (line_body.cuh): one thread per segment forms the
+// segment's pivots and its responses g = T_p^-1 e_first, h = T_p^-1 e_last to
+// unit interface values, then one thread the interface system's factors.
 template <typename T>
 __global__ void line_coef_kernel(Geom g, double alpha, mhs_xi_params xi, PlaneCoef<T>* coef) {
-    __shared__ double sd[1026];
+    __shared__ double sd[1026], sg[1026], sh[1026];
     __shared__ double scz;
     for (int k = threadIdx.x; k < g.nz && k < 1026; k += blockDim.x) {
         double cx, cy, cz, d;
@@ -86,14 +90,57 @@ __global__ void line_coef_kernel(Geom g, double alpha, mhs_xi_params xi, PlaneCo
         if (k == 0) scz = cz;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
     const double cz = scz;
-    double sup = 0.0;
-    for (int k = 1; k <= g.nz - 2 && k < 1026; ++k) {
-        const double lm = 1.0 / (sd[k] - (k > 1 ? cz * sup : 0.0));
-        sup = cz * lm;
-        coef[k].lm = T(lm);
-        coef[k].lsup = T(sup);
+    const int n = min(g.nz - 2, 1024);
+    const int S = zpart_segments(n), m = zpart_len(n, S);
+    if (threadIdx.x == 0) {
+        double sup = 0.0;
+        for (int k = 1; k <= n; ++k) {
+            const double lm = 1.0 / (sd[k] - (k > 1 ? cz * sup : 0.0));
+            sup = cz * lm;
+            coef[k].lm = T(lm);
+            coef[k].lsup = T(sup);
+        }
+    }
+    const int p = int(threadIdx.x) - 32;   // warp 1: one thread per segment
+    if (p >= 0 && p < S) {
+        const int a = 1 + p * (m + 1), e = min(a + m - 1, n);
+        double lm[ZP_MMAX], sup[ZP_MMAX], wg[ZP_MMAX];
+        for (int k = a; k <= e; ++k) {
+            const int q = k - a;
+            lm[q] = 1.0 / (sd[k] - (q > 0 ? cz * sup[q - 1] : 0.0));
+            sup[q] = cz * lm[q];
+            wg[q] = (q > 0 ? -cz * wg[q - 1] : 1.0) * lm[q];   // forward elimination of e_first
+        }
+        double gk = 0.0, hk = 0.0;
+        for (int k = e; k >= a; --k) {
+            const int q = k - a;
+            gk = k == e ? wg[q] : wg[q] - sup[q] * gk;
+            hk = k == e ? lm[q] : -sup[q] * hk;   // e_last: forward values vanish above the last row
+            sg[k] = gk;
+            sh[k] = hk;
+            coef[k].zlm = T(lm[q]);
+            coef[k].zsup = T(sup[q]);
+            coef[k].zg = T(gk);
+            coef[k].zh = T(hk);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && S > 1) {
+        const double cz2 = cz * cz;
+        double rsup = 0.0;
+        for (int q = 1; q < S; ++q) {
+            const int c = q * (m + 1);   // interface plane: last of segment q-1 below, first of segment q above
+            const double L = q >= 2 ? -cz2 * sg[c - 1] : 0.0;
+            const double D = sd[c] - cz2 * (sh[c - 1] + sg[c + 1]);
+            const double U = q <= S - 2 ? -cz2 * sh[c + 1] : 0.0;
+            const double rlm = 1.0 / (D - L * rsup);
+            rsup = U * rlm;
+            coef[c].zlm = T(rlm);
+            coef[c].zsup = T(rsup);
+            coef[c].zg = T(L);
+            coef[c].zh = T(0);
+        }
     }
 }
 

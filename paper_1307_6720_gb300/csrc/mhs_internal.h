@@ -48,6 +48,13 @@ struct PlaneCoef {
     // that the separable solver's mode systems keep after the horizontal terms
     // are diagonalised (it would cancel against them if taken from d)
     T base;
+    // partitioned column solve of the FP32 z-line smoother (line_body.cuh):
+    // on a plane inside a segment, the segment's own elimination factors
+    // (zlm = 1 / local pivot, zsup = cz zlm) and the segment solution's
+    // responses zg, zh to unit values at its lower and upper interface planes;
+    // on an interface plane, the factors of the interface system (zlm = 1 /
+    // pivot, zsup = eliminated super-diagonal, zg = sub-diagonal, zh = 0)
+    T zlm, zsup, zg, zh;
 };
 
 // Geometry of one level.  Device arrays are pitched: element (i,j,k) at
