@@ -495,11 +495,15 @@ XI_STRONG = dict(xi_kind=1, xi_a=0.99, xi_kappa=0.5)   # 1 - xi(0) = 0.01: stron
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("shape", [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5), (129, 9, 65), (7, 67, 21)])
+@pytest.mark.parametrize("shape", [(17, 9, 13), (33, 17, 9), (65, 33, 33), (5, 5, 5), (129, 9, 65), (7, 67, 21),
+                                   (9, 7, 53), (5, 9, 129), (7, 5, 201)])
 def test_zline_sweep_parity(M, shape, prec):
-    """Zebra z-line sweeps (one thread per column, Thomas elimination with
-    precomputed pivots) against the oracle's line sweeps, three sweeps with
-    non-zero Dirichlet data on every face."""
+    """Zebra z-line sweeps against the oracle's line sweeps, three sweeps with
+    non-zero Dirichlet data on every face.  FP64 levels solve each column by
+    one thread (Thomas elimination with precomputed pivots); FP32 levels by
+    the partitioned solve, whose segment count follows nz: 1 (nz <= 25), 2, 4
+    (nz 53: a ragged last segment of 9 planes), 8 (nz 129) and 16 (nz 201:
+    segments of 12 planes, the last of 4)."""
     nx, ny, nz = shape
     pr, h = _make(M, nx, ny, nz, xi=XI_STRONG)
     M.mhs_set_options(h, flags=M.MHS_FLAG_ZLINE)
