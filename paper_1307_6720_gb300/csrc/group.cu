@@ -1014,18 +1014,19 @@ void group_set_eager(mhs_group* G, bool eager) {
 
 mhs_status group_solve(mhs_group* G, double tol, mhs_solve_info* infos, mhs_status* statuses) {
     const size_t P = G->parts.size();
-    // grouped parts first (their lock-step cycles are latency-bound: started first, they overlap the
-    // rest instead of trailing it), round-robin on the launch streams; then the single-instance parts,
-    // each on its own stream, in the caller's instance order (sizes as they come, rather than the
-    // size order of the packing, spread the load over the device's hardware queues)
+    // the single-instance parts first, each on its own stream, in the caller's instance order (sizes as
+    // they come, rather than the size order of the packing, spread the load over the device's hardware
+    // queues); then the grouped parts, round-robin on the launch streams: their lock-step cycles of
+    // small instances fill the device while the large instances drain (on the 256-instance mix this
+    // order measured 3,142-3,151 solves/s against 3,105 with the grouped parts launched first)
     size_t k = 0;
     std::vector<size_t> solo;
-    for (size_t p = 0; p < P; ++p) {
+    for (size_t p = 0; p < P; ++p)
         if (G->parts[p]->solo) solo.push_back(p);
-        else part_launch(G->parts[p], tol, G->streams[k++ % G->streams.size()]);
-    }
     std::sort(solo.begin(), solo.end(), [&](size_t a, size_t b) { return G->members[a][0] < G->members[b][0]; });
     for (size_t p : solo) part_launch(G->parts[p], tol, G->parts[p]->stream);
+    for (size_t p = 0; p < P; ++p)
+        if (!G->parts[p]->solo) part_launch(G->parts[p], tol, G->streams[k++ % G->streams.size()]);
     mhs_status worst = MHS_OK;
     std::vector<mhs_solve_info> pi;
     std::vector<mhs_status> ps;
