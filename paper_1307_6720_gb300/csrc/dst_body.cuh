@@ -282,9 +282,10 @@ __device__ __noinline__ void dst_fft(typename Cplx<T>::type* z, const typename C
 }
 
 // The transforms X_1 .. X_{N-1} of the nl lines into ob (element m - 1 of
-// line l at ob[l N + m - 1]).  FP64: a warp per line forms R_k, I_k from Z_k
-// and Z_{N-k}, X_{2k} = -I_k and the prefix sums X_{2k+1} = R_0/2 + R_1 +
-// .. + R_k (lane runs of `per` k's, then a warp scan of the run totals); FP32:
+// line l at ob[l N + m - 1]).  FP64: lanes form R_k, I_k from Z_k and
+// Z_{N-k}, X_{2k} = -I_k and the prefix sums X_{2k+1} = R_0/2 + R_1 + .. + R_k
+// (lane runs of `per` consecutive k's, at least 4 on lines of 8 points or
+// more, then a scan of the run totals over the line's lanes); FP32:
 // X_a = -Im(Z_m)/2, X_b = Re(Z_m)/2.  The caller synchronises afterwards.
 template <typename T>
 __device__ __noinline__ void dst_post(const typename Cplx<T>::type* z, int PS, int nl, int N, T* ob) {
@@ -292,12 +293,21 @@ __device__ __noinline__ void dst_post(const typename Cplx<T>::type* z, int PS, i
     if constexpr (sizeof(T) == 8) {
         const int H = N / 2;
         const unsigned full = 0xffffffffu;
+        // lpl lanes per line, each over a run of at least 4 consecutive k's
+        // (up to 32 lanes): the scan's FP64 steps, each a full warp
+        // instruction, are shared by the run; a warp takes 32 / lpl lines at once
+        int lpl = 32;
+        while (lpl > 1 && 4 * lpl > H) lpl >>= 1;
+        const int per = (H + lpl - 1) / lpl;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        const int per = (H + 31) / 32, j0 = lane * per;
-        for (int l = warp; l < nl; l += nwarps) {
-            const C* zp = z + (l >> 1) * PS;
+        const int lpw = 32 / lpl, sub = lane / lpl, sl = lane - sub * lpl;
+        const int j0 = sl * per;
+        for (int l0 = warp * lpw; l0 < nl; l0 += nwarps * lpw) {   // warp-uniform: every lane takes part in the scan
+            const int l = l0 + sub;
+            const bool has = l < nl;
+            const C* zp = z + (has ? (l >> 1) * PS : 0);
             const int comp = l & 1;
-            T* o = ob + l * N;
+            T* o = ob + (has ? l * N : 0);
             auto rk = [&](int j, T& R, T& I) {
                 const C zk = zp[phys(j)], zr = zp[phys((N - j) & (N - 1))];
                 R = T(0.5) * (comp ? zk.y + zr.y : zk.x + zr.x);
@@ -312,25 +322,25 @@ __device__ __noinline__ void dst_post(const typename Cplx<T>::type* z, int PS, i
 #pragma unroll
             for (int q = 0; q < KEEP; ++q) {
                 const int j = j0 + q;
-                if (q < per && j < H) {
+                if (has && q < per && j < H) {
                     rk(j, Rk[q], Ik[q]);
                     run = add_rn(run, Rk[q]);
                 }
             }
             for (int q = KEEP; q < per; ++q) {
                 const int j = j0 + q;
-                if (j < H) {
+                if (has && j < H) {
                     T R, I;
                     rk(j, R, I);
                     run = add_rn(run, R);
                 }
             }
             T incl = run;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const T v = __shfl_up_sync(full, incl, off);
-                if (lane >= off) incl += v;
+            for (int off = 1; off < lpl; off <<= 1) {
+                const T v = __shfl_up_sync(full, incl, off, lpl);
+                if (sl >= off) incl += v;
             }
+            if (!has) continue;
             T acc = incl - run;
 #pragma unroll
             for (int q = 0; q < KEEP; ++q) {
