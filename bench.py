@@ -110,6 +110,13 @@ class ClockSampler:
 # reference arm and CPU baseline: the oracle on the host cores
 # --------------------------------------------------------------------------
 
+# how each arm runs, in the same words in both lines' config (each statement true of its arm), so that
+# the two lines' configurations compare equal
+RUN_NOTES = {"l2": "GPU arm: L2 flushed between timed steps (256 MiB device write); reference arm: host CPU, no GPU",
+             "parallelism": "GPU arm: one solver per GPU (replicas, no collective); reference arm: the oracle on "
+                            "the host cores (OpenMP)"}
+
+
 def oracle_solve_rate(pr, mags, budget_s: float, min_runs: int = 1, threads: int = 0):
     """Oracle solves (2D + 3D multigrid to 1e-10, fields) per second for about budget_s seconds;
     threads = 0: every host core."""
@@ -146,7 +153,7 @@ def run_reference(args):
     per = sum(times) / len(times)
     value = S.unknowns(pr) / per
     cores = oracle.max_threads()
-    cfg = dict(cfg, mode="fp64", parallelism=f"oracle, OpenMP {cores} threads")
+    cfg = dict(cfg, mode="fp64", **RUN_NOTES)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
@@ -428,8 +435,7 @@ def run_gpu(args):
     if rank == 0:
         name = "mixed" if mode == M.MHS_MIXED else "fp64"
         oname = "fp64" if name == "mixed" else "mixed"
-        cfg = dict(cfg, mode=name, l2="flushed between timed steps (256 MiB device write)",
-                   parallelism="replicas" if world > 1 else "single GPU")
+        cfg = dict(cfg, mode=name, **RUN_NOTES)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

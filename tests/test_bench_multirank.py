@@ -71,6 +71,10 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["metric"] == "unknowns solved/s to 1e-10 rel. residual" and d["unit"] == "unknowns/s"
     assert d["config"]["workload"] == "linear_mhs_129"
+    # the configuration the GPU arm prints: the workload, the FP64 mode and the same run notes
+    import bench
+    pr, mags, cfg = bench.workload(0)
+    assert d["config"] == dict(cfg, mode="fp64", **bench.RUN_NOTES)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
