@@ -898,8 +898,8 @@ mhs_status part_wait(GPart* G, mhs_solve_info* infos, mhs_status* statuses, doub
         const SolveCtl& b = G->gathered_host[n + q];
         c->ctl_host[0] = a;
         c->ctl_host[1] = b;
-        max2 = std::max(max2, a.cycles);
-        max3 = std::max(max3, b.cycles);
+        max2 = std::max(max2, a.bodies);   // while iterations: the most bodies any instance ran
+        max3 = std::max(max3, b.bodies);
         mhs_status s = MHS_OK;
         if (a.status != MHS_OK || b.status != MHS_OK) s = MHS_ERR_NONFINITE;
         else if (!(a.bnorm == 0.0 || a.rel < tol) || !(b.bnorm == 0.0 || b.rel < tol)) s = MHS_ERR_NO_CONVERGENCE;

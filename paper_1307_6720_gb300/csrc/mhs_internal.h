@@ -138,6 +138,7 @@ struct SolveCtl {
     int cycles;
     int status;        // MHS_OK or MHS_ERR_NONFINITE
     int cont;          // 1 while another cycle is needed
+    int bodies;        // cycles run by a while body (the full-multigrid cycle of the prologue is not one)
 };
 
 // One level of a multigrid sub-hierarchy solved inside a single CTA.

@@ -824,7 +824,7 @@ mhs_status solve_end(mhs_ctx* c, double tol, int mode, mhs_solve_info* info) {
     const SolveCtl& b = c->ctl_host[1];
     if (c->pending_graph) {
         const long long* n = c->launched_count;
-        count_launches(n[0] + a.cycles * n[1] + n[2] + b.cycles * n[3]);
+        count_launches(n[0] + a.bodies * n[1] + n[2] + b.bodies * n[3]);
     }
     if (info) {
         info->cycles_2d = a.cycles;

@@ -32,6 +32,7 @@ __device__ __forceinline__ void bnorm_body(const double* __restrict__ partial, i
         ctl->cycles = 0;
         ctl->status = MHS_OK;
         ctl->cont = 0;
+        ctl->bodies = 0;
     }
 }
 
@@ -50,6 +51,7 @@ __device__ __forceinline__ int check_body(const double* __restrict__ partial, in
         const double b = ctl->bnorm;
         const double rel = b > 0.0 ? rn / b : 0.0;
         if (first == 0 || (first == 2 && ctl->cont)) ctl->cycles += 1;
+        if (first == 0) ctl->bodies += 1;
         ctl->rel = rel;
         if (first == 1) ctl->rel0 = rel;
         cont = (b > 0.0 && rel >= ctl->tol && ctl->cycles < ctl->max_cycles) ? 1 : 0;

@@ -127,13 +127,21 @@ def test_group_per_instance_status_and_errors(M):
 
 def test_group_eager_launches_match_graph(M):
     """The host-driven form of a group solve (for profilers) runs the same
-    launches as the graph: bitwise the same P and cycle counts."""
+    launches as the graph: bitwise the same P and cycle counts, and as many
+    launches as the graph path accounts for (per-section counts times the
+    while-loop iterations)."""
     hs, prs, _ = _members(M, seed=3)
     g = M.mhs_group_create(hs, M.MHS_MIXED)
+    M.mhs_group_solve(g, len(hs), 1e-10)
+    n0 = M.mhs_kernel_launches()
     infos_g, _ = M.mhs_group_solve(g, len(hs), 1e-10)
+    n_graph = M.mhs_kernel_launches() - n0
     ref = [_phi(M, h, pr) for h, pr in zip(hs, prs)]
     M.mhs_group_set_eager(g, True)
+    n0 = M.mhs_kernel_launches()
     infos_e, sts = M.mhs_group_solve(g, len(hs), 1e-10)
+    n_eager = M.mhs_kernel_launches() - n0
+    assert n_graph == n_eager > 0, (n_graph, n_eager)
     assert all(s == M.MHS_OK for s in sts)
     for q, (h, pr) in enumerate(zip(hs, prs)):
         assert infos_e[q]["cycles_3d"] == infos_g[q]["cycles_3d"]

@@ -229,22 +229,28 @@ def test_mimetic_bz_divergence_free(M):
 def test_graph_and_eager_paths_agree_bitwise(M, mode):
     """The captured solve (conditional while nodes, device-side convergence
     test) and the eager launch sequence run the same kernels in the same
-    order: identical results, cycle counts and residuals."""
+    order: identical results, cycle counts and residuals, and the launch
+    count the graph path reports from its per-section counts and the number
+    of while-body iterations equals the eager path's count of its launches."""
     pr, bz = S.linear_mhs(65, seed=12)
     out = []
     for timing in (False, True):   # kernel timing forces the eager path
         h = M.mhs_create(65, 65, 65, 1.0, 1.0, 1.0, pr["alpha"], _xi(M, pr))
         M.mhs_set_kernel_timing(h, timing)
         M.mhs_set_lower_bz(h, bz)
+        M.mhs_solve(h, 1e-10, mode)   # first solve: capture, coefficients
+        n0 = M.mhs_kernel_launches()
         info = M.mhs_solve(h, 1e-10, mode)
+        n = M.mhs_kernel_launches() - n0
         phi = np.zeros((65, 65, 65))
         M.mhs_get_phi(h, phi)
         M.mhs_destroy(h)
-        out.append((info, phi))
-    (ia, pa), (ib, pb) = out
+        out.append((info, phi, n))
+    (ia, pa, na), (ib, pb, nb) = out
     assert np.array_equal(pa, pb)
     for k in ("cycles_2d", "cycles_3d", "rel_res_2d", "rel_res_3d"):
         assert ia[k] == ib[k], k
+    assert na == nb > 0, (na, nb)
 
 
 def test_repeated_graph_launches_and_option_changes(M):
