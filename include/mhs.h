@@ -444,6 +444,13 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
  *                    (zero boundary values; the level's r and t are
  *                    scratch); levels whose sine transforms are fast
  *                    or short (see sep_coarse), else MHS_ERR_INVALID_ARG
+ *   MHS_OP_RESTRICT_RED: MHS_OP_RESTRICT of a residual taken right after a
+ *                    red-black sweep, which vanishes at the black nodes
+ *                    (i+j+k odd): only the centre and the 12 edge neighbours
+ *                    of each fine node under a coarse one are read (the
+ *                    form the FP64 V-cycles use); r[level] must be +0 at
+ *                    the black nodes, where the result then equals
+ *                    MHS_OP_RESTRICT's
  * For the finest interior level, A includes the Dirichlet data held in u's
  * boundary entries.  Errors: MHS_ERR_INVALID_ARG, MHS_ERR_CUDA. */
 #define MHS_FIELD_U 0
@@ -457,6 +464,7 @@ MHS_API mhs_status mhs_level_shape(mhs_handle h, int dim, int level, int* nx, in
 #define MHS_OP_VCYCLE 5
 #define MHS_OP_EXACT 6
 #define MHS_OP_RESID_RESTRICT 7
+#define MHS_OP_RESTRICT_RED 8
 MHS_API mhs_status mhs_level_write(mhs_handle h, int dim, int level, int field, int prec, const double* src);
 MHS_API mhs_status mhs_level_read(mhs_handle h, int dim, int level, int field, int prec, double* dst);
 MHS_API mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec);

@@ -576,9 +576,10 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
     mhs_status s = level_check(h, dim, level, MHS_FIELD_U, prec);
     if (s != MHS_OK) return s;
     mhs::Hierarchy& H = dim == 3 ? h->h3 : h->h2;
-    if ((op == MHS_OP_RESTRICT || op == MHS_OP_PROLONG || op == MHS_OP_RESID_RESTRICT) && level >= H.nlev() - 1)
+    if ((op == MHS_OP_RESTRICT || op == MHS_OP_PROLONG || op == MHS_OP_RESID_RESTRICT || op == MHS_OP_RESTRICT_RED) &&
+        level >= H.nlev() - 1)
         return fail(MHS_ERR_INVALID_ARG, "no coarser level");
-    if (op < MHS_OP_SMOOTH || op > MHS_OP_RESID_RESTRICT) return fail(MHS_ERR_INVALID_ARG, "unknown op");
+    if (op < MHS_OP_SMOOTH || op > MHS_OP_RESTRICT_RED) return fail(MHS_ERR_INVALID_ARG, "unknown op");
     if (op == MHS_OP_EXACT && !mhs::sep_level_ok(H.g[level]))
         return fail(MHS_ERR_INVALID_ARG, "exact solve needs nx - 1 and ny - 1 powers of two, or nx, ny <= 66");
     return guarded([&] {
@@ -592,6 +593,9 @@ mhs_status mhs_level_op(mhs_handle h, int dim, int level, int op, int prec) {
                 mhs::launch_residual<T>(g, dim, A.coef, A.u, A.f, A.r, nullptr, 0, st);
                 break;
             case MHS_OP_RESTRICT: mhs::launch_restrict<T>(g, H.g[level + 1], dim, A.r, C.f, (T*)nullptr, st); break;
+            case MHS_OP_RESTRICT_RED:
+                mhs::launch_restrict<T>(g, H.g[level + 1], dim, A.r, C.f, (T*)nullptr, st, true);
+                break;
             case MHS_OP_PROLONG: mhs::launch_prolong<T>(H.g[level + 1], g, dim, C.u, A.u, st); break;
             case MHS_OP_COARSE:
                 if (2 * g.n * sizeof(T) > 200 * 1024) throw mhs::Error(MHS_ERR_INVALID_ARG, "level too large for the one-CTA solve");

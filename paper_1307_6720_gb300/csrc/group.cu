@@ -215,6 +215,8 @@ void build_dim(GPart* G, GDim& D, int dim) {
                 rs.p[1] = C.f;
                 rs.p[2] = C.u;
                 rs.ia[1] = top;
+                rs.ia[2] = red_l ? 1 : 0;                                      // after this level's residual
+                rs.ia[3] = (l == 0 && red_residual_rotated(c, H)) ? 1 : 0;    // in a rotated cycle
                 restr[l].push_back(rs);
             } else {   // FP32 levels: the solo V-cycle's fused residual and restriction
                 GItem r = item(q, fat(resid_restrict_grid(gc, d3)), g, ctl);
@@ -562,7 +564,7 @@ void gvcycle(GPart* G, GDim& D, int s, int fmg_step, int gate) {
 void gvcycle_rotated(GPart* G, GDim& D, int gate) {
     cudaStream_t st = G->stream;
     const int d3 = D.dim == 3;
-    glaunch_restrict<double>(D.restr[0], d3, -1, gate, st);
+    glaunch_restrict<double>(D.restr[0], d3, -1, gate, st, 1);
     gvcycle_from<double>(G, D, 1, -1, gate, false);
     const SubParams<double>* params = static_cast<const SubParams<double>*>(D.params);
     glaunch_subcycle<double>(D.subz, params, d3, 0, -1, gate, D.sub_smem, 32, st);

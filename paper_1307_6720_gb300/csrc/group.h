@@ -48,7 +48,7 @@ void glaunch_residual(const GTable& t, int d3, int fmg_step, int gate, cudaStrea
 template <typename T>
 void glaunch_residual_norm(const GTable& t, int d3, int gate, cudaStream_t st);
 template <typename T>
-void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st);
+void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st, int rotated = 0);
 // residual and restriction in one pass (FP32 levels; items: p = u, f, coarse
 // f, coarse u)
 template <typename T>

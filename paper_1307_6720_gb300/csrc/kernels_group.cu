@@ -118,13 +118,15 @@ __global__ void __launch_bounds__(RR_THREADS) g_resid_restrict_kernel(const GIte
                                k.gd);
 }
 
+// rotated: the restriction of a rotated FP64 cycle (red residual flag in
+// ia[3]) rather than of a V-cycle level after its own residual (ia[2])
 template <typename T, bool D3>
-__global__ void g_restrict_kernel(const GItem* items, int n, int fmg_step, int gate) {
+__global__ void g_restrict_kernel(const GItem* items, int n, int fmg_step, int gate, int rotated) {
     GBlock k;
     if (!locate(items, n, gate, -1, fmg_step, k)) return;
     const GItem& it = *k.it;
     restrict_body<T, D3>(it.g, it.g2, static_cast<const T*>(it.p[0]), static_cast<T*>(it.p[1]),
-                         static_cast<T*>(it.p[2]), k.b, k.gd);
+                         static_cast<T*>(it.p[2]), k.b, k.gd, (rotated ? it.ia[3] : it.ia[2]) != 0);
 }
 
 template <typename T, bool D3>
@@ -299,10 +301,10 @@ void glaunch_residual_norm(const GTable& t, int d3, int gate, cudaStream_t st) {
 }
 
 template <typename T>
-void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st) {
+void glaunch_restrict(const GTable& t, int d3, int fmg_step, int gate, cudaStream_t st, int rotated) {
     if (!t.n) return;
-    if (d3) g_restrict_kernel<T, true><<<t.blocks, kMG, 0, st>>>(t.items, t.n, fmg_step, gate);
-    else g_restrict_kernel<T, false><<<t.blocks, kMG, 0, st>>>(t.items, t.n, fmg_step, gate);
+    if (d3) g_restrict_kernel<T, true><<<t.blocks, kMG, 0, st>>>(t.items, t.n, fmg_step, gate, rotated);
+    else g_restrict_kernel<T, false><<<t.blocks, kMG, 0, st>>>(t.items, t.n, fmg_step, gate, rotated);
     after_launch();
 }
 
@@ -424,7 +426,7 @@ void glaunch_gather_ctl(SolveCtl* const* ctls, int n, SolveCtl* out, cudaStream_
     template void glaunch_zline<T>(const GTable&, int, int, int, int, cudaStream_t);                          \
     template void glaunch_residual<T>(const GTable&, int, int, int, cudaStream_t);                            \
     template void glaunch_residual_norm<T>(const GTable&, int, int, cudaStream_t);                            \
-    template void glaunch_restrict<T>(const GTable&, int, int, int, cudaStream_t);                            \
+    template void glaunch_restrict<T>(const GTable&, int, int, int, cudaStream_t, int);                            \
     template void glaunch_resid_restrict<T>(const GTable&, int, int, int, cudaStream_t);                      \
     template void glaunch_prolong<T>(const GTable&, int, int, int, cudaStream_t);                             \
     template void glaunch_subcycle<T>(const GTable&, const SubParams<T>*, int, int, int, int, size_t, int, cudaStream_t);

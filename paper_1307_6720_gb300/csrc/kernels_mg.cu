@@ -234,8 +234,9 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int n, do
 }
 
 template <typename T, bool D3>
-__global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc, T* __restrict__ uc) {
-    restrict_body<T, D3>(gf, gc, rf, fc, uc, blockIdx, gridDim);
+__global__ void restrict_kernel(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ fc, T* __restrict__ uc,
+                                int red) {
+    restrict_body<T, D3>(gf, gc, rf, fc, uc, blockIdx, gridDim, red != 0);
 }
 
 template <typename T, bool D3>
@@ -498,11 +499,12 @@ void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t 
 }
 
 template <typename T>
-void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st) {
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st,
+                     bool red) {
     const int d3 = dim == 3;
     const dim3 grid = restrict_grid(gc, d3);
-    if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
-    else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero);
+    if (d3) restrict_kernel<T, true><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero, red ? 1 : 0);
+    else restrict_kernel<T, false><<<grid, dim3(BX, BY), 0, st>>>(gf, gc, rf, fc, uc_zero, red ? 1 : 0);
     count_launches(1);
     MHS_CUDA(cudaGetLastError());
 }
@@ -588,7 +590,7 @@ int launch_lift_norm(const Geom& g3, const PlaneCoef<double>* coef, const double
     template void launch_smooth<T>(const Geom&, int, const PlaneCoef<T>*, T*, const T*, cudaStream_t, int);    \
     template int launch_residual<T>(const Geom&, int, const PlaneCoef<T>*, const T*, const T*, T*, double*,    \
                                     int, cudaStream_t, bool);                                                  \
-    template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t);           \
+    template void launch_restrict<T>(const Geom&, const Geom&, int, const T*, T*, T*, cudaStream_t, bool);           \
     template void launch_resid_restrict<T>(const Geom&, const Geom&, int, const PlaneCoef<T>*, const T*, const T*, \
                                            T*, T*, cudaStream_t);                                                 \
     template void launch_prolong<T>(const Geom&, const Geom&, int, const T*, T*, cudaStream_t);                \

@@ -201,22 +201,46 @@ __device__ __forceinline__ void residual_body_v4(const Geom& g, const PlaneCoef<
 // make this the same weighted sum up to the order of the additions.  With
 // uc != nullptr the coarse iterate is zeroed at the same nodes (the initial
 // guess of the coarse-grid correction).
+//
+// red: rf is a residual taken right after a red-black sweep, zero (stored as
+// +0) at the black nodes, those with i + j + k odd.  The fine node under a
+// coarse one is red, so of its 27 neighbours only the centre and the 12 edge
+// neighbours (two offsets non-zero) can be non-zero, and each (1, 2, 1) triple
+// has either zero ends (fma(2, b, +0) = 2b) or a zero middle
+// (fma(2, +0, a + c) = a + c): the same sums are formed from the 13 red
+// values with 18 instead of 27 FP64 operations, equal to the full form's
+// (up to the sign of a zero result).
 template <typename T, bool D3>
 __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, const T* __restrict__ rf,
-                                              T* __restrict__ fc, T* __restrict__ uc, dim3 b, dim3 gd) {
+                                              T* __restrict__ fc, T* __restrict__ uc, dim3 b, dim3 gd,
+                                              bool red = false) {
     const int I = 1 + b.x * blockDim.x + threadIdx.x;
     const int J = 1 + b.y * blockDim.y + threadIdx.y;
     if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    const ptrdiff_t sy = (ptrdiff_t)gf.px, sz = (ptrdiff_t)gf.plane;
     for (int K = D3 ? 1 + b.z : 0; K <= (D3 ? gc.nz - 2 : 0); K += gd.z) {
         const size_t o = at(gf, 2 * I, 2 * J, D3 ? 2 * K : 0);
-        auto row = [&](size_t ob) { return fma(T(2), rf[ob], rf[ob - 1] + rf[ob + 1]); };
-        auto plane = [&](size_t oc) { return fma(T(2), row(oc), row(oc - gf.px) + row(oc + gf.px)); };
         T acc;
-        if (D3) {
-            const T lo = plane(o - gf.plane), mid = plane(o), hi = plane(o + gf.plane);
-            acc = fma(T(2), mid, lo + hi) * T(1.0 / 64.0);
+        if (red) {
+            const T* q = rf + o;
+            // a plane whose centre node is red: centre row 2b, the two off rows a + c
+            auto plane_r = [&](const T* c) { return fma(T(2), fma(T(2), c[0], T(0)), (c[-sy - 1] + c[-sy + 1]) + (c[sy - 1] + c[sy + 1])); };
+            if (D3) {
+                // a plane whose centre node is black: centre row a + c, the two off rows 2b
+                auto plane_b = [&](const T* c) { return fma(T(2), c[-1] + c[1], fma(T(2), c[-sy], T(0)) + fma(T(2), c[sy], T(0))); };
+                acc = fma(T(2), plane_r(q), plane_b(q - sz) + plane_b(q + sz)) * T(1.0 / 64.0);
+            } else {
+                acc = plane_r(q) * T(1.0 / 16.0);
+            }
         } else {
-            acc = plane(o) * T(1.0 / 16.0);
+            auto row = [&](size_t ob) { return fma(T(2), rf[ob], rf[ob - 1] + rf[ob + 1]); };
+            auto plane = [&](size_t oc) { return fma(T(2), row(oc), row(oc - gf.px) + row(oc + gf.px)); };
+            if (D3) {
+                const T lo = plane(o - gf.plane), mid = plane(o), hi = plane(o + gf.plane);
+                acc = fma(T(2), mid, lo + hi) * T(1.0 / 64.0);
+            } else {
+                acc = plane(o) * T(1.0 / 16.0);
+            }
         }
         fc[at(gc, I, J, K)] = acc;
         if (uc) uc[at(gc, I, J, K)] = T(0);

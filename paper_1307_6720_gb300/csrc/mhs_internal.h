@@ -287,7 +287,8 @@ int launch_residual(const Geom& g, int dim, const PlaneCoef<T>* coef, const T* u
 // finish partial sums into *out (fixed order)
 void launch_norm_finish(const double* partial, int n, double* out, cudaStream_t st);
 template <typename T>
-void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st);
+void launch_restrict(const Geom& gf, const Geom& gc, int dim, const T* rf, T* fc, T* uc_zero, cudaStream_t st,
+                     bool red = false);   // red: rf is zero at black nodes (restrict_body)
 template <typename T>
 void launch_prolong(const Geom& gc, const Geom& gf, int dim, const T* uc, T* uf, cudaStream_t st);
 // residual of u and its full-weighting restriction to fc in one launch (the

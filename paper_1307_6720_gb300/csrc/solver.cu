@@ -324,9 +324,11 @@ struct LevelOps {
 
 // the coarse-grid correction of level l from its residual: restriction of
 // the residual in A.r (unless the fused pass of FP32 levels has already
-// restricted it), the coarser cycle, interpolation added to u
+// restricted it; red: A.r is a residual taken on red nodes only), the coarser
+// cycle, interpolation added to u
 template <typename T>
-static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>& o, bool restricted) {
+static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>& o, bool restricted,
+                              bool red = false) {
     cudaStream_t st = c->stream;
     const bool dbl = sizeof(T) == 8;
     LevelArrays<T>& A = arrays<T>(H, l);
@@ -335,7 +337,7 @@ static void coarse_correction(mhs_ctx* c, Hierarchy& H, int l, const LevelOps<T>
     if (!restricted) {
         TimedScope t(c->timer, dbl ? MHS_KT_RESTRICT64 : MHS_KT_RESTRICT32, (N + 2 * Nc) * s,
                      Nc * (H.dim == 3 ? 54.0 : 18.0), st, o.fine);
-        launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, A.r, C.f, C.u, st);
+        launch_restrict<T>(H.g[l], H.g[l + 1], H.dim, A.r, C.f, C.u, st, red);
     }
     vcycle<T>(c, H, l + 1);
     {
@@ -390,7 +392,7 @@ void vcycle(mhs_ctx* c, Hierarchy& H, int l) {
         TimedScope t(c->timer, MHS_KT_RESID64, sweep_bytes, o.N * o.res_flops, st, o.fine);
         launch_residual<T>(g, H.dim, A.coef, A.u, o.f, A.r, nullptr, 0, st, red_residual_level(c, H));
     }
-    coarse_correction<T>(c, H, l, o, !dbl);
+    coarse_correction<T>(c, H, l, o, !dbl, dbl && red_residual_level(c, H));
     smooth_n<T>(c, H, l, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
 }
 
@@ -419,10 +421,18 @@ bool red_residual_fmg(const mhs_ctx* c, const Hierarchy& H) {
     return rotated_cycles(c, H) && point_smoothing(c, H) && c->opts.nu2 >= 1;
 }
 
+// the residual that a rotated cycle restricts (that of the latest test: the
+// full-multigrid cycle's for the first cycle, a rotated cycle's after it) is
+// taken on red nodes whichever test it comes from; without the full-multigrid
+// cycle the first one is the full residual of the solve's first test
+bool red_residual_rotated(const mhs_ctx* c, const Hierarchy& H) {
+    return red_residual_cycle(c, H) && red_residual_fmg(c, H) && !(c->opts.flags & MHS_FLAG_NO_FMG);
+}
+
 static void vcycle_rotated(mhs_ctx* c, Hierarchy& H) {
     const LevelOps<double> o(c, H, 0);
     const double sweep_bytes = o.N * (2 * o.s + o.fs);
-    coarse_correction<double>(c, H, 0, o, false);
+    coarse_correction<double>(c, H, 0, o, false, red_residual_rotated(c, H));
     smooth_n<double>(c, H, 0, o.f, c->opts.nu2, o.fine, sweep_bytes, o.N * o.upd_flops);
     smooth_n<double>(c, H, 0, o.f, c->opts.nu1, o.fine, sweep_bytes, o.N * o.upd_flops);
 }

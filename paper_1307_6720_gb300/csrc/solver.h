@@ -87,6 +87,7 @@ bool rotated_cycles(const mhs_ctx* c, const Hierarchy& H);
 bool red_residual_level(const mhs_ctx* c, const Hierarchy& H);
 bool red_residual_cycle(const mhs_ctx* c, const Hierarchy& H);
 bool red_residual_fmg(const mhs_ctx* c, const Hierarchy& H);
+bool red_residual_rotated(const mhs_ctx* c, const Hierarchy& H);
 
 // conversions between the FP64 staging buffer and FP32 level arrays (kernels_mg.cu)
 void launch_d2f(const double* src, float* dst, size_t n, cudaStream_t st);

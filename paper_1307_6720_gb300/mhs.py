@@ -28,7 +28,7 @@ MHS_FLAG_ZLINE, MHS_FLAG_POINT, MHS_FLAG_SEPARABLE, MHS_FLAG_LOWER_FP64 = 64, 12
 MHS_FLAG_STAGED_TRANSFORMS = 1024
 MHS_FIELD_U, MHS_FIELD_F, MHS_FIELD_R = 0, 1, 2
 (MHS_OP_SMOOTH, MHS_OP_RESIDUAL, MHS_OP_RESTRICT, MHS_OP_PROLONG, MHS_OP_COARSE, MHS_OP_VCYCLE, MHS_OP_EXACT,
- MHS_OP_RESID_RESTRICT) = range(8)
+ MHS_OP_RESID_RESTRICT, MHS_OP_RESTRICT_RED) = range(9)
 
 
 class XiParams(ctypes.Structure):

@@ -120,6 +120,37 @@ def test_residual_after_sweep_vanishes_on_black_nodes(M, shape):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dim", [3, 2])
+@pytest.mark.parametrize("shape", [(33, 17, 9), (67, 35, 19)])
+def test_red_restriction_equals_full_restriction(M, dim, prec, shape):
+    """The restriction the FP64 V-cycles apply to a residual taken right after
+    a red-black sweep reads only the red nodes (i+j+k even) of the 27-point
+    stencil; on a residual that is +0 at every black node it gives the values
+    of the full restriction (same sums, the zero terms left out) and the
+    oracle's full weighting."""
+    nx, ny, nz = shape
+    pr, h = _make(M, nx, ny, nz)
+    rng = np.random.default_rng(17)
+    fine = (nz, ny, nx) if dim == 3 else (ny, nx)
+    r = rng.standard_normal(fine)
+    idx = np.indices(fine).sum(axis=0)
+    r[idx % 2 == 1] = 0.0
+    inner = (slice(1, -1),) * len(fine)
+    mask = np.zeros(fine, bool); mask[inner] = True
+    r[~mask] = 0.0
+    out = []
+    for op in (M.MHS_OP_RESTRICT, M.MHS_OP_RESTRICT_RED):
+        M.mhs_level_write(h, dim, 0, M.MHS_FIELD_R, prec, r)
+        M.mhs_level_op(h, dim, 0, op, prec)
+        out.append(_read(M, h, dim, 1, M.MHS_FIELD_F, prec))
+    assert np.array_equal(out[0], out[1])
+    want = oracle.restrict(r if prec == 0 else r.astype(np.float32).astype(np.float64))
+    cin = (slice(1, -1),) * len(fine)
+    assert _rel(out[1][cin], want[cin]) < _tol(prec)
+    M.mhs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [3, 2])
 def test_restriction_and_prolongation_parity(M, dim, prec):
     nx, ny, nz = 33, 17, 9
     pr, h = _make(M, nx, ny, nz)
