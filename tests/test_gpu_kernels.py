@@ -74,6 +74,38 @@ def test_smooth_parity_3d(M, shape, prec):
     M.mhs_destroy(h)
 
 
+@pytest.mark.parametrize("shape", [(17, 17, 9), (33, 33, 17), (9, 9, 33), (67, 67, 11)])
+def test_fp64_smooth_with_equal_xy_coefficients(M, shape):
+    """FP64 sweeps on planes whose x and y coefficients are equal (h_x = h_y,
+    as in the linear-MHS workloads): the colour passes agree with the oracle's
+    red-black sweeps to rounding in 3D and on the lower-boundary level, and
+    the fused out-of-place FP64 sweep gives bitwise the same iterate."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + nz)
+    u = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 30
+    out = []
+    for flags in (0, M.MHS_FLAG_FUSED_SWEEP64):
+        pr, h = _make(M, nx, ny, nz, Ly=1.0)
+        M.mhs_set_options(h, flags=flags | M.MHS_FLAG_POINT, sep_coarse=-1)
+        M.mhs_level_write(h, 3, 0, M.MHS_FIELD_U, 0, u)
+        M.mhs_level_write(h, 3, 0, M.MHS_FIELD_F, 0, f)
+        for _ in range(3):
+            M.mhs_level_op(h, 3, 0, M.MHS_OP_SMOOTH, 0)
+        out.append(_read(M, h, 3, 0, M.MHS_FIELD_U, 0))
+        if flags == 0:   # the lower-boundary level: 5-point passes
+            u2 = rng.standard_normal((ny, nx))
+            f2 = rng.standard_normal((ny, nx)) * 30
+            M.mhs_level_write(h, 2, 0, M.MHS_FIELD_U, 0, u2)
+            M.mhs_level_write(h, 2, 0, M.MHS_FIELD_F, 0, f2)
+            for _ in range(3):
+                M.mhs_level_op(h, 2, 0, M.MHS_OP_SMOOTH, 0)
+            assert _rel(_read(M, h, 2, 0, M.MHS_FIELD_U, 0), oracle.rbgs2d(pr, u2, f2, 3)) < 1e-12
+        M.mhs_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    assert _rel(out[0], oracle.rbgs3d(pr, u, f, 3)) < 1e-12
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_residual_parity_3d(M, shape, prec):
