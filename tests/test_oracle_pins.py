@@ -422,6 +422,39 @@ def test_restriction_is_scaled_adjoint_of_prolongation(shape):
     assert abs(np.sum(Rr * e) - 2.0**-d * np.sum(r * Ie)) < 1e-12 * np.sum(np.abs(r)) * np.abs(e).max()
 
 
+@pytest.mark.parametrize("shape", [(9, 17, 13), (17, 9)])
+def test_full_weighting_of_red_residual_reads_centre_and_edges(shape):
+    """Full weighting of a fine field that vanishes at the nodes with odd
+    index sum (a residual right after a red-black sweep) is the centre node
+    times 2^-d plus the edge neighbours (two offsets non-zero) times 2^-(d+2):
+    the face and corner neighbours of the fine node under a coarse one all
+    have odd index sums.  The GPU's red-node restriction reads only these 13
+    (2D: 5) nodes; this fixes the identity from the definition of full
+    weighting, independently of both implementations."""
+    d = len(shape)
+    rng = np.random.default_rng(23)
+    r = rng.standard_normal(shape)
+    r[np.indices(shape).sum(axis=0) % 2 == 1] = 0.0
+    inner = tuple(slice(1, -1) for _ in shape)
+    mask = np.zeros(shape, bool); mask[inner] = True
+    r[~mask] = 0.0
+    Rr = oracle.restrict(r)
+    cs = oracle.coarse_shape(shape)
+    want = np.zeros(cs)
+    offs = [o for o in np.ndindex(*(3,) * d)]
+    for C in np.ndindex(*cs):
+        if any(c == 0 or c == n - 1 for c, n in zip(C, cs)):
+            continue
+        F = tuple(2 * c for c in C)
+        acc = 2.0**-d * r[F]
+        for o in offs:
+            off = tuple(x - 1 for x in o)
+            if sum(1 for x in off if x) == 2:
+                acc += 2.0**-(d + 2) * r[tuple(f + x for f, x in zip(F, off))]
+        want[C] = acc
+    assert np.allclose(Rr, want, rtol=1e-14, atol=1e-15)
+
+
 def test_transfer_operators_reproduce_linear_functions():
     shape = (9, 13, 17)
     cs = oracle.coarse_shape(shape)
